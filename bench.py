@@ -1,0 +1,348 @@
+#!/usr/bin/env python3
+"""Throughput of the GB300 EM-PIC timestep (gather + Boris push + Esirkepov
+deposit + Yee update) in particle-steps/s, with the HBM roofline fraction of
+the dominant kernel, the end-to-end figure through the C ABI with host
+buffers, and the FP64 oracle timed on the host cores as the CPU baseline.
+
+Default workload: 3D laser-wakefield box 256x256x1024 cells (x, y
+transverse, z the propagation axis), dx=dy=1, dz=0.3, dt=0.27 c/omega0,
+n=0.0025 n_c at 8 particles per cell (536,870,912 electrons), cold, a0=4
+laser (waist 60, FWHM 30), open z with a moving window, quadratic shapes,
+FP32.  A step is one full timestep of every particle and cell.
+
+    python bench.py [--steps K] [--warmup W] [--impl native|reference]
+Under torchrun each rank advances its own replica on its own GPU (the path
+has no exchange step on one GPU), timed with a barrier on both sides.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (gather+push+deposit), % HBM roofline; batched & adjoint vs plain"
+UNIT = "particle-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="lwfa_3d", choices=["lwfa_3d", "thermal_2d", "bunch_3d"])
+    ap.add_argument("--scale", type=float, default=1.0, help="shrink every grid axis (debug runs only)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget-s", type=float, default=20.0)
+    ap.add_argument("--tuning", default="", help="json dict of pic_tuning overrides")
+    ap.add_argument("--out", default="", help="also write the JSON line to this file")
+    return ap.parse_args()
+
+
+def workload(name, scale):
+    from paper_1310_0930_gb300 import inputs
+    if name == "lwfa_3d":
+        n = (256, 256, 1024)
+        if scale != 1.0:
+            n = tuple(max(16, int(round(v * scale / 8)) * 8) for v in n)
+        return inputs.lwfa_3d(n=n)
+    if name == "bunch_3d":
+        return inputs.bunch_3d()
+    return inputs.thermal_2d()
+
+
+def particle_chunks(w):
+    from paper_1310_0930_gb300 import inputs
+    if w.dim == 3:
+        chunks = list(inputs.background_chunks(w, 64))
+    else:
+        chunks = [inputs.background(w)]
+    if w.bunch is not None:
+        chunks.append(inputs.bunch(w))
+    return chunks
+
+
+def algorithmic_bytes(w, n_particles):
+    """Bytes the method must move once per step (state read + write): per
+    particle 2 * (4 packed cell + 4*dim offsets + 12 momentum [+4 weight]);
+    per cell 96 = gather E,B (24) + J write (12) + Yee reads E,B,J (36) +
+    writes E,B (24).  The push kernel alone: particles + 36 B per cell."""
+    sp = 4 + 4 * w.dim + 12 + (4 if (w.knots is not None or w.bunch is not None) else 0)
+    step = n_particles * 2 * sp + w.n_cells * 96
+    push = n_particles * 2 * sp + w.n_cells * 36
+    return step, push, sp
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.proc = None
+        sel = []
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            sel = ["-i", uuid if uuid.startswith("GPU-") else "GPU-" + uuid]
+        except Exception:
+            sel = []
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                          "-lms", "200"] + sel, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(w, budget_s, steps_hint=None):
+    """Time the FP64 oracle, as it stands, on a bounded crop of the same
+    workload (same cells, dt, density, ppc, order, laser) on all host cores."""
+    import oracle
+    from paper_1310_0930_gb300 import inputs
+    cores = os.cpu_count() or 1
+
+    def make(ncrop):
+        c = inputs.Workload(w.name, w.dim, ncrop, w.d, w.dt, w.order, w.ppc, w.density, uth=w.uth,
+                            jitter=w.jitter, seed=w.seed, open_last=w.open_last, laser=w.laser, window=w.window)
+        parts = inputs.background(c)
+        laser = None
+        if c.laser is not None:
+            L = c.laser
+            laser = dict(a0=L.a0, waist=L.waist, fwhm=L.fwhm, plane=L.plane, pol=L.pol, t_peak=L.peak_time())
+        sim = oracle.Sim(c.dim, c.n, c.d, c.dt, c.order, open_last=c.open_last, laser=laser, nthreads=cores)
+        x = np.zeros((3, parts.n))
+        x[: c.dim] = parts.positions64()
+        sim.load(x, parts.u.astype(np.float64), parts.w.astype(np.float64))
+        return sim, parts.n
+
+    # calibrate on a small crop, then size the sample to the budget
+    if w.dim == 3:
+        base = (16, 16, 64)
+    else:
+        base = (32, 32)
+    sim, n = make(base)
+    t0 = time.perf_counter()
+    sim.step(1)
+    t_ps = (time.perf_counter() - t0) / n
+    steps = steps_hint or 3
+    target = max(n, int(budget_s / max(t_ps, 1e-9) / steps))
+    if w.dim == 3:
+        grow = max(1.0, (target / n) ** 0.5)
+        ncrop = (min(w.n[0], int(16 * grow) // 8 * 8 or 16), min(w.n[1], int(16 * grow) // 8 * 8 or 16), 64)
+    else:
+        grow = max(1.0, (target / n) ** 0.5)
+        ncrop = (min(w.n[0], int(32 * grow) // 8 * 8), min(w.n[1], int(32 * grow) // 8 * 8))
+    sim, n = make(ncrop)
+    t0 = time.perf_counter()
+    sim.step(steps)
+    dt_s = time.perf_counter() - t0
+    return {"value": n * steps / dt_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "FP64 oracle, %s crop %s cells (%d particles, same d/dt/density/ppc/order/laser), "
+                      "%d steps, %.1f s" % (w.name, "x".join(map(str, ncrop)), n, steps, dt_s)}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = workload(args.workload, args.scale)
+    per_step_budget = 60.0 / max(1, args.steps + args.warmup)
+    cb = cpu_baseline(w, per_step_budget * (args.steps + args.warmup), steps_hint=args.steps + args.warmup)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "grid": list(w.n), "ppc": list(w.ppc), "order": w.order},
+            "cpu_baseline": {"kind": cb["kind"], "cores": cb["cores"], "sample": cb["sample"], "value": cb["value"]},
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    from paper_1310_0930_gb300.sim import Simulation, TorchMemory
+    from paper_1310_0930_gb300 import inputs
+
+    w = workload(args.workload, args.scale)
+    tuning = json.loads(args.tuning) if args.tuning else None
+    chunks = particle_chunks(w)
+    n0 = sum(c.n for c in chunks)
+    room = 4 * int(np.prod(w.n[:-1])) * w.ppc_total * 12 + 65536
+    cap = n0 + room
+
+    # ---- device-resident throughput (inputs already in HBM) ----------------
+    mem = TorchMemory(device=local)
+    sim = Simulation(w, tuning=tuning, capacity=cap, memory=mem)
+    for c in chunks:
+        sim.load(c)
+    sim.step(args.warmup)
+    sim.sync()
+    d0 = sim.diagnostics()
+    st = mem.stream
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(local)
+    sim.profile_begin(args.steps)
+    barrier()
+    torch.cuda.synchronize()
+    ev0.record(st)
+    sim.step(args.steps)
+    ev1.record(st)
+    torch.cuda.synchronize()
+    barrier()
+    phases, launches = sim.profile_end()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    d1 = sim.diagnostics()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    n_avg = 0.5 * (d0["n_particles"] + d1["n_particles"])
+    value = world * n_avg * args.steps / (ms / 1e3)
+    step_bytes, push_bytes, sp = algorithmic_bytes(w, n_avg)
+    push_ms = phases["push"] / args.steps
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = push_bytes / (push_ms / 1e3) / 1e9
+    status = d1["status"]
+    sim.close()
+    del sim
+
+    # ---- end to end through the C ABI with host buffers ----------------------
+    e2e = None
+    if not args.no_e2e:
+        pinned = []
+        h2d = 0
+        for c in chunks:
+            arrs = []
+            for a in (c.cell, c.off, c.u, c.w):
+                t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+                arrs.append(t)
+                h2d += t.numel() * t.element_size()
+            pinned.append(inputs.Particles(*[t.numpy() for t in arrs]))
+        mem2 = TorchMemory(device=local)
+        sim2 = Simulation(w, tuning=tuning, capacity=cap, memory=mem2)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for c in pinned:
+            sim2.load(c)
+        for _ in range(args.steps):
+            sim2.step(1)
+            sim2.sync()  # device -> host read of the step's status
+        dd = sim2.diagnostics()  # energies and particle count back to the host
+        t1 = time.perf_counter()
+        barrier()
+        sec = t1 - t0
+        if world > 1:
+            t = torch.tensor([sec], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            sec = float(t.item())
+        e2e = {"value": world * n0 * args.steps / sec, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(96 + 96 / args.steps),
+               "includes": "pic_load_particles from pinned host memory, %d x (pic_step + pic_sync), "
+                           "pic_diagnostics" % args.steps}
+        sim2.close()
+        del sim2, pinned
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, args.cpu_budget_s)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "%s %s cells, %d ppc, order %d" % (w.name, "x".join(map(str, w.n)), w.ppc_total,
+                                                                 w.order),
+                   "grid": list(w.n), "d": list(w.d), "dt": w.dt, "particles": int(n_avg),
+                   "window": w.window is not None, "laser_a0": w.laser.a0 if w.laser else None,
+                   "l2": "inputs larger than L2 (%.1f GB particle state)" % (n_avg * sp / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "timed": "device-resident state, phase events recorded on the library stream"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "push_kernel<%d,%d>" % (w.dim, w.order),
+                     "bytes_per_launch": push_bytes, "avg_launch_ms": push_ms,
+                     "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json)" if peaks else "fallback"},
+        "step_roofline_frac": step_bytes / (ms / args.steps / 1e3) / 1e9 / peak,
+        "phase_ms_per_step": {k: v / args.steps for k, v in phases.items()},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "status": status,
+    }
+    if rank == 0:
+        s = json.dumps(line)
+        print(s, flush=True)
+        if args.out:
+            with open(args.out, "w") as f:
+                f.write(s + "\n")
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

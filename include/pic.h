@@ -1,0 +1,269 @@
+/*
+ * pic.h -- C ABI of the GB300 (sm_103a) electromagnetic particle-in-cell
+ * timestep library.
+ *
+ * One timestep (Fonseca et al., Sec. 2 and Sec. 5.2 steps i-v):
+ *   gather E and B at each particle with order-p B-spline weights, each
+ *   component at its own Yee location (Sec. 5.1, Sec. 5.2 step ii);
+ *   relativistic Boris push of u = gamma*beta (Sec. 2, Sec. 5.2 step iii);
+ *   position update on an integer cell index plus an FP32 offset from the
+ *   cell's lower vertex (Sec. 5.1);
+ *   charge-conserving current deposit on the straight segment (Sec. 5.2,
+ *   Esirkepov's decomposition);
+ *   Yee FDTD update B(1/2) -> E -> B(1/2) (Sec. 2, Sec. 3 "local field
+ *   solver").
+ * Normalised units, c = 1: dE/dt = curl B - J, dB/dt = -curl E, div E = rho.
+ * Lengths in c/omega, fields in m c omega / e, charge and mass in units of
+ * the electron's magnitude.  A particle's weight w is a density (n / ppc):
+ * rho(node) = sum q w S(x - node).
+ *
+ * Layout conventions shared by every call:
+ *   axis 0 is the fastest in memory; field arrays are component arrays of
+ *   n0*n1*n2 FP32 values, idx = i + n0*(j + n1*k) (n2 = 1 in 2D);
+ *   Yee locations in cells: Ex (1/2,0,0) Ey (0,1/2,0) Ez (0,0,1/2)
+ *   Bx (0,1/2,1/2) By (1/2,0,1/2) Bz (1/2,1/2,0); in 2D the third axis is
+ *   absent and Ez, Jz sit on nodes;
+ *   the last axis is the propagation axis of the laser and of the moving
+ *   window; it may be open (Mur fields, absorbing particles); the other axes
+ *   are periodic;
+ *   particle arrays are component-major: cell[dim][n], off[dim][n],
+ *   u[3][n], w[n], id[n].
+ *
+ * Ownership: the library owns all device memory, allocated at pic_create /
+ * first load through the caller's allocator when one is given (else
+ * cudaMalloc).  Host pointers passed in are borrowed for the duration of the
+ * call only.  The CUDA stream is borrowed; every device operation of a
+ * handle is ordered on it.  One handle is used by one host thread at a time.
+ *
+ * Errors: every int-returning call returns PIC_OK (0) or a negative PIC_E*
+ * code and never aborts.  Conditions detected on the device (capacity
+ * overflow, a bounded wait that gave up) are latched in a device status word
+ * and returned by the next pic_sync / pic_diagnostics / read call.
+ */
+#ifndef PIC_GB300_H
+#define PIC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_ABI_VERSION 1
+
+/* exported entry points (the library is built with hidden visibility) */
+#if defined(__GNUC__)
+#define PIC_API __attribute__((visibility("default")))
+#else
+#define PIC_API
+#endif
+
+#define PIC_OK 0
+#define PIC_EINVAL (-1)    /* bad argument or configuration (Courant >= 1, bad order, bits) */
+#define PIC_ENOMEM (-2)    /* allocation failed */
+#define PIC_ECUDA (-3)     /* a CUDA runtime call failed */
+#define PIC_EOVERFLOW (-4) /* particle capacity exceeded (no trap; work dropped and latched) */
+#define PIC_ETIMEOUT (-5)  /* a bounded device wait gave up */
+#define PIC_ESTATE (-6)    /* call not valid in the handle's current state */
+
+#define PIC_BC_PERIODIC 0
+#define PIC_BC_OPEN 1 /* last axis only: first-order Mur fields, absorbing particles */
+
+/* field selectors for pic_read_fields / pic_write_fields */
+#define PIC_EX 0
+#define PIC_EY 1
+#define PIC_EZ 2
+#define PIC_BX 3
+#define PIC_BY 4
+#define PIC_BZ 5
+#define PIC_JX 6
+#define PIC_JY 7
+#define PIC_JZ 8
+#define PIC_RHO 9 /* charge density of the particles (computed on read) */
+
+/* Grid: dim = 2 or 3; n cells per axis (n[2] ignored in 2D); d cell sizes;
+ * dt must satisfy the Yee Courant condition dt * sqrt(sum 1/d^2) < 1
+ * (Sec. 2: "the time step is then chosen according to the Courant
+ * condition").  bc_last: PIC_BC_PERIODIC or PIC_BC_OPEN. */
+typedef struct {
+    int32_t dim;
+    int32_t n[3];
+    double d[3];
+    double dt;
+    int32_t bc_last;
+    int32_t reserved;
+} pic_grid;
+
+/* One mobile species (immobile neutralising ions are implied: the initial
+ * electron charge is the background).  ppc and the density profile are used
+ * for plasma injected by the moving window: ppc[a] particles per axis at
+ * offsets (m + 1/2)/ppc[a], cold, weight density(z_lab)/prod(ppc).
+ * density(z) is piecewise linear through n_knots equally spaced knots over
+ * [profile_z0, profile_z1] (clamped outside), or the constant `density` when
+ * n_knots == 0.  per_particle_weight = 1 makes pic_load_particles require w;
+ * otherwise every particle carries weight w_const. */
+typedef struct {
+    double q, m;
+    int32_t ppc[3];
+    int32_t per_particle_weight;
+    double w_const;
+    double density;
+    const double *profile_knots;
+    int32_t n_knots;
+    int32_t reserved;
+    double profile_z0, profile_z1;
+} pic_species;
+
+/* Laser antenna (Sec. 2 laser driver): one-way plane source at node `plane`
+ * of the last axis, polarised along `pol_axis` (0 in 2D), travelling towards
+ * +last axis: E_inc = a0 exp(-r^2/waist^2) exp(-2 ln2 (xi - t_peak)^2/fwhm^2)
+ * cos(omega0 (xi - t_peak)), xi = t - (z - z_plane), r from the box axis.
+ * Active until the moving window first shifts. */
+typedef struct {
+    int32_t enabled;
+    int32_t pol_axis;
+    int32_t plane;
+    int32_t reserved;
+    double a0, omega0, waist, fwhm, t_peak;
+} pic_laser;
+
+/* Moving window along the last axis (Sec. 2): once t >= t_start the box
+ * shifts one cell back whenever velocity * (t - t_start) passes the next
+ * multiple of d[last]; the new front layer is injected with plasma. */
+typedef struct {
+    int32_t enabled;
+    int32_t reserved;
+    double velocity, t_start;
+} pic_window;
+
+/* Allocator hooks (e.g. the PyTorch caching allocator).  alloc returns a
+ * device pointer of at least `bytes` (16-byte aligned) or NULL. */
+typedef void *(*pic_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*pic_free_fn)(void *ptr, void *ctx);
+
+/* Tuning: tile[a] cells per tile per axis (powers of two, 0 = default);
+ * sort_interval steps between tile sorts (0 = default); drift: cells a
+ * particle may stray outside its tile between sorts and still use the
+ * staged fast path (-1 = default); block: threads per tile CTA (0 = default);
+ * use_graph: capture each step kind in a CUDA graph and replay it. */
+typedef struct {
+    int32_t tile[3];
+    int32_t sort_interval;
+    int32_t drift;
+    int32_t block;
+    int32_t use_graph;
+    int32_t reserved;
+} pic_tuning;
+
+typedef struct {
+    int32_t abi_version; /* PIC_ABI_VERSION */
+    int32_t shape_order; /* B-spline order 1, 2 or 3 (Table 3 "interpolation level") */
+    pic_grid grid;
+    int32_t n_species;   /* must be 1 */
+    int32_t track_ids;   /* 1: keep a per-particle int32 id through sorts */
+    const pic_species *species;
+    pic_laser laser;
+    pic_window window;
+    uint64_t seed;
+    int64_t capacity;    /* particle slots (0 = 1.25x the first load + injection room) */
+    pic_tuning tuning;
+    pic_alloc_fn alloc;  /* NULL: cudaMalloc */
+    pic_free_fn free;
+    void *alloc_ctx;
+    void *stream;        /* cudaStream_t, borrowed; NULL = default stream */
+} pic_config;
+
+typedef struct {
+    int64_t step;
+    double time;
+    int64_t shifts;        /* moving-window shifts so far */
+    double W_E, W_B;       /* 1/2 sum E^2 V, 1/2 sum B^2 V at integer time */
+    double W_kin;          /* V sum w m (gamma - 1), gamma from u^{n-1/2} */
+    double gauss_resid;    /* max|div E - (rho - rho_0)| / max|rho_0| */
+    int64_t n_particles;   /* live particles */
+    double imbalance;      /* max / mean particles per occupied tile (Sec. 3) */
+    int64_t slow_path;     /* particles outside their tile's staged region, last step */
+    int32_t status;        /* latched device status (PIC_OK or a PIC_E* code) */
+    int32_t reserved;
+} pic_diag;
+
+typedef struct pic_s pic_t;
+
+/* Validate `cfg`, allocate grid and state, zero the fields.  *out receives
+ * the handle.  Errors: PIC_EINVAL (Courant, order, dims not encodable in the
+ * packed cell index, unsupported species count), PIC_ENOMEM, PIC_ECUDA. */
+PIC_API int pic_create(const pic_config *cfg, pic_t **out);
+
+/* Batched form: n independent runs of equal dim and shape order advanced
+ * together, each kernel phase covering every run's tiles in one launch.
+ * The other calls address run 0 until pic_select_run chooses another. */
+PIC_API int pic_create_batch(const pic_config *cfgs, int32_t n, pic_t **out);
+PIC_API int pic_select_run(pic_t *h, int32_t run);
+PIC_API int32_t pic_num_runs(const pic_t *h);
+
+/* Append n particles of `species` (0) to the current run.  cell[dim][n]:
+ * cell index per axis in [0, n_a); off[dim][n]: FP32 offset in [0, 1) from
+ * the cell's lower vertex (Sec. 5.1); u[3][n]: gamma*beta; w[n]: weights
+ * (required iff per_particle_weight, else ignored and may be NULL).  Host
+ * pointers.  Particles are sorted into tiles before the next step.
+ * Errors: PIC_EINVAL (index out of range), PIC_EOVERFLOW (capacity), PIC_ESTATE
+ * (after the first step). */
+PIC_API int pic_load_particles(pic_t *h, int32_t species, int64_t n, const int32_t *cell, const float *off,
+                       const float *u, const float *w);
+
+/* Enqueue nsteps timesteps of every run on the handle's stream; returns
+ * without waiting.  Device-side conditions are latched (see pic_sync). */
+PIC_API int pic_step(pic_t *h, int32_t nsteps);
+
+/* Wait for the handle's stream and return the latched device status. */
+PIC_API int pic_sync(pic_t *h);
+
+/* Copy field `which` of the current run into dst (n_elems >= n0*n1*n2),
+ * ordered in the window frame (index 0 of the last axis = rear of the
+ * window).  on_device: dst is a device pointer (else host).  PIC_RHO is the
+ * current particles' charge density.  Synchronises the stream. */
+PIC_API int pic_read_fields(pic_t *h, int32_t which, float *dst, size_t n_elems, int32_t on_device);
+
+/* Overwrite field `which` (E or B components only) of the current run from
+ * src (window-frame order, n_elems = n0*n1*n2); on_device as above. */
+PIC_API int pic_write_fields(pic_t *h, int32_t which, const float *src, size_t n_elems, int32_t on_device);
+
+/* Copy the live particles of the current run to host arrays: cell[dim][cap],
+ * off[dim][cap], u[3][cap], w[cap], id[cap] (id only with track_ids; any
+ * pointer may be NULL to skip it).  Cell indices are in the window frame.
+ * *n receives the count; PIC_EOVERFLOW if it exceeds cap (nothing copied). */
+PIC_API int pic_read_particles(pic_t *h, int32_t species, int32_t *cell, float *off, float *u, float *w,
+                       int32_t *id, int64_t cap, int64_t *n);
+
+/* Compute diagnostics of the current run (synchronises the stream). */
+PIC_API int pic_diagnostics(pic_t *h, pic_diag *out);
+
+/* Phase timing with CUDA events recorded on the handle's stream around each
+ * phase of every step (steps then run without graph replay).
+ * pic_profile_begin(h, max_steps) arms it for up to max_steps steps;
+ * pic_profile_end(h, ms, n_phases, launches) synchronises and writes the
+ * summed milliseconds of each phase into ms[0..n_phases) in the order
+ * PIC_PH_* below, and the number of kernels the profiled steps launched into
+ * *launches. */
+#define PIC_PH_SORT 0
+#define PIC_PH_ZERO_J 1
+#define PIC_PH_PUSH 2
+#define PIC_PH_YEE_B1 3
+#define PIC_PH_YEE_E 4 /* includes the Mur save/apply */
+#define PIC_PH_YEE_B2 5
+#define PIC_PH_WINDOW 6 /* end-of-step bookkeeping, window shift and injection */
+#define PIC_NUM_PHASES 7
+PIC_API int pic_profile_begin(pic_t *h, int32_t max_steps);
+PIC_API int pic_profile_end(pic_t *h, double *ms, int32_t n_phases, int64_t *launches);
+
+/* Release everything (waits for the stream first).  NULL is ignored. */
+PIC_API void pic_destroy(pic_t *h);
+
+/* Static description of a status code. */
+PIC_API const char *pic_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIC_GB300_H */

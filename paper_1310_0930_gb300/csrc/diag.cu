@@ -1,0 +1,275 @@
+// diag.cu -- particle load / readback and diagnostics of one run: charge
+// density, energies, Gauss-law residual and the tile load imbalance
+// (max / mean particles per occupied tile, the paper's imbalance metric of
+// Sec. 3 taken over tiles instead of nodes).
+#include "common.cuh"
+#include "internal.h"
+
+namespace pic {
+
+namespace {
+
+__global__ void pack_kernel(const Run *__restrict__ run, long long base, long long n, int dim,
+                            const int32_t *__restrict__ cell, const float *__restrict__ off,
+                            const float *__restrict__ u, const float *__restrict__ w)
+{
+    const Run &r = *run;
+    RunState &s = *r.state;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const ParticleBuf pb = r.P[s.buf];
+    const long long o = base + i;
+    int c[3] = {0, 0, 0};
+    bool ok = true;
+    for (int a = 0; a < dim; ++a) {
+        c[a] = cell[(long long)a * n + i];
+        float f = off[(long long)a * n + i];
+        ok = ok && c[a] >= 0 && c[a] < r.n[a] && f >= 0.f && f < 1.f;
+        pb.off[a][o] = f;
+    }
+    if (ok && r.open_last) {
+        // the caller gives window-frame indices; storage is the ring
+        int st = c[dim - 1] + s.origin;
+        c[dim - 1] = st >= r.n[dim - 1] ? st - r.n[dim - 1] : st;
+    }
+    if (!ok) atomicOr(&s.status, kStatusBadIndex);
+    pb.cell[o] = ok ? pack_cell(r, c[0], c[1], dim == 3 ? c[2] : 0) : -1;
+    pb.u[0][o] = u[i];
+    pb.u[1][o] = u[n + i];
+    pb.u[2][o] = u[2 * n + i];
+    if (pb.w) pb.w[o] = w ? w[i] : r.w_const;
+    if (pb.id) pb.id[o] = (int32_t)o;
+}
+
+__global__ void set_count_kernel(const Run *__restrict__ run, long long n_total, int sorted)
+{
+    RunState &s = *run->state;
+    s.n_total = n_total;
+    if (sorted) s.n_sorted = n_total;
+}
+
+__device__ __forceinline__ bool live(const Run &r, const RunState &s, int32_t c, int &cx, int &cy, int &cz)
+{
+    if (c < 0) return false;
+    unpack_cell(r, c, cx, cy, cz);
+    if (r.open_last) {
+        int pl = phys_last(r, s, r.dim == 3 ? cz : cy);
+        if (pl < r.margin || pl >= r.n[r.dim - 1] - r.margin) return false;
+    }
+    return true;
+}
+
+template <int DIM, int P>
+__global__ void charge_kernel(const Run *__restrict__ run, float *__restrict__ rho, long long cap)
+{
+    const Run &r = *run;
+    const RunState &s = *r.state;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.n_total) return;
+    const ParticleBuf pb = r.P[s.buf];
+    int c[3];
+    if (!live(r, s, pb.cell[i], c[0], c[1], c[2])) return;
+    int base[3] = {0, 0, 0};
+    float w[3][P + 1] = {};
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) Shape<P>::node(c[a], pb.off[a][i], base[a], w[a]);
+    const float qw = r.q * (pb.w ? pb.w[i] : r.w_const);
+    const int n0 = r.n[0], n1 = r.n[1], n2 = DIM == 3 ? r.n[2] : 1;
+#pragma unroll
+    for (int qz = 0; qz < (DIM == 3 ? P + 1 : 1); ++qz)
+#pragma unroll
+        for (int qy = 0; qy <= P; ++qy)
+#pragma unroll
+            for (int qx = 0; qx <= P; ++qx) {
+                float v = qw * w[0][qx] * w[1][qy] * (DIM == 3 ? w[2][qz] : 1.f);
+                int x = wrapi(base[0] + qx, n0), y = wrapi(base[1] + qy, n1);
+                int z = DIM == 3 ? wrapi(base[2] + qz, n2) : 0;
+                atomicAdd(rho + x + n0 * (y + n1 * z), v);
+            }
+}
+
+__device__ __forceinline__ unsigned long long warp_slot(unsigned long long *count, bool want)
+{
+    const unsigned act = __activemask();
+    const unsigned m = __ballot_sync(act, want);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(act) - 1;
+    unsigned long long base = 0;
+    if (lane == leader && m) base = atomicAdd(count, (unsigned long long)__popc(m));
+    base = __shfl_sync(act, base, leader);
+    return base + __popc(m & ((1u << lane) - 1));
+}
+
+__global__ void unpack_kernel(const Run *__restrict__ run, long long cap, int dim, int32_t *cell, float *off,
+                              float *u, float *w, int32_t *id, unsigned long long *count)
+{
+    const Run &r = *run;
+    const RunState &s = *r.state;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const ParticleBuf pb = r.P[s.buf];
+    int c[3] = {0, 0, 0};
+    const bool ok = i < s.n_total && live(r, s, pb.cell[i], c[0], c[1], c[2]);
+    const unsigned long long o = warp_slot(count, ok);
+    if (!ok || (long long)o >= cap) return;
+    if (r.open_last) c[dim - 1] = phys_last(r, s, c[dim - 1]);
+    for (int a = 0; a < dim; ++a) {
+        if (cell) cell[(long long)a * cap + o] = c[a];
+        if (off) off[(long long)a * cap + o] = pb.off[a][i];
+    }
+    if (u) {
+        u[o] = pb.u[0][i];
+        u[cap + o] = pb.u[1][i];
+        u[2 * cap + o] = pb.u[2][i];
+    }
+    if (w) w[o] = pb.w ? pb.w[i] : r.w_const;
+    if (id) id[o] = pb.id ? pb.id[i] : -1;
+}
+
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (wid == 0) {
+        t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    }
+    __syncthreads();
+    return t;  // valid in thread 0
+}
+
+__global__ void field_energy_kernel(const Run *__restrict__ run, double *out)
+{
+    const Run &r = *run;
+    __shared__ double sh[32];
+    double e2 = 0.0, b2 = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < r.ncell; i += gridDim.x * blockDim.x)
+        for (int c = 0; c < 3; ++c) {
+            double e = r.E[c][i], b = r.B[c][i];
+            e2 += e * e;
+            b2 += b * b;
+        }
+    double te = block_sum(e2, sh);
+    double tb = block_sum(b2, sh);
+    if (threadIdx.x == 0) {
+        atomicAdd(out + 0, te);
+        atomicAdd(out + 1, tb);
+    }
+}
+
+__global__ void kinetic_kernel(const Run *__restrict__ run, double *out)
+{
+    const Run &r = *run;
+    const RunState &s = *r.state;
+    __shared__ double sh[32];
+    const ParticleBuf pb = r.P[s.buf];
+    double k = 0.0, cnt = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < s.n_total;
+         i += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        if (!live(r, s, pb.cell[i], c[0], c[1], c[2])) continue;
+        double ux = pb.u[0][i], uy = pb.u[1][i], uz = pb.u[2][i];
+        double w = pb.w ? pb.w[i] : r.w_const;
+        k += w * (double)r.m * (sqrt(1.0 + ux * ux + uy * uy + uz * uz) - 1.0);
+        cnt += 1.0;
+    }
+    double tk = block_sum(k, sh);
+    double tc = block_sum(cnt, sh);
+    if (threadIdx.x == 0) {
+        atomicAdd(out + 2, tk);
+        atomicAdd(out + 3, tc);
+    }
+}
+
+template <int DIM>
+__global__ void gauss_kernel(const Run *__restrict__ run, const float *__restrict__ rho, unsigned *umax)
+{
+    const Run &r = *run;
+    const int n0 = r.n[0], n1 = r.n[1], n2 = DIM == 3 ? r.n[2] : 1;
+    float mr = 0.f, m0 = 0.f;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < r.ncell; idx += gridDim.x * blockDim.x) {
+        int i = idx % n0, j = (idx / n0) % n1, k = DIM == 3 ? idx / (n0 * n1) : 0;
+        int mx = (i == 0 ? n0 - 1 : i - 1) + n0 * (j + n1 * k);
+        int my = i + n0 * ((j == 0 ? n1 - 1 : j - 1) + n1 * k);
+        double dv = ((double)r.E[0][idx] - r.E[0][mx]) / r.d[0] + ((double)r.E[1][idx] - r.E[1][my]) / r.d[1];
+        if (DIM == 3) {
+            int mz = i + n0 * (j + n1 * (k == 0 ? n2 - 1 : k - 1));
+            dv += ((double)r.E[2][idx] - r.E[2][mz]) / r.d[2];
+        }
+        double res = dv - ((double)rho[idx] - (double)r.rho0[idx]);
+        mr = fmaxf(mr, (float)fabs(res));
+        m0 = fmaxf(m0, fabsf(r.rho0[idx]));
+    }
+    atomicMax(umax + 0, __float_as_uint(mr));
+    atomicMax(umax + 1, __float_as_uint(m0));
+}
+
+__global__ void tiles_kernel(const Run *__restrict__ run, unsigned *umax)
+{
+    const Run &r = *run;
+    unsigned mx = 0, occ = 0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < r.ntiles; t += gridDim.x * blockDim.x) {
+        unsigned c = (unsigned)(r.tile_off[t + 1] - r.tile_off[t]);
+        mx = c > mx ? c : mx;
+        occ += c > 0;
+    }
+    atomicMax(umax + 2, mx);
+    atomicAdd(umax + 3, occ);
+}
+
+}  // namespace
+
+cudaError_t launch_pack(const Run *run, long long base, long long n, int dim, const int32_t *cell,
+                        const float *off, const float *u, const float *w, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    pack_kernel<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, st>>>(run, base, n, dim, cell, off, u, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_count(const Run *run, long long n_total, int sorted, cudaStream_t st)
+{
+    set_count_kernel<<<1, 1, 0, st>>>(run, n_total, sorted);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_charge(int dim, int order, const Run *run, float *rho, long long cap, cudaStream_t st)
+{
+    unsigned g = (unsigned)((cap + kBlock - 1) / kBlock);
+    if (g == 0) return cudaSuccess;
+    if (dim == 2) {
+        if (order == 1) charge_kernel<2, 1><<<g, kBlock, 0, st>>>(run, rho, cap);
+        else if (order == 2) charge_kernel<2, 2><<<g, kBlock, 0, st>>>(run, rho, cap);
+        else charge_kernel<2, 3><<<g, kBlock, 0, st>>>(run, rho, cap);
+    } else {
+        if (order == 1) charge_kernel<3, 1><<<g, kBlock, 0, st>>>(run, rho, cap);
+        else if (order == 2) charge_kernel<3, 2><<<g, kBlock, 0, st>>>(run, rho, cap);
+        else charge_kernel<3, 3><<<g, kBlock, 0, st>>>(run, rho, cap);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const Run *run, long long cap, int dim, int32_t *cell, float *off, float *u, float *w,
+                          int32_t *id, unsigned long long *count, cudaStream_t st)
+{
+    unsigned g = (unsigned)((cap + kBlock - 1) / kBlock);
+    if (g == 0) return cudaSuccess;
+    unpack_kernel<<<g, kBlock, 0, st>>>(run, cap, dim, cell, off, u, w, id, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diag(int dim, const Run *run, const float *rho, long long cap, double *out, cudaStream_t st)
+{
+    unsigned *umax = reinterpret_cast<unsigned *>(out + 8);
+    field_energy_kernel<<<1024, kBlock, 0, st>>>(run, out);
+    kinetic_kernel<<<1024, kBlock, 0, st>>>(run, out);
+    if (dim == 3) gauss_kernel<3><<<1024, kBlock, 0, st>>>(run, rho, umax);
+    else gauss_kernel<2><<<1024, kBlock, 0, st>>>(run, rho, umax);
+    tiles_kernel<<<256, kBlock, 0, st>>>(run, umax);
+    (void)cap;
+    return cudaGetLastError();
+}
+
+}  // namespace pic

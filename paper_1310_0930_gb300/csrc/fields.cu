@@ -1,0 +1,395 @@
+// fields.cu -- Yee FDTD update (Sec. 2, Sec. 3 "local field solver"), the
+// open last axis (first-order Mur fields), the laser antenna (one-way plane
+// source) and the moving window (Sec. 2) on device-resident state.
+//
+// Per timestep: B -= (dt/2) curl E (forward differences), E += dt (curl B -
+// J) (backward differences), B -= (dt/2) curl E.  Cell-parallel, one thread
+// per cell and all three components, neighbours wrapped periodically.  On an
+// open last axis the storage is a ring: physical index = storage - origin.
+#include "common.cuh"
+#include "internal.h"
+
+namespace pic {
+
+namespace {
+
+__device__ __forceinline__ int seg_run(const Seg &s, int b)
+{
+    int lo = 0, hi = s.nruns - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (s.start[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ bool laser_active(const Run &r, const RunState &s)
+{
+    return r.laser_on && s.shifts == 0;
+}
+
+// Incident antenna field (double precision; a few thousand values per step).
+__device__ double laser_field(const Run &r, double r2, double xi)
+{
+    double dx = xi - r.t_peak;
+    double env = exp(-2.0 * 0.69314718055994530942 * dx * dx / (r.fwhm * r.fwhm));
+    return r.a0 * exp(-r2 / (r.waist * r.waist)) * env * cos(r.omega0 * dx);
+}
+
+// squared distance from the box axis of E_pol's transverse location
+__device__ double laser_r2(const Run &r, int i, int j)
+{
+    const int last = r.dim - 1;
+    double r2 = 0.0;
+    int idx[2] = {i, j};
+    for (int a = 0; a < last; ++a) {
+        double off = (a == r.laser_pol) ? 0.5 : 0.0;
+        double pos = ((double)idx[a] + off) * r.d[a];
+        double ctr = 0.5 * r.n[a] * (double)r.d[a];
+        r2 += (pos - ctr) * (pos - ctr);
+    }
+    return r2;
+}
+
+template <int DIM>
+__global__ void yee_b_kernel(const Run *__restrict__ runs, Seg seg, int second)
+{
+    const int ri = seg_run(seg, blockIdx.x);
+    const Run &r = runs[ri];
+    const int idx = (blockIdx.x - seg.start[ri]) * blockDim.x + threadIdx.x;
+    if (idx >= r.ncell) return;
+    const RunState &s = *r.state;
+    const int n0 = r.n[0], n1 = r.n[1];
+    const int i = idx % n0, j = (idx / n0) % n1, k = DIM == 3 ? idx / (n0 * n1) : 0;
+    const int cx = (i + 1 == n0 ? 0 : i + 1) + n0 * (j + n1 * k);
+    const int cy = i + n0 * ((j + 1 == n1 ? 0 : j + 1) + n1 * k);
+    const float h = 0.5f * r.dt;
+    const float *Ex = r.E[0], *Ey = r.E[1], *Ez = r.E[2];
+    float *Bx = r.B[0], *By = r.B[1], *Bz = r.B[2];
+    const float ex = Ex[idx], ey = Ey[idx], ez = Ez[idx];
+    const float dEz_dy = (Ez[cy] - ez) * r.inv_d[1], dEz_dx = (Ez[cx] - ez) * r.inv_d[0];
+    const float dEy_dx = (Ey[cx] - ey) * r.inv_d[0], dEx_dy = (Ex[cy] - ex) * r.inv_d[1];
+    float dEy_dz = 0.f, dEx_dz = 0.f;
+    if (DIM == 3) {
+        const int n2 = r.n[2];
+        const int cz = i + n0 * (j + n1 * (k + 1 == n2 ? 0 : k + 1));
+        dEy_dz = (Ey[cz] - ey) * r.inv_d[2];
+        dEx_dz = (Ex[cz] - ex) * r.inv_d[2];
+    }
+    const int nl = r.n[DIM - 1];
+    const int il = phys_last(r, s, DIM == 3 ? k : j);
+    const bool outside = r.open_last && il == nl - 1;  // half-integer positions beyond the end
+    if (DIM == 3) {
+        if (!outside) {
+            Bx[idx] -= h * (dEz_dy - dEy_dz);
+            By[idx] -= h * (dEx_dz - dEz_dx);
+        }
+        Bz[idx] -= h * (dEy_dx - dEx_dy);
+    } else {
+        if (!outside) {
+            Bx[idx] -= h * dEz_dy;
+            Bz[idx] -= h * (dEy_dx - dEx_dy);
+        }
+        By[idx] -= h * (-dEz_dx);
+    }
+    if (laser_active(r, s) && il == r.laser_plane - 1) {
+        // B_b one plane behind saw the total E_pol: remove the incident part.
+        int bcomp;
+        double sgn;
+        if (DIM == 3) {
+            bcomp = r.laser_pol == 0 ? 1 : 0;
+            sgn = r.laser_pol == 0 ? 1.0 : -1.0;
+        } else {
+            bcomp = 2;
+            sgn = -1.0;
+        }
+        const double t = s.time + (second ? (double)r.dt : 0.0);
+        const double e = laser_field(r, laser_r2(r, i, j), t);
+        r.B[bcomp][idx] += (float)(sgn * (double)h * (double)r.inv_d[DIM - 1] * e);
+    }
+}
+
+template <int DIM>
+__global__ void yee_e_kernel(const Run *__restrict__ runs, Seg seg)
+{
+    const int ri = seg_run(seg, blockIdx.x);
+    const Run &r = runs[ri];
+    const int idx = (blockIdx.x - seg.start[ri]) * blockDim.x + threadIdx.x;
+    if (idx >= r.ncell) return;
+    const RunState &s = *r.state;
+    const int n0 = r.n[0], n1 = r.n[1];
+    const int i = idx % n0, j = (idx / n0) % n1, k = DIM == 3 ? idx / (n0 * n1) : 0;
+    const int mx = (i == 0 ? n0 - 1 : i - 1) + n0 * (j + n1 * k);
+    const int my = i + n0 * ((j == 0 ? n1 - 1 : j - 1) + n1 * k);
+    const float dt = r.dt;
+    float *Ex = r.E[0], *Ey = r.E[1], *Ez = r.E[2];
+    const float *Bx = r.B[0], *By = r.B[1], *Bz = r.B[2];
+    const float bx = Bx[idx], by = By[idx], bz = Bz[idx];
+    const float dBz_dy = (bz - Bz[my]) * r.inv_d[1], dBz_dx = (bz - Bz[mx]) * r.inv_d[0];
+    const float dBy_dx = (by - By[mx]) * r.inv_d[0], dBx_dy = (bx - Bx[my]) * r.inv_d[1];
+    float dBy_dz = 0.f, dBx_dz = 0.f;
+    if (DIM == 3) {
+        const int n2 = r.n[2];
+        const int mz = i + n0 * (j + n1 * (k == 0 ? n2 - 1 : k - 1));
+        dBy_dz = (by - By[mz]) * r.inv_d[2];
+        dBx_dz = (bx - Bx[mz]) * r.inv_d[2];
+    }
+    float nv[3];
+    nv[0] = Ex[idx] + dt * (dBz_dy - dBy_dz - r.J[0][idx]);
+    nv[1] = Ey[idx] + dt * (dBx_dz - dBz_dx - r.J[1][idx]);
+    nv[2] = Ez[idx] + dt * (dBy_dx - dBx_dy - r.J[2][idx]);
+    const int nl = r.n[DIM - 1];
+    const int il = phys_last(r, s, DIM == 3 ? k : j);
+    if (r.open_last) {
+        const int t0 = 0, t1 = DIM == 3 ? 1 : 2, nrm = DIM == 3 ? 2 : 1;
+        if (il == 0 || il == nl - 1) {  // tangential: set by the Mur update afterwards
+            nv[t0] = Ex[idx];
+            nv[t1] = t1 == 1 ? Ey[idx] : Ez[idx];
+        }
+        if (il == nl - 1) nv[nrm] = 0.f;
+    }
+    if (laser_active(r, s) && il == r.laser_plane) {
+        // E_pol on the plane saw the scattered B_b one plane behind: add the incident B.
+        const double th = s.time + 0.5 * (double)dt;
+        const double e = laser_field(r, laser_r2(r, i, j), th + 0.5 * (double)r.d[DIM - 1]);
+        nv[r.laser_pol] += (float)((double)dt * (double)r.inv_d[DIM - 1] * e);
+    }
+    Ex[idx] = nv[0];
+    Ey[idx] = nv[1];
+    Ez[idx] = nv[2];
+}
+
+__global__ void zero_j_kernel(const Run *__restrict__ runs, Seg seg)
+{
+    const int ri = seg_run(seg, blockIdx.x);
+    const Run &r = runs[ri];
+    const int idx = (blockIdx.x - seg.start[ri]) * blockDim.x + threadIdx.x;
+    if (idx >= r.ncell) return;
+    r.J[0][idx] = 0.f;
+    r.J[1][idx] = 0.f;
+    r.J[2][idx] = 0.f;
+}
+
+// storage offset of physical plane `pl` (last axis) and transverse position q
+__device__ __forceinline__ int plane_index(const Run &r, const RunState &s, int pl, int q)
+{
+    const int nl = r.n[r.dim - 1];
+    const int plane = r.ncell / nl;
+    int st = pl + s.origin;
+    st = st >= nl ? st - nl : st;
+    return q + plane * st;
+}
+
+// Mur: keep E^n of the two tangential components on physical planes 0, 1,
+// nl-2, nl-1 before the E update.
+__global__ void mur_save_kernel(const Run *__restrict__ runs, Seg seg)
+{
+    const int ri = seg_run(seg, blockIdx.x);
+    const Run &r = runs[ri];
+    if (!r.open_last) return;
+    const int nl = r.n[r.dim - 1];
+    const int plane = r.ncell / nl;
+    const int q = (blockIdx.x - seg.start[ri]) * blockDim.x + threadIdx.x;
+    if (q >= plane) return;
+    const RunState &s = *r.state;
+    const int pls[4] = {0, 1, nl - 2, nl - 1};
+    const float *F[2] = {r.E[0], r.dim == 3 ? r.E[1] : r.E[2]};
+    for (int t = 0; t < 2; ++t)
+        for (int p = 0; p < 4; ++p) r.mur[(t * 4 + p) * plane + q] = F[t][plane_index(r, s, pls[p], q)];
+}
+
+// first-order Mur at normal incidence:
+// F_0^{n+1} = F_1^n + (dt - d)/(dt + d) (F_1^{n+1} - F_0^n), likewise at the far end.
+__global__ void mur_apply_kernel(const Run *__restrict__ runs, Seg seg)
+{
+    const int ri = seg_run(seg, blockIdx.x);
+    const Run &r = runs[ri];
+    if (!r.open_last) return;
+    const int nl = r.n[r.dim - 1];
+    const int plane = r.ncell / nl;
+    const int q = (blockIdx.x - seg.start[ri]) * blockDim.x + threadIdx.x;
+    if (q >= plane) return;
+    const RunState &s = *r.state;
+    const float dl = r.d[r.dim - 1];
+    const float coef = (r.dt - dl) / (r.dt + dl);
+    float *F[2] = {r.E[0], r.dim == 3 ? r.E[1] : r.E[2]};
+    for (int t = 0; t < 2; ++t) {
+        const float o0 = r.mur[(t * 4 + 0) * plane + q], o1 = r.mur[(t * 4 + 1) * plane + q];
+        const float om1 = r.mur[(t * 4 + 2) * plane + q], om = r.mur[(t * 4 + 3) * plane + q];
+        const int c0 = plane_index(r, s, 0, q), c1 = plane_index(r, s, 1, q);
+        const int cm = plane_index(r, s, nl - 1, q), cm1 = plane_index(r, s, nl - 2, q);
+        F[t][c0] = o1 + coef * (F[t][c1] - o0);
+        F[t][cm] = om1 + coef * (F[t][cm1] - om);
+    }
+}
+
+// time advance and the moving-window decision (one thread per run)
+__global__ void end_step_kernel(const Run *__restrict__ runs, int nruns)
+{
+    const int ri = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ri >= nruns) return;
+    const Run &r = runs[ri];
+    RunState &s = *r.state;
+    s.time += (double)r.dt;
+    s.step += 1;
+    s.slow_last = s.slow;
+    s.slow = 0;
+    s.shift_pending = 0;
+    if (r.window_on && s.time >= r.window_t0) {
+        const double travelled = r.window_v * (s.time - r.window_t0);
+        if (travelled >= (double)(s.shifts + 1) * (double)r.d[r.dim - 1]) {
+            const int nl = r.n[r.dim - 1];
+            s.shifts += 1;
+            s.origin = s.origin + 1 == nl ? 0 : s.origin + 1;
+            s.shift_pending = 1;
+        }
+    }
+}
+
+// zero E and B on the plane that became the new front (storage origin-1)
+__global__ void window_zero_kernel(const Run *__restrict__ runs, Seg seg)
+{
+    const int ri = seg_run(seg, blockIdx.x);
+    const Run &r = runs[ri];
+    const RunState &s = *r.state;
+    if (!s.shift_pending) return;
+    const int nl = r.n[r.dim - 1];
+    const int plane = r.ncell / nl;
+    const int q = (blockIdx.x - seg.start[ri]) * blockDim.x + threadIdx.x;
+    if (q >= plane) return;
+    const int idx = plane_index(r, s, nl - 1, q);
+    for (int c = 0; c < 3; ++c) {
+        r.E[c][idx] = 0.f;
+        r.B[c][idx] = 0.f;
+    }
+}
+
+__device__ double profile_density(const Run &r, double z)
+{
+    if (r.n_knots <= 0 || r.knots == nullptr) return r.density;
+    if (r.n_knots == 1) return r.knots[0];
+    double f = (z - r.z0) / (r.z1 - r.z0) * (r.n_knots - 1);
+    if (f <= 0.0) return r.knots[0];
+    if (f >= r.n_knots - 1) return r.knots[r.n_knots - 1];
+    int i = (int)floor(f);
+    double t = f - i;
+    return r.knots[i] * (1.0 - t) + r.knots[i + 1] * t;
+}
+
+// Inject one cold, regularly placed layer of cells at physical last-axis
+// index nl - margin - 1 (appended to the unsorted tail).
+__global__ void window_inject_kernel(const Run *__restrict__ runs, Seg seg)
+{
+    const int ri = seg_run(seg, blockIdx.x);
+    const Run &r = runs[ri];
+    const RunState &s = *r.state;
+    if (!s.shift_pending) return;
+    const int dim = r.dim, nl = r.n[dim - 1];
+    const int ncol = r.ncell / nl;
+    const int ppc_t = r.ppc[0] * r.ppc[1] * (dim == 3 ? r.ppc[2] : 1);
+    const long long count = (long long)ncol * ppc_t;
+    const long long q = (long long)(blockIdx.x - seg.start[ri]) * blockDim.x + threadIdx.x;
+    if (q >= count) return;
+    const long long base = s.n_total;
+    if (base + count > r.capacity) return;  // overflow is latched by the commit kernel
+    const int col = (int)(q / ppc_t);
+    int sub = (int)(q % ppc_t);
+    int m[3] = {0, 0, 0};
+    for (int a = 0; a < dim; ++a) {
+        m[a] = sub % r.ppc[a];
+        sub /= r.ppc[a];
+    }
+    int c[3] = {0, 0, 0};
+    c[0] = col % r.n[0];
+    if (dim == 3) c[1] = col / r.n[0];
+    const int kcell = nl - r.margin - 1;
+    int st = kcell + s.origin;
+    c[dim - 1] = st >= nl ? st - nl : st;
+    const ParticleBuf pb = r.P[s.buf];
+    const long long slot = base + q;
+    pb.cell[slot] = pack_cell(r, c[0], c[1], dim == 3 ? c[2] : 0);
+    float off_last = 0.f;
+    for (int a = 0; a < dim; ++a) {
+        float o = ((float)m[a] + 0.5f) / (float)r.ppc[a];
+        pb.off[a][slot] = o;
+        if (a == dim - 1) off_last = o;
+    }
+    pb.u[0][slot] = 0.f;
+    pb.u[1][slot] = 0.f;
+    pb.u[2][slot] = 0.f;
+    if (pb.w) {
+        const double zlab = ((double)kcell + (double)off_last + (double)s.shifts) * (double)r.d[dim - 1];
+        pb.w[slot] = (float)(profile_density(r, zlab) / ppc_t);
+    }
+    if (pb.id) pb.id[slot] = -1;
+}
+
+__global__ void window_commit_kernel(const Run *__restrict__ runs, int nruns)
+{
+    const int ri = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ri >= nruns) return;
+    const Run &r = runs[ri];
+    RunState &s = *r.state;
+    if (!s.shift_pending) return;
+    const int nl = r.n[r.dim - 1];
+    const long long count =
+        (long long)(r.ncell / nl) * r.ppc[0] * r.ppc[1] * (r.dim == 3 ? r.ppc[2] : 1);
+    if (s.n_total + count > r.capacity) s.status |= kStatusOverflow;
+    else s.n_total += count;
+    s.shift_pending = 0;
+}
+
+}  // namespace
+
+cudaError_t launch_zero_j(const Run *runs, Seg cells, cudaStream_t st)
+{
+    zero_j_kernel<<<cells.nblocks, kBlock, 0, st>>>(runs, cells);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_yee_b(int dim, const Run *runs, Seg cells, int second_half, cudaStream_t st)
+{
+    if (dim == 3) yee_b_kernel<3><<<cells.nblocks, kBlock, 0, st>>>(runs, cells, second_half);
+    else yee_b_kernel<2><<<cells.nblocks, kBlock, 0, st>>>(runs, cells, second_half);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_yee_e(int dim, const Run *runs, Seg cells, cudaStream_t st)
+{
+    if (dim == 3) yee_e_kernel<3><<<cells.nblocks, kBlock, 0, st>>>(runs, cells);
+    else yee_e_kernel<2><<<cells.nblocks, kBlock, 0, st>>>(runs, cells);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mur_save(const Run *runs, Seg planes, cudaStream_t st)
+{
+    mur_save_kernel<<<planes.nblocks, kBlock, 0, st>>>(runs, planes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mur_apply(const Run *runs, Seg planes, cudaStream_t st)
+{
+    mur_apply_kernel<<<planes.nblocks, kBlock, 0, st>>>(runs, planes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_end_step(const Run *runs, int nruns, cudaStream_t st)
+{
+    end_step_kernel<<<(nruns + 127) / 128, 128, 0, st>>>(runs, nruns);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_window(const Run *runs, Seg planes, Seg inject, cudaStream_t st)
+{
+    window_zero_kernel<<<planes.nblocks, kBlock, 0, st>>>(runs, planes);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    window_inject_kernel<<<inject.nblocks, kBlock, 0, st>>>(runs, inject);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    window_commit_kernel<<<(planes.nruns + 127) / 128, 128, 0, st>>>(runs, planes.nruns);
+    return cudaGetLastError();
+}
+
+}  // namespace pic

@@ -1,0 +1,52 @@
+// internal.h -- host-side launchers of the device kernels (not part of the
+// public C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace pic {
+
+struct Run;
+struct RunState;
+struct Item;
+
+// Segmented 1-D launches over several runs: block b belongs to the run r with
+// start[r] <= b < start[r+1]; runs are located by binary search.
+struct Seg {
+    int nruns;
+    const int *start;  // device array [nruns + 1]
+    int nblocks;
+};
+
+constexpr int kBlock = 256;
+
+size_t push_smem_bytes(int dim, int order, const int *tile, int drift);
+cudaError_t launch_push(int dim, int order, const Run *runs, const Item *items, int nitems, size_t smem,
+                        int block, int tail_block, cudaStream_t st);
+
+// fields.cu
+cudaError_t launch_zero_j(const Run *runs, Seg cells, cudaStream_t st);
+cudaError_t launch_yee_b(int dim, const Run *runs, Seg cells, int second_half, cudaStream_t st);
+cudaError_t launch_yee_e(int dim, const Run *runs, Seg cells, cudaStream_t st);
+cudaError_t launch_mur_save(const Run *runs, Seg planes, cudaStream_t st);
+cudaError_t launch_mur_apply(const Run *runs, Seg planes, cudaStream_t st);
+cudaError_t launch_end_step(const Run *runs, int nruns, cudaStream_t st);
+cudaError_t launch_window(const Run *runs, Seg planes, Seg inject, cudaStream_t st);
+
+// sort.cu
+cudaError_t launch_sort(const Run *runs, int nruns, Seg parts, int max_tiles, cudaStream_t st);
+
+// diag.cu
+cudaError_t launch_pack(const Run *run, long long base, long long n, int dim, const int32_t *cell,
+                        const float *off, const float *u, const float *w, cudaStream_t st);
+cudaError_t launch_set_count(const Run *run, long long n_total, int sorted, cudaStream_t st);
+cudaError_t launch_charge(int dim, int order, const Run *run, float *rho, long long cap, cudaStream_t st);
+cudaError_t launch_unpack(const Run *run, long long cap, int dim, int32_t *cell, float *off, float *u, float *w,
+                          int32_t *id, unsigned long long *count, cudaStream_t st);
+// out (16 doubles): [0] sum E^2, [1] sum B^2, [2] sum w m (gamma - 1), [3] live particles;
+// out+8 viewed as unsigned[4]: max|div E - (rho - rho0)| and max|rho0| (float bits),
+// max particles in a tile, occupied tiles.
+cudaError_t launch_diag(int dim, const Run *run, const float *rho, long long cap, double *out, cudaStream_t st);
+
+}  // namespace pic

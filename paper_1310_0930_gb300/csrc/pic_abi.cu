@@ -1,0 +1,844 @@
+// pic_abi.cu -- host side of the C ABI declared in include/pic.h.
+//
+// Owns the device state of one or more independent runs, validates
+// configurations, orders every device operation on the borrowed stream and
+// replays each kind of timestep (with / without the periodic tile sort) as a
+// captured CUDA graph.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pic.h"
+#include "common.cuh"
+#include "internal.h"
+
+using namespace pic;
+
+namespace {
+
+constexpr int kTail = 256;  // particles per tail work item
+
+struct HostRun {
+    pic_config cfg;
+    pic_species sp;
+    std::vector<double> knots;
+    Run r;
+    long long inject_per_shift = 0;
+    float *rho = nullptr;  // diagnostics scratch (charge density)
+};
+
+}  // namespace
+
+struct pic_s {
+    int nruns = 0, cur = 0, dim = 2, order = 2;
+    cudaStream_t stream = nullptr;
+    pic_alloc_fn alloc = nullptr;
+    pic_free_fn free = nullptr;
+    void *ctx = nullptr;
+    std::vector<HostRun> runs;
+    std::vector<void *> allocs;
+    Run *d_runs = nullptr;
+    RunState *d_states = nullptr;
+    Item *d_items = nullptr;
+    int n_items = 0;
+    int *d_seg = nullptr;  // 4 segment tables of nruns+1 ints
+    Seg seg_cells{}, seg_planes{}, seg_parts{}, seg_inject{};
+    size_t push_smem = 0;
+    int block = 256, sort_interval = 4, drift = 1, tile[3] = {16, 16, 1};
+    bool use_graph = true;
+    bool started = false, need_sort = true, any_open = false, any_window = false;
+    int since_sort = 0;
+    int max_tiles = 0;
+    double *d_diag = nullptr;
+    unsigned long long *d_count = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    // phase profiling: events[step][PIC_NUM_PHASES + 1]
+    std::vector<cudaEvent_t> prof_events;
+    int prof_max = 0, prof_steps = 0;
+    bool prof_on = false;
+    long long prof_launches = 0;  // kernels enqueued during profiled steps
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) { return e == cudaSuccess ? PIC_OK : PIC_ECUDA; }
+
+void *dev_alloc(pic_s *h, size_t bytes)
+{
+    bytes = (bytes + 255) & ~size_t(255);
+    if (bytes == 0) bytes = 256;
+    void *p = nullptr;
+    if (h->alloc) p = h->alloc(bytes, h->ctx);
+    else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+    if (p) h->allocs.push_back(p);
+    return p;
+}
+
+void dev_free(pic_s *h, void *p)
+{
+    if (!p) return;
+    for (size_t i = 0; i < h->allocs.size(); ++i)
+        if (h->allocs[i] == p) {
+            h->allocs.erase(h->allocs.begin() + i);
+            break;
+        }
+    if (h->free) h->free(p, h->ctx);
+    else cudaFree(p);
+}
+
+int bits_for(int n)
+{
+    int b = 1;
+    while ((1 << b) < n) ++b;
+    return b;
+}
+
+bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int ilog2(int v)
+{
+    int b = 0;
+    while ((1 << b) < v) ++b;
+    return b;
+}
+
+int validate(const pic_config *c)
+{
+    if (!c || c->abi_version != PIC_ABI_VERSION) return PIC_EINVAL;
+    const pic_grid &g = c->grid;
+    if (g.dim != 2 && g.dim != 3) return PIC_EINVAL;
+    if (c->shape_order < 1 || c->shape_order > 3) return PIC_EINVAL;
+    double s = 0.0;
+    long long ncell = 1;
+    int bits = 0;
+    for (int a = 0; a < g.dim; ++a) {
+        if (g.n[a] < 4 || !(g.d[a] > 0.0)) return PIC_EINVAL;
+        s += 1.0 / (g.d[a] * g.d[a]);
+        ncell *= g.n[a];
+        bits += bits_for(g.n[a]);
+    }
+    if (!(g.dt > 0.0) || g.dt * std::sqrt(s) >= 1.0) return PIC_EINVAL;  // Courant
+    if (bits > 31 || ncell > 0x7fffffffLL) return PIC_EINVAL;
+    if (g.bc_last != PIC_BC_PERIODIC && g.bc_last != PIC_BC_OPEN) return PIC_EINVAL;
+    const int nl = g.n[g.dim - 1];
+    const int margin = c->shape_order + 1;
+    if (g.bc_last == PIC_BC_OPEN && nl < 2 * margin + 4) return PIC_EINVAL;
+    if (c->n_species != 1 || !c->species) return PIC_EINVAL;
+    const pic_species &sp = *c->species;
+    if (!(sp.m > 0.0) || sp.q == 0.0) return PIC_EINVAL;
+    if (c->laser.enabled) {
+        const pic_laser &L = c->laser;
+        if (L.plane < 1 || L.plane > nl - 2) return PIC_EINVAL;
+        if (g.dim == 2 ? L.pol_axis != 0 : (L.pol_axis != 0 && L.pol_axis != 1)) return PIC_EINVAL;
+        if (!(L.waist > 0.0) || !(L.fwhm > 0.0)) return PIC_EINVAL;
+    }
+    if (c->window.enabled) {
+        if (g.bc_last != PIC_BC_OPEN || !(c->window.velocity > 0.0)) return PIC_EINVAL;
+        for (int a = 0; a < g.dim; ++a)
+            if (sp.ppc[a] < 1) return PIC_EINVAL;
+        if (sp.n_knots > 0 && (!sp.profile_knots || !sp.per_particle_weight)) return PIC_EINVAL;
+    }
+    const pic_tuning &t = c->tuning;
+    for (int a = 0; a < g.dim; ++a)
+        if (t.tile[a] != 0 && !pow2(t.tile[a])) return PIC_EINVAL;
+    if (t.drift < -1 || t.drift > 8) return PIC_EINVAL;
+    if (t.block != 0 && t.block != 64 && t.block != 128 && t.block != 256) return PIC_EINVAL;
+    if (t.sort_interval < 0) return PIC_EINVAL;
+    return PIC_OK;
+}
+
+int status_code(int bits)
+{
+    if (bits & kStatusOverflow) return PIC_EOVERFLOW;
+    if (bits & kStatusTimeout) return PIC_ETIMEOUT;
+    if (bits & kStatusBadIndex) return PIC_EINVAL;
+    return PIC_OK;
+}
+
+int upload_runs(pic_s *h)
+{
+    std::vector<Run> tmp(h->nruns);
+    for (int i = 0; i < h->nruns; ++i) tmp[i] = h->runs[i].r;
+    cudaError_t e = cudaMemcpyAsync(h->d_runs, tmp.data(), sizeof(Run) * h->nruns, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return cuda_fail(e);
+}
+
+int set_seg(pic_s *h, int which, Seg &seg, const std::vector<long long> &items_per_run)
+{
+    std::vector<int> start(h->nruns + 1, 0);
+    for (int i = 0; i < h->nruns; ++i)
+        start[i + 1] = start[i] + (int)((items_per_run[i] + kBlock - 1) / kBlock);
+    int *dst = h->d_seg + which * (h->nruns + 1);
+    cudaError_t e = cudaMemcpyAsync(dst, start.data(), sizeof(int) * (h->nruns + 1), cudaMemcpyHostToDevice,
+                                    h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    seg.nruns = h->nruns;
+    seg.start = dst;
+    seg.nblocks = start[h->nruns];
+    return cuda_fail(e);
+}
+
+// Allocate (or grow) the two particle buffers of run `hr` to `cap` slots,
+// keeping the first `keep` slots of the current buffer.
+int alloc_particles(pic_s *h, HostRun &hr, long long cap, long long keep, int cur_buf)
+{
+    Run &r = hr.r;
+    const int dim = r.dim;
+    const bool has_w = hr.sp.per_particle_weight != 0;
+    const bool has_id = hr.cfg.track_ids != 0;
+    ParticleBuf nb[2];
+    for (int b = 0; b < 2; ++b) {
+        std::memset(&nb[b], 0, sizeof(ParticleBuf));
+        nb[b].cell = (int32_t *)dev_alloc(h, sizeof(int32_t) * cap);
+        for (int a = 0; a < dim; ++a) nb[b].off[a] = (float *)dev_alloc(h, sizeof(float) * cap);
+        for (int a = 0; a < 3; ++a) nb[b].u[a] = (float *)dev_alloc(h, sizeof(float) * cap);
+        if (has_w) nb[b].w = (float *)dev_alloc(h, sizeof(float) * cap);
+        if (has_id) nb[b].id = (int32_t *)dev_alloc(h, sizeof(int32_t) * cap);
+        if (!nb[b].cell || !nb[b].u[2] || (has_w && !nb[b].w) || (has_id && !nb[b].id)) return PIC_ENOMEM;
+        for (int a = 0; a < dim; ++a)
+            if (!nb[b].off[a]) return PIC_ENOMEM;
+    }
+    if (keep > 0 && r.P[cur_buf].cell) {
+        const ParticleBuf &o = r.P[cur_buf];
+        ParticleBuf &n = nb[cur_buf];
+        cudaError_t e = cudaSuccess;
+        e = cudaMemcpyAsync(n.cell, o.cell, sizeof(int32_t) * keep, cudaMemcpyDeviceToDevice, h->stream);
+        for (int a = 0; a < dim && e == cudaSuccess; ++a)
+            e = cudaMemcpyAsync(n.off[a], o.off[a], sizeof(float) * keep, cudaMemcpyDeviceToDevice, h->stream);
+        for (int a = 0; a < 3 && e == cudaSuccess; ++a)
+            e = cudaMemcpyAsync(n.u[a], o.u[a], sizeof(float) * keep, cudaMemcpyDeviceToDevice, h->stream);
+        if (has_w && e == cudaSuccess)
+            e = cudaMemcpyAsync(n.w, o.w, sizeof(float) * keep, cudaMemcpyDeviceToDevice, h->stream);
+        if (has_id && e == cudaSuccess)
+            e = cudaMemcpyAsync(n.id, o.id, sizeof(int32_t) * keep, cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return PIC_ECUDA;
+    }
+    for (int b = 0; b < 2; ++b) {
+        ParticleBuf &o = r.P[b];
+        if (o.cell) {
+            dev_free(h, o.cell);
+            for (int a = 0; a < dim; ++a) dev_free(h, o.off[a]);
+            for (int a = 0; a < 3; ++a) dev_free(h, o.u[a]);
+            dev_free(h, o.w);
+            dev_free(h, o.id);
+        }
+        r.P[b] = nb[b];
+    }
+    r.capacity = cap;
+    return PIC_OK;
+}
+
+int read_state(pic_s *h, int run, RunState *out)
+{
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(out, h->d_states + run, sizeof(RunState), cudaMemcpyDeviceToHost);
+    return cuda_fail(e);
+}
+
+int build_items(pic_s *h)
+{
+    std::vector<Item> items;
+    int tail_blocks = 0;
+    for (int i = 0; i < h->nruns; ++i) {
+        const HostRun &hr = h->runs[i];
+        for (int t = 0; t < hr.r.ntiles; ++t) items.push_back(Item{i, 0, t, 0});
+        if (hr.inject_per_shift > 0) {
+            long long max_tail = (long long)(h->sort_interval + 1) * hr.inject_per_shift;
+            tail_blocks = (int)((max_tail + kTail - 1) / kTail);
+            for (int b = 0; b < tail_blocks; ++b) items.push_back(Item{i, 1, b, 0});
+        }
+    }
+    if (h->d_items) dev_free(h, h->d_items);
+    h->d_items = (Item *)dev_alloc(h, sizeof(Item) * (items.size() ? items.size() : 1));
+    if (!h->d_items) return PIC_ENOMEM;
+    h->n_items = (int)items.size();
+    cudaError_t e = cudaMemcpyAsync(h->d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice,
+                                    h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return cuda_fail(e);
+}
+
+int enqueue_step(pic_s *h, bool sort)
+{
+    cudaError_t e = cudaSuccess;
+    const Run *R = h->d_runs;
+    cudaStream_t st = h->stream;
+    cudaEvent_t *ev = nullptr;
+    if (h->prof_on && h->prof_steps < h->prof_max) ev = &h->prof_events[(size_t)h->prof_steps * (PIC_NUM_PHASES + 1)];
+    auto mark = [&](int ph) {
+        if (ev && e == cudaSuccess) e = cudaEventRecord(ev[ph], st);
+    };
+    mark(PIC_PH_SORT);
+    if (sort) e = launch_sort(R, h->nruns, h->seg_parts, h->max_tiles, st);
+    mark(PIC_PH_ZERO_J);
+    if (e == cudaSuccess) e = launch_zero_j(R, h->seg_cells, st);
+    mark(PIC_PH_PUSH);
+    if (e == cudaSuccess)
+        e = launch_push(h->dim, h->order, R, h->d_items, h->n_items, h->push_smem, h->block, kTail, st);
+    mark(PIC_PH_YEE_B1);
+    if (e == cudaSuccess) e = launch_yee_b(h->dim, R, h->seg_cells, 0, st);
+    mark(PIC_PH_YEE_E);
+    if (e == cudaSuccess && h->any_open) e = launch_mur_save(R, h->seg_planes, st);
+    if (e == cudaSuccess) e = launch_yee_e(h->dim, R, h->seg_cells, st);
+    if (e == cudaSuccess && h->any_open) e = launch_mur_apply(R, h->seg_planes, st);
+    mark(PIC_PH_YEE_B2);
+    if (e == cudaSuccess) e = launch_yee_b(h->dim, R, h->seg_cells, 1, st);
+    mark(PIC_PH_WINDOW);
+    if (e == cudaSuccess) e = launch_end_step(R, h->nruns, st);
+    if (e == cudaSuccess && h->any_window) e = launch_window(R, h->seg_planes, h->seg_inject, st);
+    mark(PIC_NUM_PHASES);
+    if (ev) {
+        h->prof_steps += 1;
+        h->prof_launches += (sort ? 5 : 0) + 6 + (h->any_open ? 2 : 0) + (h->any_window ? 3 : 0);
+    }
+    return cuda_fail(e);
+}
+
+int first_step_setup(pic_s *h)
+{
+    std::vector<long long> parts(h->nruns), inj(h->nruns);
+    for (int i = 0; i < h->nruns; ++i) {
+        HostRun &hr = h->runs[i];
+        if (!hr.r.P[0].cell) {  // never loaded: give it the injection room only
+            long long cap = (long long)(h->sort_interval + 2) * hr.inject_per_shift + 4096;
+            int rc = alloc_particles(h, hr, cap, 0, 0);
+            if (rc) return rc;
+        }
+        parts[i] = hr.r.capacity;
+        inj[i] = hr.inject_per_shift;
+    }
+    int rc = upload_runs(h);
+    if (!rc) rc = set_seg(h, 2, h->seg_parts, parts);
+    if (!rc) rc = set_seg(h, 3, h->seg_inject, inj);
+    if (!rc) rc = build_items(h);
+    if (rc) return rc;
+    // the initial electron charge is the neutralising background (rho_0)
+    for (int i = 0; i < h->nruns; ++i) {
+        HostRun &hr = h->runs[i];
+        cudaError_t e = cudaMemsetAsync(hr.r.rho0, 0, sizeof(float) * hr.r.ncell, h->stream);
+        if (e == cudaSuccess) e = launch_charge(h->dim, h->order, h->d_runs + i, hr.r.rho0, hr.r.capacity, h->stream);
+        if (e != cudaSuccess) return PIC_ECUDA;
+    }
+    // sets the push kernel's shared-memory limit outside any graph capture
+    cudaError_t e = launch_push(h->dim, h->order, h->d_runs, h->d_items, 0, h->push_smem, h->block, kTail, h->stream);
+    if (e != cudaSuccess) return PIC_ECUDA;
+    h->started = true;
+    return PIC_OK;
+}
+
+int init_run(pic_s *h, HostRun &hr, int idx)
+{
+    const pic_config &c = hr.cfg;
+    Run &r = hr.r;
+    std::memset(&r, 0, sizeof(Run));
+    r.dim = c.grid.dim;
+    r.order = c.shape_order;
+    long long ncell = 1;
+    for (int a = 0; a < 3; ++a) {
+        r.n[a] = a < r.dim ? c.grid.n[a] : 1;
+        r.d[a] = a < r.dim ? (float)c.grid.d[a] : 1.f;
+        r.inv_d[a] = (float)(1.0 / (a < r.dim ? c.grid.d[a] : 1.0));
+        r.dt_over_d[a] = (float)(c.grid.dt / (a < r.dim ? c.grid.d[a] : 1.0));
+        r.bits[a] = a < r.dim ? bits_for(r.n[a]) : 0;
+        int T = a < r.dim ? h->tile[a] : 1;
+        r.tlog[a] = ilog2(T);
+        r.nt[a] = a < r.dim ? (r.n[a] + T - 1) / T : 1;
+        ncell *= r.n[a];
+    }
+    r.ncell = (int)ncell;
+    r.ntiles = r.nt[0] * r.nt[1] * r.nt[2];
+    r.dt = (float)c.grid.dt;
+    r.q = (float)hr.sp.q;
+    r.m = (float)hr.sp.m;
+    r.qm_half_dt = (float)(0.5 * hr.sp.q / hr.sp.m * c.grid.dt);
+    r.w_const = (float)hr.sp.w_const;
+    r.open_last = c.grid.bc_last == PIC_BC_OPEN;
+    r.margin = r.open_last ? c.shape_order + 1 : 0;
+    r.drift = h->drift;
+    const int nl = r.n[r.dim - 1];
+    const int plane = (int)(ncell / nl);
+    for (int a = 0; a < 3; ++a) {
+        r.E[a] = (float *)dev_alloc(h, sizeof(float) * ncell);
+        r.B[a] = (float *)dev_alloc(h, sizeof(float) * ncell);
+        r.J[a] = (float *)dev_alloc(h, sizeof(float) * ncell);
+        if (!r.E[a] || !r.B[a] || !r.J[a]) return PIC_ENOMEM;
+    }
+    r.rho0 = (float *)dev_alloc(h, sizeof(float) * ncell);
+    hr.rho = (float *)dev_alloc(h, sizeof(float) * ncell);
+    r.mur = (float *)dev_alloc(h, sizeof(float) * 8 * plane);
+    r.tile_off = (int32_t *)dev_alloc(h, sizeof(int32_t) * (r.ntiles + 1));
+    r.tile_cnt = (int32_t *)dev_alloc(h, sizeof(int32_t) * (r.ntiles + 1));
+    if (!r.rho0 || !hr.rho || !r.mur || !r.tile_off || !r.tile_cnt) return PIC_ENOMEM;
+    cudaError_t e = cudaSuccess;
+    for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+        e = cudaMemsetAsync(r.E[a], 0, sizeof(float) * ncell, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(r.B[a], 0, sizeof(float) * ncell, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(r.J[a], 0, sizeof(float) * ncell, h->stream);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(r.rho0, 0, sizeof(float) * ncell, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r.mur, 0, sizeof(float) * 8 * plane, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r.tile_off, 0, sizeof(int32_t) * (r.ntiles + 1), h->stream);
+    if (e != cudaSuccess) return PIC_ECUDA;
+    const pic_laser &L = c.laser;
+    r.laser_on = L.enabled;
+    r.laser_pol = L.pol_axis;
+    r.laser_plane = L.plane;
+    r.a0 = L.a0;
+    r.omega0 = L.omega0;
+    r.waist = L.waist;
+    r.fwhm = L.fwhm;
+    r.t_peak = L.t_peak;
+    r.window_on = c.window.enabled;
+    r.window_v = c.window.velocity;
+    r.window_t0 = c.window.t_start;
+    for (int a = 0; a < 3; ++a) r.ppc[a] = a < r.dim ? hr.sp.ppc[a] : 1;
+    r.density = hr.sp.density;
+    r.n_knots = hr.sp.n_knots;
+    r.z0 = hr.sp.profile_z0;
+    r.z1 = hr.sp.profile_z1;
+    if (hr.sp.n_knots > 0 && hr.sp.profile_knots) {
+        hr.knots.assign(hr.sp.profile_knots, hr.sp.profile_knots + hr.sp.n_knots);
+        double *dk = (double *)dev_alloc(h, sizeof(double) * hr.sp.n_knots);
+        if (!dk) return PIC_ENOMEM;
+        e = cudaMemcpyAsync(dk, hr.knots.data(), sizeof(double) * hr.sp.n_knots, cudaMemcpyHostToDevice, h->stream);
+        if (e != cudaSuccess) return PIC_ECUDA;
+        r.knots = dk;
+    }
+    hr.inject_per_shift = 0;
+    if (r.window_on) {
+        long long ppc_t = (long long)r.ppc[0] * r.ppc[1] * (r.dim == 3 ? r.ppc[2] : 1);
+        hr.inject_per_shift = (long long)plane * ppc_t;
+    }
+    r.state = h->d_states + idx;
+    return PIC_OK;
+}
+
+int create_common(const pic_config *cfgs, int n, pic_t **out)
+{
+    if (!out || !cfgs || n < 1) return PIC_EINVAL;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        int rc = validate(&cfgs[i]);
+        if (rc) return rc;
+        if (cfgs[i].grid.dim != cfgs[0].grid.dim || cfgs[i].shape_order != cfgs[0].shape_order) return PIC_EINVAL;
+    }
+    pic_s *h = new (std::nothrow) pic_s();
+    if (!h) return PIC_ENOMEM;
+    const pic_config &c0 = cfgs[0];
+    h->nruns = n;
+    h->dim = c0.grid.dim;
+    h->order = c0.shape_order;
+    h->stream = (cudaStream_t)c0.stream;
+    h->alloc = c0.alloc;
+    h->free = c0.free;
+    h->ctx = c0.alloc_ctx;
+    const pic_tuning &t = c0.tuning;
+    for (int a = 0; a < 3; ++a) {
+        int def = h->dim == 3 ? 8 : 16;
+        h->tile[a] = a < h->dim ? (t.tile[a] ? t.tile[a] : def) : 1;
+    }
+    h->drift = t.drift >= 0 ? t.drift : (h->dim == 3 ? 1 : 2);
+    h->block = t.block ? t.block : 256;
+    h->sort_interval = t.sort_interval ? t.sort_interval : 4;
+    h->use_graph = t.use_graph != 0 && h->stream != nullptr;
+    h->push_smem = push_smem_bytes(h->dim, h->order, h->tile, h->drift);
+    int dev = 0;
+    int max_smem = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        delete h;
+        return PIC_ECUDA;
+    }
+    if (h->push_smem + sizeof(Run) + 64 > (size_t)max_smem) {
+        delete h;
+        return PIC_EINVAL;  // tile + halo does not fit in shared memory
+    }
+    h->runs.resize(n);
+    h->d_runs = (Run *)dev_alloc(h, sizeof(Run) * n);
+    h->d_states = (RunState *)dev_alloc(h, sizeof(RunState) * n);
+    h->d_seg = (int *)dev_alloc(h, sizeof(int) * 4 * (n + 1));
+    h->d_diag = (double *)dev_alloc(h, sizeof(double) * 16);
+    h->d_count = (unsigned long long *)dev_alloc(h, sizeof(unsigned long long));
+    if (!h->d_runs || !h->d_states || !h->d_seg || !h->d_diag || !h->d_count) {
+        pic_destroy(h);
+        return PIC_ENOMEM;
+    }
+    if (cudaMemsetAsync(h->d_states, 0, sizeof(RunState) * n, h->stream) != cudaSuccess) {
+        pic_destroy(h);
+        return PIC_ECUDA;
+    }
+    std::vector<long long> cells(n), planes(n);
+    for (int i = 0; i < n; ++i) {
+        HostRun &hr = h->runs[i];
+        hr.cfg = cfgs[i];
+        hr.sp = *cfgs[i].species;
+        hr.cfg.species = &hr.sp;
+        int rc = init_run(h, hr, i);
+        if (rc) {
+            pic_destroy(h);
+            return rc;
+        }
+        cells[i] = hr.r.ncell;
+        planes[i] = hr.r.ncell / hr.r.n[hr.r.dim - 1];
+        h->any_open = h->any_open || hr.r.open_last;
+        h->any_window = h->any_window || hr.r.window_on;
+        h->max_tiles = hr.r.ntiles > h->max_tiles ? hr.r.ntiles : h->max_tiles;
+    }
+    int rc = upload_runs(h);
+    if (!rc) rc = set_seg(h, 0, h->seg_cells, cells);
+    if (!rc) rc = set_seg(h, 1, h->seg_planes, planes);
+    if (rc) {
+        pic_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pic_create(const pic_config *cfg, pic_t **out) { return create_common(cfg, 1, out); }
+
+int pic_create_batch(const pic_config *cfgs, int32_t n, pic_t **out) { return create_common(cfgs, n, out); }
+
+int pic_select_run(pic_t *h, int32_t run)
+{
+    if (!h || run < 0 || run >= h->nruns) return PIC_EINVAL;
+    h->cur = run;
+    return PIC_OK;
+}
+
+int32_t pic_num_runs(const pic_t *h) { return h ? h->nruns : 0; }
+
+int pic_load_particles(pic_t *h, int32_t species, int64_t n, const int32_t *cell, const float *off, const float *u,
+                       const float *w)
+{
+    if (!h || species != 0 || n < 0) return PIC_EINVAL;
+    if (h->started) return PIC_ESTATE;
+    if (n == 0) return PIC_OK;
+    if (!cell || !off || !u) return PIC_EINVAL;
+    HostRun &hr = h->runs[h->cur];
+    if (hr.sp.per_particle_weight && !w) return PIC_EINVAL;
+    RunState st;
+    int rc = read_state(h, h->cur, &st);
+    if (rc) return rc;
+    const long long have = st.n_total;
+    const long long need = have + n;
+    const long long room = (long long)(h->sort_interval + 2) * hr.inject_per_shift + 4096;
+    if (!hr.r.P[0].cell || need + room > hr.r.capacity) {
+        if (hr.cfg.capacity > 0 && need + room > hr.cfg.capacity && hr.r.P[0].cell) return PIC_EOVERFLOW;
+        long long cap = hr.cfg.capacity > 0 ? hr.cfg.capacity : (long long)(need * 1.25) + room;
+        if (cap < need + room) cap = need + room;
+        rc = alloc_particles(h, hr, cap, have, st.buf);
+        if (rc) return rc;
+        rc = upload_runs(h);
+        if (rc) return rc;
+    }
+    const int dim = hr.r.dim;
+    // stage the host arrays on the device, then pack into the current buffer
+    size_t bytes = sizeof(int32_t) * dim * n + sizeof(float) * dim * n + sizeof(float) * 3 * n +
+                   (w ? sizeof(float) * n : 0);
+    char *stage = (char *)dev_alloc(h, bytes + 1024);
+    if (!stage) return PIC_ENOMEM;
+    int32_t *dc = (int32_t *)stage;
+    float *doff = (float *)(dc + (size_t)dim * n);
+    float *du = doff + (size_t)dim * n;
+    float *dw = w ? du + (size_t)3 * n : nullptr;
+    cudaError_t e = cudaMemcpyAsync(dc, cell, sizeof(int32_t) * dim * n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(doff, off, sizeof(float) * dim * n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(du, u, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && w) e = cudaMemcpyAsync(dw, w, sizeof(float) * n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = launch_pack(h->d_runs + h->cur, have, n, dim, dc, doff, du, dw, h->stream);
+    if (e == cudaSuccess) e = launch_set_count(h->d_runs + h->cur, need, 0, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    dev_free(h, stage);
+    if (e != cudaSuccess) return PIC_ECUDA;
+    if (cudaMemcpy(&st, h->d_states + h->cur, sizeof(RunState), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return PIC_ECUDA;
+    h->need_sort = true;
+    return status_code(st.status);
+}
+
+int pic_step(pic_t *h, int32_t nsteps)
+{
+    if (!h || nsteps < 0) return PIC_EINVAL;
+    if (!h->started) {
+        int rc = first_step_setup(h);
+        if (rc) return rc;
+    }
+    for (int s = 0; s < nsteps; ++s) {
+        bool sort = h->need_sort || h->since_sort >= h->sort_interval;
+        int kind = sort ? 1 : 0;
+        if (h->use_graph && !h->prof_on) {
+            if (!h->graph[kind]) {
+                cudaGraph_t g = nullptr;
+                if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PIC_ECUDA;
+                int rc = enqueue_step(h, sort);
+                cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+                if (rc || e != cudaSuccess) {
+                    if (g) cudaGraphDestroy(g);
+                    return rc ? rc : PIC_ECUDA;
+                }
+                e = cudaGraphInstantiate(&h->graph[kind], g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) return PIC_ECUDA;
+            }
+            if (cudaGraphLaunch(h->graph[kind], h->stream) != cudaSuccess) return PIC_ECUDA;
+        } else {
+            int rc = enqueue_step(h, sort);
+            if (rc) return rc;
+        }
+        if (sort) {
+            h->need_sort = false;
+            h->since_sort = 0;
+        }
+        h->since_sort += 1;
+    }
+    return PIC_OK;
+}
+
+int pic_sync(pic_t *h)
+{
+    if (!h) return PIC_EINVAL;
+    int worst = PIC_OK;
+    for (int i = 0; i < h->nruns; ++i) {
+        RunState st;
+        int rc = read_state(h, i, &st);
+        if (rc) return rc;
+        int c = status_code(st.status);
+        if (c) worst = c;
+    }
+    return worst;
+}
+
+static int copy_field(pic_t *h, const HostRun &hr, const RunState &st, float *arr, float *ext, bool to_ext,
+                      int on_device)
+{
+    const Run &r = hr.r;
+    const int nl = r.n[r.dim - 1];
+    const size_t plane = (size_t)r.ncell / nl;
+    const int o = r.open_last ? st.origin : 0;
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : (to_ext ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice);
+    // window frame index p <-> storage (p + origin) mod nl: two contiguous slabs
+    size_t a_n = (size_t)(nl - o) * plane, b_n = (size_t)o * plane;
+    cudaError_t e;
+    if (to_ext) {
+        e = cudaMemcpyAsync(ext, arr + (size_t)o * plane, sizeof(float) * a_n, kind, h->stream);
+        if (e == cudaSuccess && b_n) e = cudaMemcpyAsync(ext + a_n, arr, sizeof(float) * b_n, kind, h->stream);
+    } else {
+        e = cudaMemcpyAsync(arr + (size_t)o * plane, ext, sizeof(float) * a_n, kind, h->stream);
+        if (e == cudaSuccess && b_n) e = cudaMemcpyAsync(arr, ext + a_n, sizeof(float) * b_n, kind, h->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return cuda_fail(e);
+}
+
+int pic_read_fields(pic_t *h, int32_t which, float *dst, size_t n_elems, int32_t on_device)
+{
+    if (!h || !dst || which < 0 || which > PIC_RHO) return PIC_EINVAL;
+    HostRun &hr = h->runs[h->cur];
+    if (n_elems < (size_t)hr.r.ncell) return PIC_EINVAL;
+    RunState st;
+    int rc = read_state(h, h->cur, &st);
+    if (rc) return rc;
+    float *src = nullptr;
+    if (which < 3) src = hr.r.E[which];
+    else if (which < 6) src = hr.r.B[which - 3];
+    else if (which < 9) src = hr.r.J[which - 6];
+    else {
+        if (!h->started) {
+            int r2 = upload_runs(h);
+            if (r2) return r2;
+        }
+        cudaError_t e = cudaMemsetAsync(hr.rho, 0, sizeof(float) * hr.r.ncell, h->stream);
+        if (e == cudaSuccess && hr.r.P[0].cell)
+            e = launch_charge(h->dim, h->order, h->d_runs + h->cur, hr.rho, hr.r.capacity, h->stream);
+        if (e != cudaSuccess) return PIC_ECUDA;
+        src = hr.rho;
+    }
+    rc = copy_field(h, hr, st, src, dst, true, on_device);
+    if (rc) return rc;
+    return status_code(st.status);
+}
+
+int pic_write_fields(pic_t *h, int32_t which, const float *src, size_t n_elems, int32_t on_device)
+{
+    if (!h || !src || which < 0 || which > PIC_BZ) return PIC_EINVAL;
+    HostRun &hr = h->runs[h->cur];
+    if (n_elems < (size_t)hr.r.ncell) return PIC_EINVAL;
+    RunState st;
+    int rc = read_state(h, h->cur, &st);
+    if (rc) return rc;
+    float *dstp = which < 3 ? hr.r.E[which] : hr.r.B[which - 3];
+    return copy_field(h, hr, st, dstp, const_cast<float *>(src), false, on_device);
+}
+
+int pic_read_particles(pic_t *h, int32_t species, int32_t *cell, float *off, float *u, float *w, int32_t *id,
+                       int64_t cap, int64_t *n)
+{
+    if (!h || species != 0 || cap < 0 || !n) return PIC_EINVAL;
+    HostRun &hr = h->runs[h->cur];
+    *n = 0;
+    if (!hr.r.P[0].cell) return PIC_OK;
+    if (!h->started) {
+        int rc = upload_runs(h);
+        if (rc) return rc;
+    }
+    RunState st;
+    int rc = read_state(h, h->cur, &st);
+    if (rc) return rc;
+    const int dim = hr.r.dim;
+    const long long slots = st.n_total;
+    const long long m = slots > 0 ? slots : 1;
+    size_t bytes = (sizeof(int32_t) * dim + sizeof(float) * dim + sizeof(float) * 4 + sizeof(int32_t)) * (size_t)m;
+    char *stage = (char *)dev_alloc(h, bytes + 1024);
+    if (!stage) return PIC_ENOMEM;
+    int32_t *dc = (int32_t *)stage;
+    float *doff = (float *)(dc + (size_t)dim * m);
+    float *du = doff + (size_t)dim * m;
+    float *dw = du + (size_t)3 * m;
+    int32_t *did = (int32_t *)(dw + m);
+    cudaError_t e = cudaMemsetAsync(h->d_count, 0, sizeof(unsigned long long), h->stream);
+    if (e == cudaSuccess) e = launch_unpack(h->d_runs + h->cur, m, dim, dc, doff, du, dw, did, h->d_count, h->stream);
+    unsigned long long cnt = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, h->d_count, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        dev_free(h, stage);
+        return PIC_ECUDA;
+    }
+    *n = (int64_t)cnt;
+    if ((long long)cnt > cap) {
+        dev_free(h, stage);
+        return PIC_EOVERFLOW;
+    }
+    for (int a = 0; a < dim && e == cudaSuccess; ++a) {
+        if (cell) e = cudaMemcpyAsync(cell + (size_t)a * cap, dc + (size_t)a * m, sizeof(int32_t) * cnt,
+                                      cudaMemcpyDeviceToHost, h->stream);
+        if (off && e == cudaSuccess)
+            e = cudaMemcpyAsync(off + (size_t)a * cap, doff + (size_t)a * m, sizeof(float) * cnt,
+                                cudaMemcpyDeviceToHost, h->stream);
+    }
+    for (int a = 0; a < 3 && u && e == cudaSuccess; ++a)
+        e = cudaMemcpyAsync(u + (size_t)a * cap, du + (size_t)a * m, sizeof(float) * cnt, cudaMemcpyDeviceToHost,
+                            h->stream);
+    if (w && e == cudaSuccess) e = cudaMemcpyAsync(w, dw, sizeof(float) * cnt, cudaMemcpyDeviceToHost, h->stream);
+    if (id && e == cudaSuccess) e = cudaMemcpyAsync(id, did, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    dev_free(h, stage);
+    if (e != cudaSuccess) return PIC_ECUDA;
+    return status_code(st.status);
+}
+
+int pic_diagnostics(pic_t *h, pic_diag *out)
+{
+    if (!h || !out) return PIC_EINVAL;
+    std::memset(out, 0, sizeof(*out));
+    HostRun &hr = h->runs[h->cur];
+    if (!h->started) {
+        int rc = upload_runs(h);
+        if (rc) return rc;
+    }
+    cudaError_t e = cudaMemsetAsync(h->d_diag, 0, sizeof(double) * 16, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(hr.rho, 0, sizeof(float) * hr.r.ncell, h->stream);
+    if (e == cudaSuccess && hr.r.P[0].cell)
+        e = launch_charge(h->dim, h->order, h->d_runs + h->cur, hr.rho, hr.r.capacity, h->stream);
+    if (e == cudaSuccess) e = launch_diag(h->dim, h->d_runs + h->cur, hr.rho, hr.r.capacity, h->d_diag, h->stream);
+    double dd[16];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dd, h->d_diag, sizeof(dd), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return PIC_ECUDA;
+    RunState st;
+    int rc = read_state(h, h->cur, &st);
+    if (rc) return rc;
+    const Run &r = hr.r;
+    const double V = (double)r.d[0] * r.d[1] * (r.dim == 3 ? r.d[2] : 1.0);
+    unsigned um[4];
+    std::memcpy(um, dd + 8, sizeof(um));
+    float mres, mrho;
+    std::memcpy(&mres, &um[0], 4);
+    std::memcpy(&mrho, &um[1], 4);
+    out->step = st.step;
+    out->time = st.time;
+    out->shifts = st.shifts;
+    out->W_E = 0.5 * dd[0] * V;
+    out->W_B = 0.5 * dd[1] * V;
+    out->W_kin = dd[2] * V;
+    out->n_particles = (int64_t)dd[3];
+    out->gauss_resid = mrho > 0.f ? (double)mres / (double)mrho : (double)mres;
+    out->imbalance = (um[3] > 0 && dd[3] > 0) ? (double)um[2] / (dd[3] / (double)um[3]) : 0.0;
+    out->slow_path = (int64_t)st.slow_last;
+    out->status = status_code(st.status);
+    return out->status;
+}
+
+int pic_profile_begin(pic_t *h, int32_t max_steps)
+{
+    if (!h || max_steps < 1) return PIC_EINVAL;
+    for (cudaEvent_t ev : h->prof_events) cudaEventDestroy(ev);
+    h->prof_events.assign((size_t)max_steps * (PIC_NUM_PHASES + 1), nullptr);
+    for (auto &ev : h->prof_events)
+        if (cudaEventCreate(&ev) != cudaSuccess) return PIC_ECUDA;
+    h->prof_max = max_steps;
+    h->prof_steps = 0;
+    h->prof_launches = 0;
+    h->prof_on = true;
+    return PIC_OK;
+}
+
+int pic_profile_end(pic_t *h, double *ms, int32_t n_phases, int64_t *launches)
+{
+    if (!h || !h->prof_on || !ms || n_phases < 1) return PIC_EINVAL;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PIC_ECUDA;
+    const int np = n_phases < PIC_NUM_PHASES ? n_phases : PIC_NUM_PHASES;
+    for (int p = 0; p < n_phases; ++p) ms[p] = 0.0;
+    for (int s = 0; s < h->prof_steps; ++s) {
+        cudaEvent_t *ev = &h->prof_events[(size_t)s * (PIC_NUM_PHASES + 1)];
+        for (int p = 0; p < np; ++p) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, ev[p], ev[p + 1]) != cudaSuccess) return PIC_ECUDA;
+            ms[p] += t;
+        }
+    }
+    if (launches) *launches = h->prof_launches;
+    h->prof_on = false;
+    return PIC_OK;
+}
+
+void pic_destroy(pic_t *h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    for (cudaEvent_t ev : h->prof_events) cudaEventDestroy(ev);
+    for (int k = 0; k < 2; ++k)
+        if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+    std::vector<void *> all = h->allocs;
+    for (void *p : all) {
+        if (h->free) h->free(p, h->ctx);
+        else cudaFree(p);
+    }
+    delete h;
+}
+
+const char *pic_strerror(int status)
+{
+    switch (status) {
+    case PIC_OK: return "ok";
+    case PIC_EINVAL: return "invalid argument or configuration";
+    case PIC_ENOMEM: return "device allocation failed";
+    case PIC_ECUDA: return "CUDA runtime error";
+    case PIC_EOVERFLOW: return "particle capacity exceeded";
+    case PIC_ETIMEOUT: return "bounded device wait gave up";
+    case PIC_ESTATE: return "call not valid in the current state";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

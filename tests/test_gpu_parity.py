@@ -1,0 +1,182 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+identical seeded inputs.
+
+Tolerances (FP32 device arithmetic against FP64):
+* per-particle momentum after one step: relative 1e-5 (floor 1e-7 absolute);
+  positions after one step: 2e-6 cells;
+* fields after up to 100 steps: relative L2 <= 1e-4 (atomics reorder the
+  current sums, so results are not bitwise reproducible);
+* energy histories over longer runs: within 1e-3 of the largest value;
+* the device's own Gauss-law residual: <= 1e-6 relative to rho_0.
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import FIELD_NAMES, pair, rel_l2, smooth_fields
+from paper_1310_0930_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _fields_close(gpu, orc, tol, names=FIELD_NAMES):
+    worst = {}
+    for name in names:
+        r = rel_l2(gpu.field(name), orc.field(name))
+        worst[name] = r
+    assert max(worst.values()) <= tol, worst
+    return worst
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_yee_vacuum_matches_oracle(dim):
+    w = inputs.thermal_2d(n=(48, 40)) if dim == 2 else inputs.thermal_3d(n=(24, 16, 20))
+    fields = smooth_fields(w, amp=0.3)
+    gpu, orc = pair(w, None, fields=fields)
+    gpu.step(50)
+    orc.step(50)
+    _fields_close(gpu, orc, 1e-5)
+    gpu.close()
+
+
+def test_one_step_momentum_position_current_parity_full_thermal_2d():
+    """128x128, 4 ppc (65,536 particles), smooth random E and B: one step."""
+    w = inputs.thermal_2d()
+    parts = inputs.background(w)
+    fields = smooth_fields(w, amp=0.05)
+    gpu, orc = pair(w, parts, fields=fields)
+    gpu.step(1)
+    orc.step(1)
+    g = gpu.particles()
+    assert g["n"] == parts.n
+    order = np.argsort(g["id"])
+    assert np.array_equal(g["id"][order], np.arange(parts.n))
+    ug = g["u"][:, order].astype(np.float64)
+    xo, uo, _ = orc.particles()
+    du = np.linalg.norm(ug - uo, axis=0)
+    un = np.linalg.norm(uo, axis=0)
+    assert np.max(du / np.maximum(un, 1e-7)) < 1e-5
+    xg = g["cell"][:, order].astype(np.float64) + g["off"][:, order]
+    dx = xg - xo[:2]
+    dx -= np.round(dx / np.array(w.n)[:, None]) * np.array(w.n)[:, None]  # periodic images
+    assert np.max(np.abs(dx)) < 2e-6
+    for name in ("Jx", "Jy", "Jz"):
+        assert rel_l2(gpu.field(name), orc.field(name)) < 1e-5, name
+    _fields_close(gpu, orc, 1e-5)
+    gpu.close()
+
+
+def test_thermal_2d_100_steps_fields_energy_gauss():
+    """128x128 thermal plasma, quadratic, 100 steps."""
+    w = inputs.thermal_2d()
+    parts = inputs.background(w)
+    gpu, orc = pair(w, parts)
+    hist_g, hist_o = [], []
+    worst_gauss = 0.0
+    for s in range(w.steps):
+        gpu.step(1)
+        orc.step(1)
+        if s % 10 == 9:
+            dg = gpu.diagnostics()
+            eo = orc.energies()
+            hist_g.append([dg["W_E"] + dg["W_B"], dg["W_kin"]])
+            hist_o.append([eo["W_E"] + eo["W_B"], eo["W_kin"]])
+            worst_gauss = max(worst_gauss, dg["gauss_resid"])
+    _fields_close(gpu, orc, 1e-4)
+    hg, ho = np.array(hist_g), np.array(hist_o)
+    for col in range(2):
+        assert np.max(np.abs(hg[:, col] - ho[:, col])) <= 1e-3 * np.max(np.abs(ho[:, col]))
+    assert worst_gauss <= 1e-6
+    gpu.close()
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_thermal_3d_orders(order):
+    w = inputs.thermal_3d(n=(16, 16, 16), steps=20, order=order)
+    parts = inputs.background(w)
+    gpu, orc = pair(w, parts)
+    gpu.step(w.steps)
+    orc.step(w.steps)
+    _fields_close(gpu, orc, 1e-4)
+    assert gpu.diagnostics()["gauss_resid"] <= 1e-6
+    gpu.close()
+
+
+@pytest.mark.parametrize("order", [1, 3])
+def test_thermal_2d_other_orders_ragged_tiles(order):
+    """40x36 cells with 16x16 tiles: partial tiles on both axes."""
+    w = inputs.thermal_2d(n=(40, 36), steps=30, order=order)
+    w.uth = 0.05
+    parts = inputs.background(w)
+    gpu, orc = pair(w, parts)
+    gpu.step(w.steps)
+    orc.step(w.steps)
+    _fields_close(gpu, orc, 1e-4)
+    gpu.close()
+
+
+def test_sort_interval_and_drift_do_not_change_results():
+    w = inputs.thermal_2d(n=(64, 64), steps=40)
+    w.uth = 0.1
+    parts = inputs.background(w)
+    runs = []
+    for tuning in ({"sort_interval": 1, "drift": 0}, {"sort_interval": 7, "drift": 3},
+                   {"sort_interval": 5, "drift": 0, "tile": (8, 8)}, {"use_graph": 0}):
+        gpu, _ = pair(w, parts, tuning=tuning)
+        gpu.step(w.steps)
+        runs.append({n: gpu.field(n) for n in FIELD_NAMES})
+        gpu.close()
+    for other in runs[1:]:
+        for n in FIELD_NAMES:
+            assert rel_l2(other[n], runs[0][n]) < 2e-5, n
+
+
+def test_lwfa_2d_laser_open_boundary_moving_window():
+    """Laser antenna, Mur ends, absorbing particles and a moving window
+    injecting plasma: 220 steps, ~80 window shifts."""
+    w = inputs.lwfa_2d(nx=64, nz=320, ppc=(2, 2), density=0.01, a0=2.0, waist=12.0, steps=220)
+    w.laser.fwhm = 8.0
+    w.window.t0 = 36.0
+    parts = inputs.background(w)
+    gpu, orc = pair(w, parts, extra=64 * 4 * 120)
+    hist_g, hist_o = [], []
+    for s in range(w.steps // 20):
+        gpu.step(20)
+        orc.step(20)
+        dg = gpu.diagnostics()
+        eo = orc.energies()
+        hist_g.append([dg["W_E"] + dg["W_B"], dg["W_kin"], dg["n_particles"], dg["shifts"]])
+        hist_o.append([eo["W_E"] + eo["W_B"], eo["W_kin"], orc.np, orc.shifts])
+    hg, ho = np.array(hist_g), np.array(hist_o)
+    assert ho[-1, 3] > 50 and np.array_equal(hg[:, 3], ho[:, 3])
+    assert np.array_equal(hg[:, 2], ho[:, 2])  # same particle count after absorption / injection
+    for col in range(2):
+        assert np.max(np.abs(hg[:, col] - ho[:, col])) <= 1e-3 * np.max(np.abs(ho[:, col]))
+    _fields_close(gpu, orc, 1e-4)
+    gpu.close()
+
+
+def test_lwfa_3d_small_laser_window():
+    w = inputs.lwfa_3d(n=(16, 16, 96), steps=90)
+    w.laser.a0, w.laser.waist, w.laser.fwhm = 1.5, 5.0, 6.0
+    w.window.t0 = 14.0
+    parts = inputs.background(w)
+    gpu, orc = pair(w, parts, extra=16 * 16 * 8 * 40)
+    gpu.step(w.steps)
+    orc.step(w.steps)
+    assert orc.shifts > 20
+    d = gpu.diagnostics()
+    assert d["shifts"] == orc.shifts and d["n_particles"] == orc.np
+    _fields_close(gpu, orc, 1e-4)
+    gpu.close()
+
+
+def test_vacuum_laser_no_particles():
+    w = inputs.lwfa_2d(nx=48, nz=200, steps=120, a0=1.0, waist=10.0)
+    w.laser.fwhm = 8.0
+    w.window = None
+    gpu, orc = pair(w, None)
+    gpu.step(w.steps)
+    orc.step(w.steps)
+    assert gpu.diagnostics()["n_particles"] == 0
+    _fields_close(gpu, orc, 1e-4)
+    gpu.close()
