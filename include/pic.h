@@ -145,7 +145,10 @@ typedef void (*pic_free_fn)(void *ptr, void *ctx);
 /* Tuning: tile[a] cells per tile per axis (powers of two, 0 = default);
  * sort_interval steps between tile sorts (0 = default); drift: cells a
  * particle may stray outside its tile between sorts and still use the
- * staged fast path (-1 = default); block: threads per tile CTA (0 = default);
+ * staged fast path (-1 = default); block: threads per tile CTA (0 = default).
+ * Compiled (tile, drift) pairs: 2D 16x16 with drift 1, 2 (default) or 3,
+ * 8x8 with 1, 32x32 with 2; 3D 8x8x8 with 1 (default) or 2; any other pair
+ * is PIC_EINVAL.
  * use_graph: capture each step kind in a CUDA graph and replay it. */
 typedef struct {
     int32_t tile[3];

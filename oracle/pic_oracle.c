@@ -694,8 +694,7 @@ int or_step(or_sim *s, double *E, double *B, double *J, double *x, double *u, do
         }
         or_yee_b(s, E, B, 0.5 * s->dt);
         or_yee_e(s, E, B, J);
-        s->time += 0.5 * s->dt; /* second half of B sees E^{n+1} at t^{n+1} */
-        s->time += 0.5 * s->dt;
+        s->time += s->dt; /* second half of B sees E^{n+1} at t^{n+1} */
         or_yee_b(s, E, B, 0.5 * s->dt);
         s->step += 1;
         if (s->window_on && s->time >= s->window_t0) {

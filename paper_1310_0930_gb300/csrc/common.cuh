@@ -57,13 +57,15 @@ struct Run {
     int nt[3];         // tiles per axis
     int ntiles;
     int ncell;
-    float d[3], inv_d[3], dt_over_d[3];
+    float d[3], inv_d[3], dt_over_d[3], d_over_dt[3];
     float dt, qm_half_dt, q, m, w_const;
+    double dt_d, d_last_d;  // exact dt and last-axis cell size for time keeping / window decisions
+    double dd[3];           // exact cell sizes (laser profile positions)
     int open_last;     // 1: last axis open (Mur, absorbing), ring-buffered for the window
     int margin;        // particles kept while margin <= phys_last < n_last - margin
     int drift;         // fast-path allowance outside the tile (cells)
     float *E[3], *B[3], *J[3];
-    float *rho0;       // initial electron charge density (neutralising background)
+    double *rho0;      // initial electron charge density (neutralising background), FP64 diagnostic
     float *mur;        // saved tangential E planes for Mur: [2][4][plane]
     ParticleBuf P[2];
     int32_t *tile_off; // [ntiles + 1] particle offsets per tile

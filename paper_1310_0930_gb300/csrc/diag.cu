@@ -60,7 +60,7 @@ __device__ __forceinline__ bool live(const Run &r, const RunState &s, int32_t c,
 }
 
 template <int DIM, int P>
-__global__ void charge_kernel(const Run *__restrict__ run, float *__restrict__ rho, long long cap)
+__global__ void charge_kernel(const Run *__restrict__ run, double *__restrict__ rho, long long cap)
 {
     const Run &r = *run;
     const RunState &s = *r.state;
@@ -73,7 +73,7 @@ __global__ void charge_kernel(const Run *__restrict__ run, float *__restrict__ r
     float w[3][P + 1] = {};
 #pragma unroll
     for (int a = 0; a < DIM; ++a) Shape<P>::node(c[a], pb.off[a][i], base[a], w[a]);
-    const float qw = r.q * (pb.w ? pb.w[i] : r.w_const);
+    const double qw = (double)r.q * (double)(pb.w ? pb.w[i] : r.w_const);
     const int n0 = r.n[0], n1 = r.n[1], n2 = DIM == 3 ? r.n[2] : 1;
 #pragma unroll
     for (int qz = 0; qz < (DIM == 3 ? P + 1 : 1); ++qz)
@@ -81,7 +81,7 @@ __global__ void charge_kernel(const Run *__restrict__ run, float *__restrict__ r
         for (int qy = 0; qy <= P; ++qy)
 #pragma unroll
             for (int qx = 0; qx <= P; ++qx) {
-                float v = qw * w[0][qx] * w[1][qy] * (DIM == 3 ? w[2][qz] : 1.f);
+                double v = qw * (double)w[0][qx] * (double)w[1][qy] * (DIM == 3 ? (double)w[2][qz] : 1.0);
                 int x = wrapi(base[0] + qx, n0), y = wrapi(base[1] + qy, n1);
                 int z = DIM == 3 ? wrapi(base[2] + qz, n2) : 0;
                 atomicAdd(rho + x + n0 * (y + n1 * z), v);
@@ -184,7 +184,7 @@ __global__ void kinetic_kernel(const Run *__restrict__ run, double *out)
 }
 
 template <int DIM>
-__global__ void gauss_kernel(const Run *__restrict__ run, const float *__restrict__ rho, unsigned *umax)
+__global__ void gauss_kernel(const Run *__restrict__ run, const double *__restrict__ rho, unsigned *umax)
 {
     const Run &r = *run;
     const int n0 = r.n[0], n1 = r.n[1], n2 = DIM == 3 ? r.n[2] : 1;
@@ -198,9 +198,9 @@ __global__ void gauss_kernel(const Run *__restrict__ run, const float *__restric
             int mz = i + n0 * (j + n1 * (k == 0 ? n2 - 1 : k - 1));
             dv += ((double)r.E[2][idx] - r.E[2][mz]) / r.d[2];
         }
-        double res = dv - ((double)rho[idx] - (double)r.rho0[idx]);
+        double res = dv - (rho[idx] - r.rho0[idx]);
         mr = fmaxf(mr, (float)fabs(res));
-        m0 = fmaxf(m0, fabsf(r.rho0[idx]));
+        m0 = fmaxf(m0, (float)fabs(r.rho0[idx]));
     }
     atomicMax(umax + 0, __float_as_uint(mr));
     atomicMax(umax + 1, __float_as_uint(m0));
@@ -235,7 +235,20 @@ cudaError_t launch_set_count(const Run *run, long long n_total, int sorted, cuda
     return cudaGetLastError();
 }
 
-cudaError_t launch_charge(int dim, int order, const Run *run, float *rho, long long cap, cudaStream_t st)
+__global__ void to_float_kernel(const double *__restrict__ src, float *__restrict__ dst, long long n)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (float)src[i];
+}
+
+cudaError_t launch_to_float(const double *src, float *dst, long long n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    to_float_kernel<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, st>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_charge(int dim, int order, const Run *run, double *rho, long long cap, cudaStream_t st)
 {
     unsigned g = (unsigned)((cap + kBlock - 1) / kBlock);
     if (g == 0) return cudaSuccess;
@@ -260,7 +273,7 @@ cudaError_t launch_unpack(const Run *run, long long cap, int dim, int32_t *cell,
     return cudaGetLastError();
 }
 
-cudaError_t launch_diag(int dim, const Run *run, const float *rho, long long cap, double *out, cudaStream_t st)
+cudaError_t launch_diag(int dim, const Run *run, const double *rho, long long cap, double *out, cudaStream_t st)
 {
     unsigned *umax = reinterpret_cast<unsigned *>(out + 8);
     field_energy_kernel<<<1024, kBlock, 0, st>>>(run, out);

@@ -45,8 +45,8 @@ __device__ double laser_r2(const Run &r, int i, int j)
     int idx[2] = {i, j};
     for (int a = 0; a < last; ++a) {
         double off = (a == r.laser_pol) ? 0.5 : 0.0;
-        double pos = ((double)idx[a] + off) * r.d[a];
-        double ctr = 0.5 * r.n[a] * (double)r.d[a];
+        double pos = ((double)idx[a] + off) * r.dd[a];
+        double ctr = 0.5 * r.n[a] * r.dd[a];
         r2 += (pos - ctr) * (pos - ctr);
     }
     return r2;
@@ -104,7 +104,7 @@ __global__ void yee_b_kernel(const Run *__restrict__ runs, Seg seg, int second)
             bcomp = 2;
             sgn = -1.0;
         }
-        const double t = s.time + (second ? (double)r.dt : 0.0);
+        const double t = s.time + (second ? r.dt_d : 0.0);
         const double e = laser_field(r, laser_r2(r, i, j), t);
         r.B[bcomp][idx] += (float)(sgn * (double)h * (double)r.inv_d[DIM - 1] * e);
     }
@@ -151,8 +151,8 @@ __global__ void yee_e_kernel(const Run *__restrict__ runs, Seg seg)
     }
     if (laser_active(r, s) && il == r.laser_plane) {
         // E_pol on the plane saw the scattered B_b one plane behind: add the incident B.
-        const double th = s.time + 0.5 * (double)dt;
-        const double e = laser_field(r, laser_r2(r, i, j), th + 0.5 * (double)r.d[DIM - 1]);
+        const double th = s.time + 0.5 * r.dt_d;
+        const double e = laser_field(r, laser_r2(r, i, j), th + 0.5 * r.d_last_d);
         nv[r.laser_pol] += (float)((double)dt * (double)r.inv_d[DIM - 1] * e);
     }
     Ex[idx] = nv[0];
@@ -231,14 +231,14 @@ __global__ void end_step_kernel(const Run *__restrict__ runs, int nruns)
     if (ri >= nruns) return;
     const Run &r = runs[ri];
     RunState &s = *r.state;
-    s.time += (double)r.dt;
+    s.time += r.dt_d;
     s.step += 1;
     s.slow_last = s.slow;
     s.slow = 0;
     s.shift_pending = 0;
     if (r.window_on && s.time >= r.window_t0) {
         const double travelled = r.window_v * (s.time - r.window_t0);
-        if (travelled >= (double)(s.shifts + 1) * (double)r.d[r.dim - 1]) {
+        if (travelled >= (double)(s.shifts + 1) * r.d_last_d) {
             const int nl = r.n[r.dim - 1];
             s.shifts += 1;
             s.origin = s.origin + 1 == nl ? 0 : s.origin + 1;
@@ -319,7 +319,7 @@ __global__ void window_inject_kernel(const Run *__restrict__ runs, Seg seg)
     pb.u[1][slot] = 0.f;
     pb.u[2][slot] = 0.f;
     if (pb.w) {
-        const double zlab = ((double)kcell + (double)off_last + (double)s.shifts) * (double)r.d[dim - 1];
+        const double zlab = ((double)kcell + (double)off_last + (double)s.shifts) * r.d_last_d;
         pb.w[slot] = (float)(profile_density(r, zlab) / ppc_t);
     }
     if (pb.id) pb.id[slot] = -1;

@@ -21,9 +21,12 @@ struct Seg {
 
 constexpr int kBlock = 256;
 
+// Particle kernel (push.cuh) over the compiled tile menu (push_menu.h).
+// push_smem_bytes returns 0 for a (tile, drift) pair that is not compiled.
+int push_default_drift(int dim, const int *tile);
 size_t push_smem_bytes(int dim, int order, const int *tile, int drift);
-cudaError_t launch_push(int dim, int order, const Run *runs, const Item *items, int nitems, size_t smem,
-                        int block, int tail_block, cudaStream_t st);
+cudaError_t launch_push(int dim, int order, const int *tile, int drift, const Run *runs, const Item *items,
+                        int nitems, int block, int tail_block, cudaStream_t st);
 
 // fields.cu
 cudaError_t launch_zero_j(const Run *runs, Seg cells, cudaStream_t st);
@@ -41,12 +44,15 @@ cudaError_t launch_sort(const Run *runs, int nruns, Seg parts, int max_tiles, cu
 cudaError_t launch_pack(const Run *run, long long base, long long n, int dim, const int32_t *cell,
                         const float *off, const float *u, const float *w, cudaStream_t st);
 cudaError_t launch_set_count(const Run *run, long long n_total, int sorted, cudaStream_t st);
-cudaError_t launch_charge(int dim, int order, const Run *run, float *rho, long long cap, cudaStream_t st);
+// charge density of the live particles accumulated in FP64 (diagnostics only)
+cudaError_t launch_charge(int dim, int order, const Run *run, double *rho, long long cap, cudaStream_t st);
+cudaError_t launch_to_float(const double *src, float *dst, long long n, cudaStream_t st);
 cudaError_t launch_unpack(const Run *run, long long cap, int dim, int32_t *cell, float *off, float *u, float *w,
                           int32_t *id, unsigned long long *count, cudaStream_t st);
 // out (16 doubles): [0] sum E^2, [1] sum B^2, [2] sum w m (gamma - 1), [3] live particles;
-// out+8 viewed as unsigned[4]: max|div E - (rho - rho0)| and max|rho0| (float bits),
+// out+8 viewed as unsigned[4]: max|div E - (rho - rho0)| and max|rho0| (float bits of the
+// FP64 values rounded down to FP32),
 // max particles in a tile, occupied tiles.
-cudaError_t launch_diag(int dim, const Run *run, const float *rho, long long cap, double *out, cudaStream_t st);
+cudaError_t launch_diag(int dim, const Run *run, const double *rho, long long cap, double *out, cudaStream_t st);
 
 }  // namespace pic

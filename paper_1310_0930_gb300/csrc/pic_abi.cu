@@ -26,7 +26,8 @@ struct HostRun {
     std::vector<double> knots;
     Run r;
     long long inject_per_shift = 0;
-    float *rho = nullptr;  // diagnostics scratch (charge density)
+    double *rho = nullptr;  // diagnostics scratch (charge density, FP64)
+    float *rho32 = nullptr; // FP32 copy for pic_read_fields(PIC_RHO)
 };
 
 }  // namespace
@@ -144,7 +145,7 @@ int validate(const pic_config *c)
     for (int a = 0; a < g.dim; ++a)
         if (t.tile[a] != 0 && !pow2(t.tile[a])) return PIC_EINVAL;
     if (t.drift < -1 || t.drift > 8) return PIC_EINVAL;
-    if (t.block != 0 && t.block != 64 && t.block != 128 && t.block != 256) return PIC_EINVAL;
+    if (t.block != 0 && t.block != 128 && t.block != 256 && t.block != 512) return PIC_EINVAL;
     if (t.sort_interval < 0) return PIC_EINVAL;
     return PIC_OK;
 }
@@ -279,7 +280,7 @@ int enqueue_step(pic_s *h, bool sort)
     if (e == cudaSuccess) e = launch_zero_j(R, h->seg_cells, st);
     mark(PIC_PH_PUSH);
     if (e == cudaSuccess)
-        e = launch_push(h->dim, h->order, R, h->d_items, h->n_items, h->push_smem, h->block, kTail, st);
+        e = launch_push(h->dim, h->order, h->tile, h->drift, R, h->d_items, h->n_items, h->block, kTail, st);
     mark(PIC_PH_YEE_B1);
     if (e == cudaSuccess) e = launch_yee_b(h->dim, R, h->seg_cells, 0, st);
     mark(PIC_PH_YEE_E);
@@ -320,12 +321,13 @@ int first_step_setup(pic_s *h)
     // the initial electron charge is the neutralising background (rho_0)
     for (int i = 0; i < h->nruns; ++i) {
         HostRun &hr = h->runs[i];
-        cudaError_t e = cudaMemsetAsync(hr.r.rho0, 0, sizeof(float) * hr.r.ncell, h->stream);
+        cudaError_t e = cudaMemsetAsync(hr.r.rho0, 0, sizeof(double) * hr.r.ncell, h->stream);
         if (e == cudaSuccess) e = launch_charge(h->dim, h->order, h->d_runs + i, hr.r.rho0, hr.r.capacity, h->stream);
         if (e != cudaSuccess) return PIC_ECUDA;
     }
     // sets the push kernel's shared-memory limit outside any graph capture
-    cudaError_t e = launch_push(h->dim, h->order, h->d_runs, h->d_items, 0, h->push_smem, h->block, kTail, h->stream);
+    cudaError_t e =
+        launch_push(h->dim, h->order, h->tile, h->drift, h->d_runs, h->d_items, 0, h->block, kTail, h->stream);
     if (e != cudaSuccess) return PIC_ECUDA;
     h->started = true;
     return PIC_OK;
@@ -344,6 +346,7 @@ int init_run(pic_s *h, HostRun &hr, int idx)
         r.d[a] = a < r.dim ? (float)c.grid.d[a] : 1.f;
         r.inv_d[a] = (float)(1.0 / (a < r.dim ? c.grid.d[a] : 1.0));
         r.dt_over_d[a] = (float)(c.grid.dt / (a < r.dim ? c.grid.d[a] : 1.0));
+        r.d_over_dt[a] = (float)((a < r.dim ? c.grid.d[a] : 1.0) / c.grid.dt);
         r.bits[a] = a < r.dim ? bits_for(r.n[a]) : 0;
         int T = a < r.dim ? h->tile[a] : 1;
         r.tlog[a] = ilog2(T);
@@ -353,6 +356,9 @@ int init_run(pic_s *h, HostRun &hr, int idx)
     r.ncell = (int)ncell;
     r.ntiles = r.nt[0] * r.nt[1] * r.nt[2];
     r.dt = (float)c.grid.dt;
+    r.dt_d = c.grid.dt;
+    r.d_last_d = c.grid.d[c.grid.dim - 1];
+    for (int a = 0; a < 3; ++a) r.dd[a] = a < r.dim ? c.grid.d[a] : 1.0;
     r.q = (float)hr.sp.q;
     r.m = (float)hr.sp.m;
     r.qm_half_dt = (float)(0.5 * hr.sp.q / hr.sp.m * c.grid.dt);
@@ -368,19 +374,20 @@ int init_run(pic_s *h, HostRun &hr, int idx)
         r.J[a] = (float *)dev_alloc(h, sizeof(float) * ncell);
         if (!r.E[a] || !r.B[a] || !r.J[a]) return PIC_ENOMEM;
     }
-    r.rho0 = (float *)dev_alloc(h, sizeof(float) * ncell);
-    hr.rho = (float *)dev_alloc(h, sizeof(float) * ncell);
+    r.rho0 = (double *)dev_alloc(h, sizeof(double) * ncell);
+    hr.rho = (double *)dev_alloc(h, sizeof(double) * ncell);
+    hr.rho32 = (float *)dev_alloc(h, sizeof(float) * ncell);
     r.mur = (float *)dev_alloc(h, sizeof(float) * 8 * plane);
     r.tile_off = (int32_t *)dev_alloc(h, sizeof(int32_t) * (r.ntiles + 1));
     r.tile_cnt = (int32_t *)dev_alloc(h, sizeof(int32_t) * (r.ntiles + 1));
-    if (!r.rho0 || !hr.rho || !r.mur || !r.tile_off || !r.tile_cnt) return PIC_ENOMEM;
+    if (!r.rho0 || !hr.rho || !hr.rho32 || !r.mur || !r.tile_off || !r.tile_cnt) return PIC_ENOMEM;
     cudaError_t e = cudaSuccess;
     for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
         e = cudaMemsetAsync(r.E[a], 0, sizeof(float) * ncell, h->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(r.B[a], 0, sizeof(float) * ncell, h->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(r.J[a], 0, sizeof(float) * ncell, h->stream);
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(r.rho0, 0, sizeof(float) * ncell, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r.rho0, 0, sizeof(double) * ncell, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(r.mur, 0, sizeof(float) * 8 * plane, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(r.tile_off, 0, sizeof(int32_t) * (r.ntiles + 1), h->stream);
     if (e != cudaSuccess) return PIC_ECUDA;
@@ -442,11 +449,15 @@ int create_common(const pic_config *cfgs, int n, pic_t **out)
         int def = h->dim == 3 ? 8 : 16;
         h->tile[a] = a < h->dim ? (t.tile[a] ? t.tile[a] : def) : 1;
     }
-    h->drift = t.drift >= 0 ? t.drift : (h->dim == 3 ? 1 : 2);
-    h->block = t.block ? t.block : 256;
+    h->drift = t.drift >= 0 ? t.drift : push_default_drift(h->dim, h->tile);
+    h->block = t.block ? t.block : (h->dim == 3 ? 512 : 256);
     h->sort_interval = t.sort_interval ? t.sort_interval : 4;
     h->use_graph = t.use_graph != 0 && h->stream != nullptr;
     h->push_smem = push_smem_bytes(h->dim, h->order, h->tile, h->drift);
+    if (h->push_smem == 0) {  // (tile, drift) not among the compiled configurations
+        delete h;
+        return PIC_EINVAL;
+    }
     int dev = 0;
     int max_smem = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -657,11 +668,12 @@ int pic_read_fields(pic_t *h, int32_t which, float *dst, size_t n_elems, int32_t
             int r2 = upload_runs(h);
             if (r2) return r2;
         }
-        cudaError_t e = cudaMemsetAsync(hr.rho, 0, sizeof(float) * hr.r.ncell, h->stream);
+        cudaError_t e = cudaMemsetAsync(hr.rho, 0, sizeof(double) * hr.r.ncell, h->stream);
         if (e == cudaSuccess && hr.r.P[0].cell)
             e = launch_charge(h->dim, h->order, h->d_runs + h->cur, hr.rho, hr.r.capacity, h->stream);
+        if (e == cudaSuccess) e = launch_to_float(hr.rho, hr.rho32, hr.r.ncell, h->stream);
         if (e != cudaSuccess) return PIC_ECUDA;
-        src = hr.rho;
+        src = hr.rho32;
     }
     rc = copy_field(h, hr, st, src, dst, true, on_device);
     if (rc) return rc;
@@ -747,7 +759,7 @@ int pic_diagnostics(pic_t *h, pic_diag *out)
         if (rc) return rc;
     }
     cudaError_t e = cudaMemsetAsync(h->d_diag, 0, sizeof(double) * 16, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(hr.rho, 0, sizeof(float) * hr.r.ncell, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(hr.rho, 0, sizeof(double) * hr.r.ncell, h->stream);
     if (e == cudaSuccess && hr.r.P[0].cell)
         e = launch_charge(h->dim, h->order, h->d_runs + h->cur, hr.rho, hr.r.capacity, h->stream);
     if (e == cudaSuccess) e = launch_diag(h->dim, h->d_runs + h->cur, hr.rho, hr.r.capacity, h->d_diag, h->stream);

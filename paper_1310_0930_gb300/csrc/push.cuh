@@ -1,0 +1,663 @@
+// push.cuh -- fused particle kernel of the EM-PIC timestep (Sec. 5.2 steps
+// i-v): per particle, B-spline weights -> gather of E and B at the Yee
+// locations -> relativistic Boris push -> move on (cell, offset) -> Esirkepov
+// charge-conserving current deposit.
+//
+// One CTA per tile (a block of TX x TY x TZ cells).  The tile's E and B plus
+// a halo are staged in shared memory; its particles (sorted by tile) are
+// loaded coalesced from the structure-of-arrays buffers with the next
+// particle prefetched; the current of the whole tile is accumulated in a
+// shared-memory J tile (the GPU form of the paper's per-thread current
+// copies, Sec. 3.1) and flushed to global J once with atomics (the paper's
+// reduction of the copies).
+//
+// The J tile holds each value as two int32 words (hi, lo) of a fixed-point
+// number with a per-tile scale S = 2^30 / (1.01 sum |q w|): every single
+// contribution c satisfies |c| <= |q w| |v| <= |q w|, so |sum hi| < 2^31;
+// lo carries 12 more bits of the remainder.  Native int32 shared-memory
+// atomics replace FP32 ones (which the hardware emulates with a
+// compare-and-swap loop), integer sums are order-independent, and the
+// resolution, 2^-42 of the tile's total |q w|, is finer than FP32 rounding
+// of the per-node sums.
+//
+// Tile geometry and the drift allowance are template parameters, so every
+// shared-memory address in a particle's stencil is a base register plus an
+// immediate offset.  A particle that strayed further than D cells out of
+// its tile since the last sort, and every particle of the unsorted tail
+// (freshly injected plasma), takes the slow path: the same arithmetic on
+// global memory with FP32 global atomics.
+#pragma once
+#include "common.cuh"
+#include "internal.h"
+
+namespace pic {
+namespace push_detail {
+
+constexpr float kLoScale = 4096.f;  // 12 bits for the lo word
+
+template <int DIM, int P, int TX, int TY, int TZ, int D>
+struct Geo {
+    static constexpr int GLO = Reach<P>::GLO, GHI = Reach<P>::GHI, DLO = Reach<P>::DLO, DHI = Reach<P>::DHI;
+    static constexpr int FX = TX + 2 * D + GLO + GHI, FY = TY + 2 * D + GLO + GHI;
+    static constexpr int FZ = DIM == 3 ? TZ + 2 * D + GLO + GHI : 1;
+    static constexpr int FHX = D + GLO, FHY = D + GLO, FHZ = DIM == 3 ? D + GLO : 0;
+    static constexpr int JX = TX + 2 * D + DLO + DHI, JY = TY + 2 * D + DLO + DHI;
+    static constexpr int JZ = DIM == 3 ? TZ + 2 * D + DLO + DHI : 1;
+    static constexpr int JHX = D + DLO, JHY = D + DLO, JHZ = DIM == 3 ? D + DLO : 0;
+    static constexpr int FVOL = FX * FY * FZ, JVOL = JX * JY * JZ;
+    static __host__ __device__ constexpr int tile(int a) { return a == 0 ? TX : (a == 1 ? TY : (DIM == 3 ? TZ : 1)); }
+    static constexpr size_t SMEM = sizeof(float) * 6 * FVOL + sizeof(int) * 2 * 3 * JVOL;
+};
+
+// ---------------------------------------------------------------- gather
+// Component C from shared memory: bases relative to the tile origin.
+template <int DIM, int P, class G, int C>
+__device__ __forceinline__ float gather_s(const float *Fs, int bx, int by, int bz, const float *wx,
+                                          const float *wy, const float *wz)
+{
+    const float *p = Fs + C * G::FVOL + (bx + G::FHX) + G::FX * ((by + G::FHY) + G::FY * (bz + G::FHZ));
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < (DIM == 3 ? P + 1 : 1); ++c) {
+        float sy = 0.f;
+#pragma unroll
+        for (int b = 0; b <= P; ++b) {
+            float sx = 0.f;
+#pragma unroll
+            for (int a = 0; a <= P; ++a) sx = fmaf(wx[a], p[a + G::FX * (b + G::FY * c)], sx);
+            sy = fmaf(wy[b], sx, sy);
+        }
+        s = DIM == 3 ? fmaf(wz[c], sy, s) : sy;
+    }
+    return s;
+}
+
+// Component C from global memory, absolute bases wrapped periodically.
+struct GlobalFields {
+    const float *p[6];
+    int n0, n1, n2;
+};
+
+template <int DIM, int P, int C>
+__device__ __forceinline__ float gather_g(const GlobalFields &g, int bx, int by, int bz, const float *wx,
+                                          const float *wy, const float *wz)
+{
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < (DIM == 3 ? P + 1 : 1); ++c) {
+        const int z = DIM == 3 ? wrapi(bz + c, g.n2) : 0;
+        float sy = 0.f;
+#pragma unroll
+        for (int b = 0; b <= P; ++b) {
+            const int y = wrapi(by + b, g.n1);
+            const float *row = g.p[C] + g.n0 * (y + g.n1 * z);
+            float sx = 0.f;
+#pragma unroll
+            for (int a = 0; a <= P; ++a) sx = fmaf(wx[a], __ldg(row + wrapi(bx + a, g.n0)), sx);
+            sy = fmaf(wy[b], sx, sy);
+        }
+        s = DIM == 3 ? fmaf(wz[c], sy, s) : sy;
+    }
+    return s;
+}
+
+// Relativistic Boris push (Sec. 5.2 step iii): half electric kick, rotation
+// with t = (q dt / 2 m gamma) B and s = 2t/(1+t^2), half electric kick.
+__device__ __forceinline__ void boris(float h, const float *e, const float *b, float *u)
+{
+    float um0 = fmaf(h, e[0], u[0]), um1 = fmaf(h, e[1], u[1]), um2 = fmaf(h, e[2], u[2]);
+    float ig = rsqrtf(1.f + um0 * um0 + um1 * um1 + um2 * um2);
+    float t0 = h * b[0] * ig, t1 = h * b[1] * ig, t2 = h * b[2] * ig;
+    float f = 2.f * __frcp_rn(1.f + t0 * t0 + t1 * t1 + t2 * t2);
+    float s0 = f * t0, s1 = f * t1, s2 = f * t2;
+    float p0 = um0 + (um1 * t2 - um2 * t1);
+    float p1 = um1 + (um2 * t0 - um0 * t2);
+    float p2 = um2 + (um0 * t1 - um1 * t0);
+    u[0] = fmaf(h, e[0], um0 + (p1 * s2 - p2 * s1));
+    u[1] = fmaf(h, e[1], um1 + (p2 * s0 - p0 * s2));
+    u[2] = fmaf(h, e[2], um2 + (p0 * s1 - p1 * s0));
+}
+
+// Place the P+1 shape values `s` into a P+2 window at offset o (0 or 1)
+// with compile-time indexing only (no local-memory arrays).
+template <int P>
+__device__ __forceinline__ void place(const float *s, int o, float *dst)
+{
+#pragma unroll
+    for (int q = 0; q < P + 2; ++q) {
+        float lo = q <= P ? s[q] : 0.f;
+        float hi = q >= 1 ? s[q - 1] : 0.f;
+        dst[q] = o ? hi : lo;
+    }
+}
+
+// Per-axis Esirkepov window of one straight move: old and new node shapes
+// on a (P+2)-node window starting at wb, DS = S1 - S0, A = S0 + DS/2, and
+// the prefix sums of DS scaled by coef (the J_a values along a).  When the
+// nearest node did not change (shift 0) the last window node carries no
+// weight and the last prefix is exactly zero (charge conservation); it is
+// set to zero rather than to its rounding residue.
+template <int P>
+struct Axis {
+    float A[P + 2], DS[P + 2], Pre[P + 1];
+    int wb;
+    int shift;
+};
+
+template <int P>
+__device__ __forceinline__ void axis_window(int c0, float d0, int k, float d1, float coef, Axis<P> &ax)
+{
+    int bo, bn;
+    float so[P + 1], sn[P + 1], S0[P + 2], S1[P + 2];
+    Shape<P>::node(c0, d0, bo, so);
+    Shape<P>::node(c0 + k, d1, bn, sn);
+    const int s = bn - bo;  // -1, 0 or +1 for a move of less than one cell
+    ax.shift = s;
+    ax.wb = s < 0 ? bn : bo;
+    place<P>(so, s < 0 ? 1 : 0, S0);
+    place<P>(sn, s > 0 ? 1 : 0, S1);
+    float run = 0.f;
+#pragma unroll
+    for (int q = 0; q < P + 2; ++q) {
+        ax.DS[q] = S1[q] - S0[q];
+        ax.A[q] = S0[q] + 0.5f * ax.DS[q];
+        if (q < P + 1) {
+            run += ax.DS[q];
+            ax.Pre[q] = coef * run;
+        }
+    }
+    if (s == 0) ax.Pre[P] = 0.f;
+}
+
+// Esirkepov deposit (Sec. 5.2 charge-conserving deposit):
+//   3D: J_a(window) = coef_a * prefix_a(DS_a) * (A_b A_c + DS_b DS_c / 12),
+//   2D: J_x = coef_x prefix_x(DS_x) A_y, J_y = coef_y prefix_y(DS_y) A_x,
+//       J_z = q w v_z (A_x A_y + DS_x DS_y / 12),
+// coef_a = -q w d_a / dt.  (A_b A_c + DS_b DS_c/12 equals the textbook
+// S0S0 + DS S0/2 + S0 DS/2 + DS DS/3.)  `emit(comp, qa, qb, qc, v)` receives
+// each value with its window coordinates (axis order x, y, z).
+template <int DIM, int P, class Emit>
+__device__ __forceinline__ void esirkepov(const Axis<P> *ax, float qwvz, const Emit &emit)
+{
+    constexpr int W = P + 2;
+    const float twelfth = 1.f / 12.f;
+    if (DIM == 3) {
+#pragma unroll
+        for (int comp = 0; comp < 3; ++comp) {
+            const int a = comp, b = (comp + 1) % 3, c = (comp + 2) % 3;
+#pragma unroll
+            for (int qc = 0; qc < W; ++qc)
+#pragma unroll
+                for (int qb = 0; qb < W; ++qb) {
+                    const float fac = fmaf(ax[b].DS[qb] * twelfth, ax[c].DS[qc], ax[b].A[qb] * ax[c].A[qc]);
+#pragma unroll
+                    for (int qa = 0; qa < W - 1; ++qa) {
+                        int q3[3];
+                        q3[a] = qa;
+                        q3[b] = qb;
+                        q3[c] = qc;
+                        emit(comp, q3[0], q3[1], q3[2], ax[a].Pre[qa] * fac);
+                    }
+                }
+        }
+    } else {
+#pragma unroll
+        for (int qb = 0; qb < W; ++qb)
+#pragma unroll
+            for (int qa = 0; qa < W; ++qa) {
+                if (qa < W - 1) emit(0, qa, qb, 0, ax[0].Pre[qa] * ax[1].A[qb]);
+                if (qb < W - 1) emit(1, qa, qb, 0, ax[1].Pre[qb] * ax[0].A[qa]);
+                emit(2, qa, qb, 0,
+                     qwvz * fmaf(ax[0].DS[qa] * twelfth, ax[1].DS[qb], ax[0].A[qa] * ax[1].A[qb]));
+            }
+    }
+}
+
+// One particle's weights, gather, push and move.  cr: cell coordinates in
+// the accessor's frame.  Returns false for a non-finite or over-long move.
+template <int DIM, int P, class GatherFn>
+__device__ __forceinline__ bool push_move(const Run &r, const GatherFn &gather, const int *cr, const float *d,
+                                          float *u, float *d1, int *k, float &ig)
+{
+    int bn[3] = {0, 0, 0}, bh[3] = {0, 0, 0};
+    float wn[3][P + 1], wh[3][P + 1];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        Shape<P>::node(cr[a], d[a], bn[a], wn[a]);
+        Shape<P>::half(cr[a], d[a], bh[a], wh[a]);
+    }
+    if (DIM == 2) {
+#pragma unroll
+        for (int q = 0; q <= P; ++q) wn[2][q] = wh[2][q] = 0.f;
+    }
+    float e[3], b[3];
+    gather(bn, bh, wn, wh, e, b);
+    boris(r.qm_half_dt, e, b, u);
+    ig = rsqrtf(1.f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        float nd = d[a] + r.dt_over_d[a] * u[a] * ig;
+        ok = ok && nd > -1.f && nd < 2.f;  // false for NaN too
+        nd = ok ? nd : d[a];
+        float kk = floorf(nd);
+        nd = nd - kk;
+        if (nd >= 1.f) {  // FP32 rounding of a value just below an integer
+            nd = 0.f;
+            kk += 1.f;
+        }
+        d1[a] = nd;
+        k[a] = (int)kk;
+    }
+    return ok;
+}
+
+// Yee locations: E0 (h,n,n) E1 (n,h,n) E2 (n,n,h) B0 (n,h,h) B1 (h,n,h) B2 (h,h,n);
+// h = half-integer, n = integer; bit c of kHalf{X,Y,Z} marks component c as
+// half-integer along that axis.  In 2D the third entry is unused.
+constexpr unsigned kHalfX = 0x31u, kHalfY = 0x2Au, kHalfZ = 0x1Cu;
+
+// Shared-memory gather of the six components; each component's loads are
+// immediate offsets from one base address.
+template <int DIM, int P, class G>
+struct SmemGather {
+    const float *Fs;
+    __device__ __forceinline__ void operator()(const int *bn, const int *bh, const float (*wn)[P + 1],
+                                               const float (*wh)[P + 1], float *e, float *b) const
+    {
+        e[0] = gather_s<DIM, P, G, 0>(Fs, bh[0], bn[1], bn[2], wh[0], wn[1], wn[2]);
+        e[1] = gather_s<DIM, P, G, 1>(Fs, bn[0], bh[1], bn[2], wn[0], wh[1], wn[2]);
+        e[2] = gather_s<DIM, P, G, 2>(Fs, bn[0], bn[1], bh[2], wn[0], wn[1], wh[2]);
+        b[0] = gather_s<DIM, P, G, 3>(Fs, bn[0], bh[1], bh[2], wn[0], wh[1], wh[2]);
+        b[1] = gather_s<DIM, P, G, 4>(Fs, bh[0], bn[1], bh[2], wh[0], wn[1], wh[2]);
+        b[2] = gather_s<DIM, P, G, 5>(Fs, bh[0], bh[1], bn[2], wh[0], wh[1], wn[2]);
+    }
+};
+
+// Add one value to the fixed-point J tile: x = value * S split into the
+// rounded integer part (hi) and 12 bits of remainder (lo).  x is computed as
+// ps * fac with ps already scaled by S.
+__device__ __forceinline__ void fix_add(int *hi_base, int *lo_base, int off, float ps, float fac)
+{
+    const float x = ps * fac;
+    if (x == 0.f) return;
+    const float h = rintf(x);  // exact integer (|x| <= 2^30; above 2^24 x is already integral)
+    const float rem = fmaf(ps, fac, -h);
+    atomicAdd(hi_base + off, (int)h);
+    atomicAdd(lo_base + off, __float2int_rn(rem * kLoScale));
+}
+
+// 3D Esirkepov deposit into the shared-memory J tile: a loop over the three
+// components, axis roles (a, b, c) = (comp, comp+1, comp+2) selected per
+// iteration.  The last window node of an axis is visited only if some lane
+// of the warp moved its nearest node along that axis (warp-uniform branch):
+// for the common case of no node change this is 54 values instead of 144.
+template <int P, class G>
+__device__ __forceinline__ void deposit3_smem(const Axis<P> *ax, float S, int *Jhi, int *Jlo)
+{
+    constexpr int W = P + 2;
+    const float twelfth = 1.f / 12.f;
+    const unsigned act = __activemask();
+    const bool f0 = __any_sync(act, ax[0].shift != 0), f1 = __any_sync(act, ax[1].shift != 0),
+               f2 = __any_sync(act, ax[2].shift != 0);
+    const int base = (ax[0].wb + G::JHX) + G::JX * ((ax[1].wb + G::JHY) + G::JY * (ax[2].wb + G::JHZ));
+    constexpr int s0 = 1, s1 = G::JX, s2 = G::JX * G::JY;
+#pragma unroll 1
+    for (int comp = 0; comp < 3; ++comp) {
+        float pa[W - 1], Ab[W], Db[W], Ac[W], Dc[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            if (q < W - 1)
+                pa[q] = S * (comp == 0 ? ax[0].Pre[q] : (comp == 1 ? ax[1].Pre[q] : ax[2].Pre[q]));
+            Ab[q] = comp == 0 ? ax[1].A[q] : (comp == 1 ? ax[2].A[q] : ax[0].A[q]);
+            Db[q] = comp == 0 ? ax[1].DS[q] : (comp == 1 ? ax[2].DS[q] : ax[0].DS[q]);
+            Ac[q] = comp == 0 ? ax[2].A[q] : (comp == 1 ? ax[0].A[q] : ax[1].A[q]);
+            Dc[q] = comp == 0 ? ax[2].DS[q] : (comp == 1 ? ax[0].DS[q] : ax[1].DS[q]);
+        }
+        const int sa = comp == 0 ? s0 : (comp == 1 ? s1 : s2);
+        const int sb = comp == 0 ? s1 : (comp == 1 ? s2 : s0);
+        const int sc = comp == 0 ? s2 : (comp == 1 ? s0 : s1);
+        const bool fa = comp == 0 ? f0 : (comp == 1 ? f1 : f2);
+        const bool fb = comp == 0 ? f1 : (comp == 1 ? f2 : f0);
+        const bool fc = comp == 0 ? f2 : (comp == 1 ? f0 : f1);
+        int *hb = Jhi + comp * G::JVOL + base, *lb = Jlo + comp * G::JVOL + base;
+#pragma unroll
+        for (int qc = 0; qc < W; ++qc) {
+            if (qc == W - 1 && !fc) continue;
+#pragma unroll
+            for (int qb = 0; qb < W; ++qb) {
+                if (qb == W - 1 && !fb) continue;
+                const float fac = fmaf(Db[qb] * twelfth, Dc[qc], Ab[qb] * Ac[qc]);
+                const int row = qb * sb + qc * sc;
+#pragma unroll
+                for (int qa = 0; qa < W - 1; ++qa) {
+                    if (qa == W - 2 && !fa) continue;
+                    fix_add(hb, lb, row + qa * sa, pa[qa], fac);
+                }
+            }
+        }
+    }
+}
+
+// 2D Esirkepov deposit into the shared-memory J tile, same skipping rule.
+template <int P, class G>
+__device__ __forceinline__ void deposit2_smem(const Axis<P> *ax, float S, float qwvz, int *Jhi, int *Jlo)
+{
+    constexpr int W = P + 2;
+    const float twelfth = 1.f / 12.f;
+    const unsigned act = __activemask();
+    const bool f0 = __any_sync(act, ax[0].shift != 0), f1 = __any_sync(act, ax[1].shift != 0);
+    const int base = (ax[0].wb + G::JHX) + G::JX * (ax[1].wb + G::JHY);
+    float px[W - 1], py[W - 1];
+#pragma unroll
+    for (int q = 0; q < W - 1; ++q) {
+        px[q] = S * ax[0].Pre[q];
+        py[q] = S * ax[1].Pre[q];
+    }
+    const float sz = S * qwvz;
+#pragma unroll
+    for (int qb = 0; qb < W; ++qb) {
+        if (qb == W - 1 && !f1) continue;
+#pragma unroll
+        for (int qa = 0; qa < W; ++qa) {
+            if (qa == W - 1 && !f0) continue;
+            const int off = qa + G::JX * qb;
+            if (qa < W - 1 && !(qa == W - 2 && !f0)) fix_add(Jhi + base, Jlo + base, off, px[qa], ax[1].A[qb]);
+            if (qb < W - 1 && !(qb == W - 2 && !f1))
+                fix_add(Jhi + G::JVOL + base, Jlo + G::JVOL + base, off, py[qb], ax[0].A[qa]);
+            fix_add(Jhi + 2 * G::JVOL + base, Jlo + 2 * G::JVOL + base, off, sz,
+                    fmaf(ax[0].DS[qa] * twelfth, ax[1].DS[qb], ax[0].A[qa] * ax[1].A[qb]));
+        }
+    }
+}
+
+template <int DIM, int P>
+struct GlobalGather {
+    GlobalFields g;
+    __device__ __forceinline__ void operator()(const int *bn, const int *bh, const float (*wn)[P + 1],
+                                               const float (*wh)[P + 1], float *e, float *b) const
+    {
+        e[0] = gather_g<DIM, P, 0>(g, bh[0], bn[1], bn[2], wh[0], wn[1], wn[2]);
+        e[1] = gather_g<DIM, P, 1>(g, bn[0], bh[1], bn[2], wn[0], wh[1], wn[2]);
+        e[2] = gather_g<DIM, P, 2>(g, bn[0], bn[1], bh[2], wn[0], wn[1], wh[2]);
+        b[0] = gather_g<DIM, P, 3>(g, bn[0], bh[1], bh[2], wn[0], wh[1], wh[2]);
+        b[1] = gather_g<DIM, P, 4>(g, bh[0], bn[1], bh[2], wh[0], wn[1], wh[2]);
+        b[2] = gather_g<DIM, P, 5>(g, bh[0], bh[1], bn[2], wh[0], wh[1], wn[2]);
+    }
+};
+
+struct ParticleIn {
+    int32_t cell;
+    float off[3];
+    float u[3];
+    float w;
+};
+
+__device__ __forceinline__ void load_particle(const ParticleBuf &pb, int dim, long long i, float w_const,
+                                              ParticleIn &p)
+{
+    p.cell = pb.cell[i];
+    p.off[0] = pb.off[0][i];
+    p.off[1] = pb.off[1][i];
+    p.off[2] = dim == 3 ? pb.off[2][i] : 0.f;
+    p.u[0] = pb.u[0][i];
+    p.u[1] = pb.u[1][i];
+    p.u[2] = pb.u[2][i];
+    p.w = pb.w ? pb.w[i] : w_const;
+}
+
+struct SlowOut {
+    float d[3], u[3];
+    int k[3];
+    int ok;
+};
+
+// Slow path, kept out of line so that the staged fast path gets the
+// registers; arguments by value so that no fast-path variable has its
+// address taken.
+template <int DIM, int P>
+__device__ __noinline__ SlowOut advance_global(const Run &r, const GlobalFields gf, int c0, int c1, int c2, float e0,
+                                               float e1, float e2, float u0, float u1, float u2, float w)
+{
+    SlowOut o;
+    const int c[3] = {c0, c1, c2};
+    float d[3] = {e0, e1, e2}, u[3] = {u0, u1, u2};
+    int k[3] = {0, 0, 0};
+    float d1[3] = {0.f, 0.f, 0.f}, ig;
+    const GlobalGather<DIM, P> gather{gf};
+    o.ok = push_move<DIM, P>(r, gather, c, d, u, d1, k, ig);
+    if (!o.ok) return o;
+    const float qw = r.q * w;
+    Axis<P> ax[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) axis_window<P>(c[a], d[a], k[a], d1[a], -qw * r.d_over_dt[a], ax[a]);
+    float *J[3] = {r.J[0], r.J[1], r.J[2]};
+    const int n0 = gf.n0, n1 = gf.n1, n2 = gf.n2;
+    esirkepov<DIM, P>(ax, qw * u[2] * ig, [&](int comp, int qa, int qb, int qc, float v) {
+        if (v == 0.f) return;
+        const int x = wrapi(ax[0].wb + qa, n0), y = wrapi(ax[1].wb + qb, n1);
+        const int z = DIM == 3 ? wrapi(ax[DIM - 1].wb + qc, n2) : 0;
+        atomicAdd(J[comp] + x + n0 * (y + n1 * z), v);
+    });
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        o.d[a] = d1[a];
+        o.u[a] = u[a];
+        o.k[a] = k[a];
+    }
+    return o;
+}
+
+template <int DIM, int P, int TX, int TY, int TZ, int D>
+__global__ void __launch_bounds__(512) push_kernel(const Run *__restrict__ runs, const Item *__restrict__ items,
+                                                   int tail_block)
+{
+    using G = Geo<DIM, P, TX, TY, TZ, D>;
+    extern __shared__ __align__(16) float smem[];
+    __shared__ Run rs;
+    __shared__ unsigned slow_cnt;
+    __shared__ float wsum[32];
+    const Item it = items[blockIdx.x];
+    {
+        const int *src = reinterpret_cast<const int *>(runs + it.run);
+        int *dst = reinterpret_cast<int *>(&rs);
+        for (int q = threadIdx.x; q < (int)(sizeof(Run) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
+        if (threadIdx.x == 0) slow_cnt = 0;
+    }
+    __syncthreads();
+    const Run &r = rs;
+    RunState *stp = r.state;
+    const int origin = stp->origin;
+    const long long n_sorted = stp->n_sorted, n_total = stp->n_total;
+    const ParticleBuf pb = r.P[stp->buf];
+    const int n0 = r.n[0], n1 = r.n[1], n2 = DIM == 3 ? r.n[2] : 1;
+    const int nl = r.n[DIM - 1];
+    const bool tile_item = it.kind == 0;
+
+    long long p0, p1;
+    int org[3] = {0, 0, 0};
+    if (tile_item) {
+        const int t = it.a;
+        p0 = r.tile_off[t];
+        p1 = r.tile_off[t + 1];
+        org[0] = (t % r.nt[0]) * TX;
+        org[1] = ((t / r.nt[0]) % r.nt[1]) * TY;
+        if (DIM == 3) org[2] = (t / (r.nt[0] * r.nt[1])) * TZ;
+    } else {
+        p0 = n_sorted + (long long)it.a * tail_block;
+        p1 = p0 + tail_block < n_total ? p0 + tail_block : n_total;
+    }
+    if (p0 >= p1) return;
+
+    float *Fs = smem;
+    int *Jhi = reinterpret_cast<int *>(smem + 6 * G::FVOL);
+    int *Jlo = Jhi + 3 * G::JVOL;
+    float S = 1.f;  // fixed-point scale of this tile's J
+    if (tile_item) {
+        for (int l = threadIdx.x; l < G::FVOL; l += blockDim.x) {
+            const int lx = l % G::FX, ly = (l / G::FX) % G::FY, lz = l / (G::FX * G::FY);
+            const int gx = modi(org[0] - G::FHX + lx, n0);
+            const int gy = modi(org[1] - G::FHY + ly, n1);
+            const int gz = DIM == 3 ? modi(org[2] - G::FHZ + lz, n2) : 0;
+            const int g = gx + n0 * (gy + n1 * gz);
+            float v[6];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                v[c] = __ldg(r.E[c] + g);
+                v[3 + c] = __ldg(r.B[c] + g);
+            }
+#pragma unroll
+            for (int c = 0; c < 6; ++c) Fs[c * G::FVOL + l] = v[c];
+        }
+        for (int q = threadIdx.x; q < 6 * G::JVOL; q += blockDim.x) Jhi[q] = 0;
+        // scale bound: sum of |q w| over the tile's particles
+        float wtot;
+        if (pb.w) {
+            float acc = 0.f;
+            for (long long i = p0 + threadIdx.x; i < p1; i += blockDim.x) acc += fabsf(pb.w[i]);
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
+            __syncthreads();
+            wtot = 0.f;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) wtot += wsum[q];
+        } else {
+            wtot = fabsf(r.w_const) * (float)(p1 - p0);
+        }
+        const float B = 1.01f * fabsf(r.q) * wtot;
+        S = B > 0.f ? 1073741824.f / B : 1.f;
+        __syncthreads();
+    }
+
+    const GlobalFields gf{{r.E[0], r.E[1], r.E[2], r.B[0], r.B[1], r.B[2]}, n0, n1, n2};
+    const SmemGather<DIM, P, G> sgather{Fs};
+    unsigned my_slow = 0;
+    const int D_ = D;
+
+    long long i = p0 + threadIdx.x;
+    ParticleIn cur, nxt;
+    if (i < p1) load_particle(pb, DIM, i, r.w_const, cur);
+    for (; i < p1; i += blockDim.x) {
+        const long long inext = i + blockDim.x;
+        if (inext < p1) load_particle(pb, DIM, inext, r.w_const, nxt);
+        const int32_t pc = cur.cell;
+        if (pc >= 0) {
+            int c[3];
+            unpack_cell(r, pc, c[0], c[1], c[2]);
+            bool keep = true;
+            if (r.open_last) {
+                int pl = c[DIM - 1] - origin;
+                pl = pl < 0 ? pl + nl : pl;
+                keep = pl >= r.margin && pl < nl - r.margin;  // else: left the window, absorbed
+            }
+            if (!keep) {
+                pb.cell[i] = -1;
+            } else {
+                float d[3] = {cur.off[0], cur.off[1], cur.off[2]};
+                float u[3] = {cur.u[0], cur.u[1], cur.u[2]};
+                bool fast = tile_item;
+                int rel[3] = {0, 0, 0};
+                if (tile_item) {
+#pragma unroll
+                    for (int a = 0; a < DIM; ++a) {
+                        int v = c[a] - org[a];
+                        if (v < -D_) v += r.n[a];
+                        else if (v >= G::tile(a) + D_) v -= r.n[a];
+                        rel[a] = v;
+                        fast = fast && v >= -D_ && v < G::tile(a) + D_;
+                    }
+                }
+                int k[3] = {0, 0, 0};
+                bool ok;
+                if (fast) {
+                    float d1[3] = {0.f, 0.f, 0.f}, ig;
+                    ok = push_move<DIM, P>(r, sgather, rel, d, u, d1, k, ig);
+                    if (ok) {
+                        const float qw = r.q * cur.w;
+                        Axis<P> ax[DIM];
+#pragma unroll
+                        for (int a = 0; a < DIM; ++a)
+                            axis_window<P>(rel[a], d[a], k[a], d1[a], -qw * r.d_over_dt[a], ax[a]);
+                        if (DIM == 3) deposit3_smem<P, G>(reinterpret_cast<const Axis<P> *>(ax), S, Jhi, Jlo);
+                        else deposit2_smem<P, G>(reinterpret_cast<const Axis<P> *>(ax), S, qw * u[2] * ig, Jhi, Jlo);
+#pragma unroll
+                        for (int a = 0; a < DIM; ++a) d[a] = d1[a];
+                    }
+                } else {
+                    ++my_slow;
+                    const SlowOut so = advance_global<DIM, P>(r, gf, c[0], c[1], c[2], d[0], d[1], d[2], u[0], u[1],
+                                                              u[2], cur.w);
+                    ok = so.ok != 0;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        d[a] = so.d[a];
+                        u[a] = so.u[a];
+                        k[a] = so.k[a];
+                    }
+                }
+                if (!ok) {  // non-finite or over-long move: drop the particle, latch the status
+                    pb.cell[i] = -1;
+                    atomicOr(&stp->status, kStatusBadIndex);
+                } else {
+                    bool absorbed = false;
+#pragma unroll
+                    for (int a = 0; a < DIM; ++a) c[a] = wrapi(c[a] + k[a], r.n[a]);
+                    if (r.open_last) {
+                        int pl = c[DIM - 1] - origin;
+                        pl = pl < 0 ? pl + nl : pl;
+                        absorbed = pl < r.margin || pl >= nl - r.margin;
+                    }
+                    pb.cell[i] = absorbed ? -1 : pack_cell(r, c[0], c[1], DIM == 3 ? c[2] : 0);
+#pragma unroll
+                    for (int a = 0; a < DIM; ++a) pb.off[a][i] = d[a];
+                    pb.u[0][i] = u[0];
+                    pb.u[1][i] = u[1];
+                    pb.u[2][i] = u[2];
+                }
+            }
+        }
+        cur = nxt;
+    }
+    if (my_slow) atomicAdd(&slow_cnt, my_slow);
+    __syncthreads();
+    if (tile_item) {
+        // flush the tile's current to global J (wrapping the halo)
+        const float inv = 1.f / S, inv_lo = inv * (1.f / kLoScale);
+        for (int l = threadIdx.x; l < G::JVOL; l += blockDim.x) {
+            int hi[3], lo[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                hi[c] = Jhi[c * G::JVOL + l];
+                lo[c] = Jlo[c * G::JVOL + l];
+            }
+            if (((hi[0] | lo[0]) | (hi[1] | lo[1]) | (hi[2] | lo[2])) == 0) continue;
+            const int lx = l % G::JX, ly = (l / G::JX) % G::JY, lz = l / (G::JX * G::JY);
+            const int gx = modi(org[0] - G::JHX + lx, n0);
+            const int gy = modi(org[1] - G::JHY + ly, n1);
+            const int gz = DIM == 3 ? modi(org[2] - G::JHZ + lz, n2) : 0;
+            const int g = gx + n0 * (gy + n1 * gz);
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                if (hi[c] | lo[c]) atomicAdd(r.J[c] + g, fmaf((float)lo[c], inv_lo, (float)hi[c] * inv));
+        }
+    }
+    if (threadIdx.x == 0 && slow_cnt) atomicAdd(&stp->slow, (unsigned long long)slow_cnt);
+}
+
+template <int DIM, int P, int TX, int TY, int TZ, int D>
+cudaError_t launch_t(const Run *runs, const Item *items, int nitems, int block, int tail_block, cudaStream_t st)
+{
+    using G = Geo<DIM, P, TX, TY, TZ, D>;
+    auto k = push_kernel<DIM, P, TX, TY, TZ, D>;
+    static bool attr_set = false;  // raise the opt-in shared-memory limit once
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (nitems == 0) return cudaSuccess;
+    k<<<nitems, block, G::SMEM, st>>>(runs, items, tail_block);
+    return cudaGetLastError();
+}
+
+}  // namespace push_detail
+}  // namespace pic

@@ -119,8 +119,9 @@ def test_sort_interval_and_drift_do_not_change_results():
     w.uth = 0.1
     parts = inputs.background(w)
     runs = []
-    for tuning in ({"sort_interval": 1, "drift": 0}, {"sort_interval": 7, "drift": 3},
-                   {"sort_interval": 5, "drift": 0, "tile": (8, 8)}, {"use_graph": 0}):
+    for tuning in ({"sort_interval": 1, "drift": 1}, {"sort_interval": 7, "drift": 3},
+                   {"sort_interval": 5, "tile": (8, 8)}, {"sort_interval": 3, "tile": (32, 32)},
+                   {"use_graph": 0}):
         gpu, _ = pair(w, parts, tuning=tuning)
         gpu.step(w.steps)
         runs.append({n: gpu.field(n) for n in FIELD_NAMES})
