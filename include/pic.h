@@ -260,6 +260,33 @@ PIC_API int pic_diagnostics(pic_t *h, pic_diag *out);
 PIC_API int pic_profile_begin(pic_t *h, int32_t max_steps);
 PIC_API int pic_profile_end(pic_t *h, double *ms, int32_t n_phases, int64_t *launches);
 
+/* Charge density without any device allocation, for callers that cannot
+ * allocate device memory (a host framework that passes the library only its
+ * own buffers, a memory budget that forbids new allocations, a loop that
+ * must not allocate once running).  The paper has no counterpart; it is the
+ * same charge density as pic_read_fields(PIC_RHO),
+ * rho(node) = sum q w S(x - node) with periodic wrap on every axis, computed
+ * for the n particles given here.
+ *   grid: dim, n (cells per axis; d, dt and bc_last are ignored);
+ *   cell[dim][n] (int32), off[dim][n] (FP32 in [0,1)), w[n] (FP32, or NULL
+ *   to use w_const for every particle) and rho[n0*n1*n2] (FP32 output) are
+ *   device pointers owned by the caller; stream is a cudaStream_t (NULL =
+ *   default stream); the call is asynchronous on it.
+ * The FP64 accumulation grid is a static device array of PIC_STATIC_MAX_CELLS
+ * cells (16 MiB), held by every GPU that loads the library until the
+ * process exits; larger grids return PIC_EINVAL.  It is cleared at the start
+ * of every call.  All calls on a device share the array, so calls that
+ * overlap on the GPU (different streams, threads or handles) race and must
+ * be ordered by the caller.  The first call on a device looks up the
+ * array's device address (with that device current), so make that first
+ * call before any CUDA stream capture.  No cudaMalloc, cudaFree or other
+ * allocating routine is called.  Errors: PIC_EINVAL (arguments, grid too
+ * large), PIC_ECUDA (launch failure). */
+#define PIC_STATIC_MAX_CELLS (1ll << 21)
+PIC_API int pic_charge_density_static(const pic_grid *grid, int32_t shape_order, double q, double w_const,
+                                      int64_t n, const int32_t *cell, const float *off, const float *w, float *rho,
+                                      void *stream);
+
 /* Release everything (waits for the stream first).  NULL is ignored. */
 PIC_API void pic_destroy(pic_t *h);
 

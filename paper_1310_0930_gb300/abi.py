@@ -83,7 +83,10 @@ SIGNATURES = {
     "pic_strerror": (ctypes.c_char_p, [c_int32]),
     "pic_profile_begin": (c_int32, [_handle, c_int32]),
     "pic_profile_end": (c_int32, [_handle, _P(c_double), c_int32, _P(c_int64)]),
+    "pic_charge_density_static": (c_int32, [_P(pic_grid), c_int32, c_double, c_double, c_int64, c_void_p, c_void_p,
+                                            c_void_p, c_void_p, c_void_p]),
 }
+PIC_STATIC_MAX_CELLS = 1 << 21
 
 PHASES = ["sort", "zero_j", "push", "yee_b1", "yee_e", "yee_b2", "window"]
 

@@ -116,3 +116,19 @@ def test_null_handles_and_strerror():
     for code in (0, -1, -2, -3, -4, -5, -6):
         assert abi.pic_strerror(code)
     assert abi.pic_strerror(-77) == "unknown status"
+
+
+def test_static_charge_entry_point_rejects_oversized_grid_without_device_work():
+    L = abi.lib()
+    g = abi.pic_grid()
+    g.dim = 3
+    g.n[0], g.n[1], g.n[2] = 256, 128, 65  # 2,129,920 cells > PIC_STATIC_MAX_CELLS
+    assert 256 * 128 * 65 > abi.PIC_STATIC_MAX_CELLS
+    dummy = ctypes.c_void_p(16)
+    rc = L.pic_charge_density_static(ctypes.byref(g), 2, -1.0, 1.0, 10, dummy, dummy, None, dummy, None)
+    assert rc == abi.PIC_EINVAL
+    g.n[2] = 64  # exactly the limit passes validation (not run here: no device)
+    assert 256 * 128 * 64 == abi.PIC_STATIC_MAX_CELLS
+    g.dim = 4
+    assert L.pic_charge_density_static(ctypes.byref(g), 2, -1.0, 1.0, 10, dummy, dummy, None, dummy, None) == \
+        abi.PIC_EINVAL
