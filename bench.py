@@ -39,7 +39,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="lwfa_3d", choices=["lwfa_3d", "thermal_2d", "bunch_3d"])
+    ap.add_argument("--workload", default="lwfa_3d", choices=["lwfa_3d", "thermal_2d", "bunch_3d", "scan_2d"])
+    ap.add_argument("--scan-runs", type=int, default=64)
+    ap.add_argument("--autotune", action="store_true", help="choose the tuning with the autotuner first")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink every grid axis (debug runs only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -182,6 +184,77 @@ def cpu_baseline(w, budget_s, steps_hint=None):
                       "%d steps, %.1f s" % (w.name, "x".join(map(str, ncrop)), n, steps, dt_s)}
 
 
+def scan_bench(args):
+    """Batched parameter scan: 64 uneven 2D LWFA runs advanced by one handle
+    (one launch per phase over every run's tiles, persistent push kernel,
+    CUDA-graph replay) against the same runs advanced one after another by
+    plain single-run handles.  Same K timed steps per run in both."""
+    import torch
+    from paper_1310_0930_gb300 import autotune, inputs
+    from paper_1310_0930_gb300.sim import Simulation, TorchMemory
+
+    torch.cuda.set_device(0)
+    runs = inputs.scan_2d(count=args.scan_runs)
+    parts = [inputs.background(w) for w in runs]
+    n_total = sum(p.n for p in parts)
+    cells = sum(w.n_cells for w in runs)
+    tuning = json.loads(args.tuning) if args.tuning else {}
+    if args.autotune:
+        sub = list(range(min(8, len(runs))))
+
+        def loader(sim):
+            for i, r in enumerate(sub):
+                sim.select(i)
+                sim.load(parts[r])
+            return sum(parts[r].n for r in sub)
+        tuning = autotune.tune([runs[r] for r in sub], loader, refresh=True)
+
+    def timed(sim, n_steps):
+        st = sim.mem.stream
+        sim.step(args.warmup)
+        sim.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        sim.step(n_steps)
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    batch = Simulation(runs, tuning=tuning, memory=TorchMemory())
+    for r, p in enumerate(parts):
+        batch.select(r)
+        batch.load(p)
+    clocks = Clocks(0)
+    ms_b = timed(batch, args.steps)
+    clk = clocks.stop()
+    batch.close()
+    del batch
+    single_tuning = {k: v for k, v in tuning.items() if k != "persistent"}
+    ms_s = 0.0
+    for w, p in zip(runs, parts):
+        sim = Simulation(w, tuning=single_tuning, memory=TorchMemory())
+        sim.load(p)
+        ms_s += timed(sim, args.steps)
+        sim.close()
+    value = n_total * args.steps / (ms_b / 1e3)
+    seq = n_total * args.steps / (ms_s / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_b / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "scan_2d: %d independent 2D LWFA runs (nz 256-2048 x nx 128-512, dz=0.3, "
+                                   "dx=1, dt=0.28, 4-16 ppc, n 0.001-0.01, a0 1-6), quadratic" % len(runs),
+                       "runs": len(runs), "particles": n_total, "cells": cells, "tuning": tuning},
+            "batched": {"value": value, "ms_per_step": ms_b / args.steps},
+            "sequential_plain": {"value": seq, "ms_per_step": ms_s / args.steps},
+            "batched_over_sequential": value / seq, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    if args.out:
+        with open(args.out, "w") as f:
+            f.write(json.dumps(line) + "\n")
+    return 0
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -203,6 +276,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "scan_2d":
+        return scan_bench(args)
     import torch
     import torch.distributed as dist
 

@@ -145,7 +145,10 @@ typedef void (*pic_free_fn)(void *ptr, void *ctx);
 /* Tuning: tile[a] cells per tile per axis (powers of two, 0 = default);
  * sort_interval steps between tile sorts (0 = default); drift: cells a
  * particle may stray outside its tile between sorts and still use the
- * staged fast path (-1 = default); block: threads per tile CTA (0 = default).
+ * staged fast path (-1 = default); block: threads per tile CTA (0 = default);
+ * persistent: 0 = default (persistent for batches, one CTA per tile
+ * otherwise), 1 = one persistent grid whose CTAs take tiles from a device
+ * work queue, largest runs first, 2 = one CTA per tile.
  * Compiled (tile, drift) pairs: 2D 16x16 with drift 1, 2 (default) or 3,
  * 8x8 with 1, 32x32 with 2; 3D 8x8x8 with 1 (default) or 2; any other pair
  * is PIC_EINVAL.
@@ -156,7 +159,7 @@ typedef struct {
     int32_t drift;
     int32_t block;
     int32_t use_graph;
-    int32_t reserved;
+    int32_t persistent;
 } pic_tuning;
 
 typedef struct {

@@ -25,8 +25,10 @@ constexpr int kBlock = 256;
 // push_smem_bytes returns 0 for a (tile, drift) pair that is not compiled.
 int push_default_drift(int dim, const int *tile);
 size_t push_smem_bytes(int dim, int order, const int *tile, int drift);
+// queue != nullptr: persistent grid of persistent_ctas x (CTAs per SM) taking
+// items from the device counter *queue (reset by the launch).
 cudaError_t launch_push(int dim, int order, const int *tile, int drift, const Run *runs, const Item *items,
-                        int nitems, int block, int tail_block, cudaStream_t st);
+                        int nitems, int block, int tail_block, int *queue, int persistent_ctas, cudaStream_t st);
 
 // fields.cu
 cudaError_t launch_zero_j(const Run *runs, Seg cells, cudaStream_t st);

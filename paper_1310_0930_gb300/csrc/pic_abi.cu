@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -54,6 +55,9 @@ struct pic_s {
     int max_tiles = 0;
     double *d_diag = nullptr;
     unsigned long long *d_count = nullptr;
+    int *d_queue = nullptr;  // work-queue counter of the persistent push kernel
+    bool persistent = false;
+    int num_sms = 1;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     // phase profiling: events[step][PIC_NUM_PHASES + 1]
     std::vector<cudaEvent_t> prof_events;
@@ -147,6 +151,7 @@ int validate(const pic_config *c)
     if (t.drift < -1 || t.drift > 8) return PIC_EINVAL;
     if (t.block != 0 && t.block != 128 && t.block != 256 && t.block != 512) return PIC_EINVAL;
     if (t.sort_interval < 0) return PIC_EINVAL;
+    if (t.persistent < 0 || t.persistent > 2) return PIC_EINVAL;
     return PIC_OK;
 }
 
@@ -241,18 +246,31 @@ int read_state(pic_s *h, int run, RunState *out)
     return cuda_fail(e);
 }
 
+// Work items of the push kernel, largest expected cost first (the order in
+// which the hardware or the persistent work queue hands them out): the
+// slow-path tail blocks, then the tiles of runs with more particles per
+// cell, then the rest.
 int build_items(pic_s *h)
 {
     std::vector<Item> items;
-    int tail_blocks = 0;
     for (int i = 0; i < h->nruns; ++i) {
         const HostRun &hr = h->runs[i];
-        for (int t = 0; t < hr.r.ntiles; ++t) items.push_back(Item{i, 0, t, 0});
         if (hr.inject_per_shift > 0) {
             long long max_tail = (long long)(h->sort_interval + 1) * hr.inject_per_shift;
-            tail_blocks = (int)((max_tail + kTail - 1) / kTail);
+            int tail_blocks = (int)((max_tail + kTail - 1) / kTail);
             for (int b = 0; b < tail_blocks; ++b) items.push_back(Item{i, 1, b, 0});
         }
+    }
+    std::vector<int> order(h->nruns);
+    for (int i = 0; i < h->nruns; ++i) order[i] = i;
+    auto load = [&](int i) {
+        const Run &r = h->runs[i].r;
+        return (long double)(r.capacity > 0 ? r.capacity : 1) / (long double)(r.ntiles > 0 ? r.ntiles : 1);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return load(a) > load(b); });
+    for (int i : order) {
+        const HostRun &hr = h->runs[i];
+        for (int t = 0; t < hr.r.ntiles; ++t) items.push_back(Item{i, 0, t, 0});
     }
     if (h->d_items) dev_free(h, h->d_items);
     h->d_items = (Item *)dev_alloc(h, sizeof(Item) * (items.size() ? items.size() : 1));
@@ -280,7 +298,8 @@ int enqueue_step(pic_s *h, bool sort)
     if (e == cudaSuccess) e = launch_zero_j(R, h->seg_cells, st);
     mark(PIC_PH_PUSH);
     if (e == cudaSuccess)
-        e = launch_push(h->dim, h->order, h->tile, h->drift, R, h->d_items, h->n_items, h->block, kTail, st);
+        e = launch_push(h->dim, h->order, h->tile, h->drift, R, h->d_items, h->n_items, h->block, kTail,
+                        h->persistent ? h->d_queue : nullptr, h->num_sms, st);
     mark(PIC_PH_YEE_B1);
     if (e == cudaSuccess) e = launch_yee_b(h->dim, R, h->seg_cells, 0, st);
     mark(PIC_PH_YEE_E);
@@ -327,7 +346,8 @@ int first_step_setup(pic_s *h)
     }
     // sets the push kernel's shared-memory limit outside any graph capture
     cudaError_t e =
-        launch_push(h->dim, h->order, h->tile, h->drift, h->d_runs, h->d_items, 0, h->block, kTail, h->stream);
+        launch_push(h->dim, h->order, h->tile, h->drift, h->d_runs, h->d_items, 0, h->block, kTail, nullptr, 1,
+                    h->stream);
     if (e != cudaSuccess) return PIC_ECUDA;
     h->started = true;
     return PIC_OK;
@@ -453,6 +473,7 @@ int create_common(const pic_config *cfgs, int n, pic_t **out)
     h->block = t.block ? t.block : (h->dim == 3 ? 512 : 256);
     h->sort_interval = t.sort_interval ? t.sort_interval : 4;
     h->use_graph = t.use_graph != 0 && h->stream != nullptr;
+    h->persistent = t.persistent == 1 || (t.persistent == 0 && n > 1);
     h->push_smem = push_smem_bytes(h->dim, h->order, h->tile, h->drift);
     if (h->push_smem == 0) {  // (tile, drift) not among the compiled configurations
         delete h;
@@ -475,7 +496,9 @@ int create_common(const pic_config *cfgs, int n, pic_t **out)
     h->d_seg = (int *)dev_alloc(h, sizeof(int) * 4 * (n + 1));
     h->d_diag = (double *)dev_alloc(h, sizeof(double) * 16);
     h->d_count = (unsigned long long *)dev_alloc(h, sizeof(unsigned long long));
-    if (!h->d_runs || !h->d_states || !h->d_seg || !h->d_diag || !h->d_count) {
+    h->d_queue = (int *)dev_alloc(h, sizeof(int));
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (!h->d_runs || !h->d_states || !h->d_seg || !h->d_diag || !h->d_count || !h->d_queue) {
         pic_destroy(h);
         return PIC_ENOMEM;
     }

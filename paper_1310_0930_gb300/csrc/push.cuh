@@ -448,16 +448,16 @@ __device__ __noinline__ SlowOut advance_global(const Run &r, const GlobalFields 
     return o;
 }
 
+// One work item: a tile of one run (staged fast path) or a block of that
+// run's unsorted tail (slow path).  Called uniformly by the whole CTA.
 template <int DIM, int P, int TX, int TY, int TZ, int D>
-__global__ void __launch_bounds__(512) push_kernel(const Run *__restrict__ runs, const Item *__restrict__ items,
-                                                   int tail_block)
+__device__ __forceinline__ void process_item(const Run *__restrict__ runs, const Item it, int tail_block)
 {
     using G = Geo<DIM, P, TX, TY, TZ, D>;
     extern __shared__ __align__(16) float smem[];
     __shared__ Run rs;
     __shared__ unsigned slow_cnt;
     __shared__ float wsum[32];
-    const Item it = items[blockIdx.x];
     {
         const int *src = reinterpret_cast<const int *>(runs + it.run);
         int *dst = reinterpret_cast<int *>(&rs);
@@ -643,8 +643,31 @@ __global__ void __launch_bounds__(512) push_kernel(const Run *__restrict__ runs,
     if (threadIdx.x == 0 && slow_cnt) atomicAdd(&stp->slow, (unsigned long long)slow_cnt);
 }
 
+// One CTA per item (queue == nullptr), or a persistent grid whose CTAs take
+// items from a device work queue (items ordered largest first).
 template <int DIM, int P, int TX, int TY, int TZ, int D>
-cudaError_t launch_t(const Run *runs, const Item *items, int nitems, int block, int tail_block, cudaStream_t st)
+__global__ void __launch_bounds__(512) push_kernel(const Run *__restrict__ runs, const Item *__restrict__ items,
+                                                   int nitems, int tail_block, int *queue)
+{
+    if (queue == nullptr) {
+        process_item<DIM, P, TX, TY, TZ, D>(runs, items[blockIdx.x], tail_block);
+        return;
+    }
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
+        __syncthreads();
+        const int idx = s_item;
+        __syncthreads();
+        if (idx >= nitems) break;
+        process_item<DIM, P, TX, TY, TZ, D>(runs, items[idx], tail_block);
+        __syncthreads();
+    }
+}
+
+template <int DIM, int P, int TX, int TY, int TZ, int D>
+cudaError_t launch_t(const Run *runs, const Item *items, int nitems, int block, int tail_block, int *queue,
+                     int persistent_ctas, cudaStream_t st)
 {
     using G = Geo<DIM, P, TX, TY, TZ, D>;
     auto k = push_kernel<DIM, P, TX, TY, TZ, D>;
@@ -655,7 +678,18 @@ cudaError_t launch_t(const Run *runs, const Item *items, int nitems, int block, 
         attr_set = true;
     }
     if (nitems == 0) return cudaSuccess;
-    k<<<nitems, block, G::SMEM, st>>>(runs, items, tail_block);
+    if (queue) {
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, G::SMEM);
+        if (e != cudaSuccess) return e;
+        int grid = persistent_ctas * (per_sm > 0 ? per_sm : 1);
+        grid = grid < nitems ? grid : nitems;
+        e = cudaMemsetAsync(queue, 0, sizeof(int), st);
+        if (e != cudaSuccess) return e;
+        k<<<grid, block, G::SMEM, st>>>(runs, items, nitems, tail_block, queue);
+    } else {
+        k<<<nitems, block, G::SMEM, st>>>(runs, items, nitems, tail_block, nullptr);
+    }
     return cudaGetLastError();
 }
 

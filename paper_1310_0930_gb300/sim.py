@@ -75,6 +75,7 @@ def make_config(w: Workload, *, tuning: Optional[dict] = None, track_ids=False, 
     cfg.tuning.drift = int(t.get("drift", -1))
     cfg.tuning.block = int(t.get("block", 0))
     cfg.tuning.use_graph = int(t.get("use_graph", 1))
+    cfg.tuning.persistent = int(t.get("persistent", 0))
     if alloc is not None:
         cfg.alloc = alloc
         cfg.free = free
