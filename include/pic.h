@@ -263,6 +263,45 @@ PIC_API int pic_diagnostics(pic_t *h, pic_diag *out);
 PIC_API int pic_profile_begin(pic_t *h, int32_t max_steps);
 PIC_API int pic_profile_end(pic_t *h, double *ms, int32_t n_phases, int64_t *launches);
 
+/* ---- adjoint form --------------------------------------------------------
+ * Gradients of a final-state objective through the timestep, by the
+ * discrete adjoint (reverse mode of the FP32 forward arithmetic) with step
+ * checkpointing and segment recomputation.  Objective (a smooth "trailing
+ * window" of the last axis, positions in window-frame cells):
+ *   L = sum w K sigma / sum w sigma,  K = m (gamma - 1),
+ *   sigma(z) = logistic((z - z_lo)/width) * logistic((z_hi - z)/width).
+ * Requirements: a single run, track_ids = 1, per_particle_weight = 1, no
+ * moving window, particles loaded, no step taken yet. */
+typedef struct {
+    double z_lo, z_hi, width;
+} pic_objective;
+
+/* Arm the reverse mode for a forward run of total_steps steps: allocates the
+ * adjoint arrays, ceil(total/checkpoint_every) checkpoints (particle state and
+ * E, B) and one segment of per-step records; the following pic_step calls
+ * save a checkpoint every checkpoint_every steps (steps then run without
+ * graph replay). */
+PIC_API int pic_adjoint_begin(pic_t *h, int32_t total_steps, int32_t checkpoint_every);
+
+/* L of the current state (no adjoint). */
+PIC_API int pic_objective_value(pic_t *h, const pic_objective *obj, double *L);
+
+/* After exactly total_steps forward steps: L, dL/da0 (laser amplitude),
+ * dL/dknots[n_knots] (the piecewise-linear density profile of pic_species:
+ * w = density(z at load) / prod(ppc)) and dL/dw[n] per particle id (host
+ * arrays; any output may be NULL).  The handle is left in a recomputed
+ * intermediate state and cannot be stepped further (PIC_ESTATE). */
+PIC_API int pic_adjoint_backward(pic_t *h, const pic_objective *obj, double *L, double *dL_da0, double *dL_dknots,
+                                 int32_t n_knots, double *dL_dw);
+
+/* Transpose of the field part of one step (B half, E, B half, with the
+ * open-end Mur updates and the antenna) applied in place to
+ * lam[6][n0*n1*n2] = (lamEx, lamEy, lamEz, lamBx, lamBy, lamBz) (host, window
+ * frame); lam_j[3][...] (host, may be NULL) receives the adjoint of the
+ * current.  t is the time at the start of the step.  A building block of
+ * pic_adjoint_backward, exposed for transpose (dot-product) checks. */
+PIC_API int pic_adjoint_fields(pic_t *h, float *lam, float *lam_j, double t);
+
 /* Charge density without any device allocation, for callers that cannot
  * allocate device memory (a host framework that passes the library only its
  * own buffers, a memory budget that forbids new allocations, a loop that

@@ -57,6 +57,10 @@ class pic_config(ctypes.Structure):
                 ("alloc_ctx", c_void_p), ("stream", c_void_p)]
 
 
+class pic_objective(ctypes.Structure):
+    _fields_ = [("z_lo", c_double), ("z_hi", c_double), ("width", c_double)]
+
+
 class pic_diag(ctypes.Structure):
     _fields_ = [("step", c_int64), ("time", c_double), ("shifts", c_int64), ("W_E", c_double), ("W_B", c_double),
                 ("W_kin", c_double), ("gauss_resid", c_double), ("n_particles", c_int64),
@@ -83,6 +87,11 @@ SIGNATURES = {
     "pic_strerror": (ctypes.c_char_p, [c_int32]),
     "pic_profile_begin": (c_int32, [_handle, c_int32]),
     "pic_profile_end": (c_int32, [_handle, _P(c_double), c_int32, _P(c_int64)]),
+    "pic_adjoint_begin": (c_int32, [_handle, c_int32, c_int32]),
+    "pic_objective_value": (c_int32, [_handle, _P(pic_objective), _P(c_double)]),
+    "pic_adjoint_backward": (c_int32, [_handle, _P(pic_objective), _P(c_double), _P(c_double), c_void_p, c_int32,
+                                       c_void_p]),
+    "pic_adjoint_fields": (c_int32, [_handle, c_void_p, c_void_p, c_double]),
     "pic_charge_density_static": (c_int32, [_P(pic_grid), c_int32, c_double, c_double, c_int64, c_void_p, c_void_p,
                                             c_void_p, c_void_p, c_void_p]),
 }

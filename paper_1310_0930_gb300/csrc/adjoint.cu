@@ -1,0 +1,866 @@
+// adjoint.cu -- discrete adjoint of the EM-PIC timestep (reverse mode of
+// exactly the forward arithmetic of push.cuh and fields.cu), for gradients
+// of a scalar objective of the final particle state with respect to the
+// particle weights (hence a density profile) and the laser amplitude a0.
+//
+// Reverse of one step n (forward: push/deposit -> B half -> E -> B half):
+//   (i)   B^{n+1} = B^{n+1/2} - h curl_f E^{n+1} (+ antenna, t^{n+1}):
+//         lamE -= h curl_b(m_B lamB)
+//   (ii)  E^{n+1} = Mur(E^n, E~), E~ = E^n + dt (curl_b B^{n+1/2} - J) (+ antenna):
+//         T = lamE on updated entries (+ Mur terms), lamB += dt curl_f(T),
+//         lamJ = -dt T, lamE <- T on updated entries (+ Mur terms)
+//   (iii) B^{n+1/2} = B^n - h curl_f E^n (+ antenna, t^n): as (i)
+//   (iv)  particles: deposit transpose = gather of lamJ with the shape
+//         derivatives; move, Boris and gather transposes; gather transpose
+//         scatters into lamE, lamB.
+// curl_b (backward differences) is the transpose of curl_f (forward
+// differences) on the staggered grid; m_B masks the B entries the forward
+// leaves frozen beyond an open end.  Particle adjoints live in arrays indexed
+// by particle id, so the tile sort between steps does not matter.
+#include <cstdint>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace pic {
+namespace {
+
+__device__ double laser_unit(const Run &r, double r2, double xi)
+{
+    // antenna field for a0 = 1 (the forward field is linear in a0)
+    double dx = xi - r.t_peak;
+    double env = exp(-2.0 * 0.69314718055994530942 * dx * dx / (r.fwhm * r.fwhm));
+    return exp(-r2 / (r.waist * r.waist)) * env * cos(r.omega0 * dx);
+}
+
+__device__ double laser_r2_adj(const Run &r, int i, int j)
+{
+    const int last = r.dim - 1;
+    double r2 = 0.0;
+    int idx[2] = {i, j};
+    for (int a = 0; a < last; ++a) {
+        double off = (a == r.laser_pol) ? 0.5 : 0.0;
+        double pos = ((double)idx[a] + off) * r.dd[a];
+        double ctr = 0.5 * r.n[a] * r.dd[a];
+        r2 += (pos - ctr) * (pos - ctr);
+    }
+    return r2;
+}
+
+__device__ __forceinline__ double block_reduce(double v, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (wid == 0) {
+        t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    }
+    __syncthreads();
+    return t;
+}
+
+// B entries frozen by the forward beyond an open end (half-integer
+// positions on the last axis at physical index nl-1).
+template <int DIM>
+__device__ __forceinline__ bool b_frozen(const Run &r, int comp, int il)
+{
+    if (!r.open_last || il != r.n[DIM - 1] - 1) return false;
+    return DIM == 3 ? comp != 2 : comp != 1;
+}
+
+// (i)/(iii): lamE -= h curl_b(m_B lamB); antenna: lam_a0 += <lamB, dB/da0>.
+template <int DIM>
+__global__ void adj_b_kernel(const Run *__restrict__ run, AdjPtrs A, int origin, double t_b, int laser_on,
+                             double *la0)
+{
+    const Run &r = *run;
+    __shared__ double sh[32];
+    double acc = 0.0;
+    const int n0 = r.n[0], n1 = r.n[1], n2 = DIM == 3 ? r.n[2] : 1, nl = r.n[DIM - 1];
+    const float h = 0.5f * r.dt;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < r.ncell; idx += gridDim.x * blockDim.x) {
+        const int i = idx % n0, j = (idx / n0) % n1, k = DIM == 3 ? idx / (n0 * n1) : 0;
+        const int mx = (i == 0 ? n0 - 1 : i - 1) + n0 * (j + n1 * k);
+        const int my = i + n0 * ((j == 0 ? n1 - 1 : j - 1) + n1 * k);
+        const int mz = DIM == 3 ? i + n0 * (j + n1 * (k == 0 ? n2 - 1 : k - 1)) : idx;
+        auto il_of = [&](int jj, int kk) {
+            int s = (DIM == 3 ? kk : jj) - origin;
+            return s < 0 ? s + nl : s;
+        };
+        const int il = il_of(j, k);
+        const int il_my = il_of(j == 0 ? n1 - 1 : j - 1, k);
+        const int il_mz = DIM == 3 ? il_of(j, k == 0 ? n2 - 1 : k - 1) : il;
+        auto mb = [&](int comp, int at, int ill) { return b_frozen<DIM>(r, comp, ill) ? 0.f : A.lB[comp][at]; };
+        const float bx = mb(0, idx, il), by = mb(1, idx, il), bz = mb(2, idx, il);
+        const float dBz_dy = (bz - mb(2, my, il_my)) * r.inv_d[1], dBz_dx = (bz - mb(2, mx, il)) * r.inv_d[0];
+        const float dBy_dx = (by - mb(1, mx, il)) * r.inv_d[0], dBx_dy = (bx - mb(0, my, il_my)) * r.inv_d[1];
+        float dBy_dz = 0.f, dBx_dz = 0.f;
+        if (DIM == 3) {
+            dBy_dz = (by - mb(1, mz, il_mz)) * r.inv_d[2];
+            dBx_dz = (bx - mb(0, mz, il_mz)) * r.inv_d[2];
+        }
+        A.lE[0][idx] -= h * (dBz_dy - dBy_dz);
+        A.lE[1][idx] -= h * (dBx_dz - dBz_dx);
+        A.lE[2][idx] -= h * (dBy_dx - dBx_dy);
+        if (laser_on && il == r.laser_plane - 1) {
+            int bcomp;
+            double sgn;
+            if (DIM == 3) {
+                bcomp = r.laser_pol == 0 ? 1 : 0;
+                sgn = r.laser_pol == 0 ? 1.0 : -1.0;
+            } else {
+                bcomp = 2;
+                sgn = -1.0;
+            }
+            acc += (double)A.lB[bcomp][idx] * sgn * (double)h * (double)r.inv_d[DIM - 1] *
+                   laser_unit(r, laser_r2_adj(r, i, j), t_b);
+        }
+    }
+    double t = block_reduce(acc, sh);
+    if (threadIdx.x == 0 && t != 0.0) atomicAdd(la0, t);
+}
+
+// (ii) part 1: T = lamE on entries the E update writes; newE = identity part.
+template <int DIM>
+__global__ void adj_e_mask_kernel(const Run *__restrict__ run, AdjPtrs A, int origin)
+{
+    const Run &r = *run;
+    const int n0 = r.n[0], n1 = r.n[1], nl = r.n[DIM - 1];
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < r.ncell; idx += gridDim.x * blockDim.x) {
+        const int j = (idx / n0) % n1, k = DIM == 3 ? idx / (n0 * n1) : 0;
+        int il = (DIM == 3 ? k : j) - origin;
+        il = il < 0 ? il + nl : il;
+        for (int c = 0; c < 3; ++c) {
+            bool upd = true;
+            if (r.open_last) {
+                const int t1 = DIM == 3 ? 1 : 2, nrm = DIM == 3 ? 2 : 1;
+                if ((c == 0 || c == t1) && (il == 0 || il == nl - 1)) upd = false;  // Mur-set tangential
+                if (c == nrm && il == nl - 1) upd = false;                          // zeroed normal
+            }
+            const float v = upd ? A.lE[c][idx] : 0.f;
+            A.T[c][idx] = v;
+            A.nE[c][idx] = v;
+        }
+    }
+}
+
+// (ii) part 2: the Mur transposes (one thread per transverse position).
+template <int DIM>
+__global__ void adj_mur_kernel(const Run *__restrict__ run, AdjPtrs A, int origin)
+{
+    const Run &r = *run;
+    if (!r.open_last) return;
+    const int nl = r.n[DIM - 1];
+    const int plane = r.ncell / nl;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= plane) return;
+    const float dl = r.d[DIM - 1];
+    const float coef = (r.dt - dl) / (r.dt + dl);
+    auto at = [&](int pl) {
+        int st = pl + origin;
+        st = st >= nl ? st - nl : st;
+        return q + plane * st;
+    };
+    const int tc[2] = {0, DIM == 3 ? 1 : 2};
+    for (int t = 0; t < 2; ++t) {
+        const int c = tc[t];
+        const int c0 = at(0), c1 = at(1), cm = at(nl - 1), cm1 = at(nl - 2);
+        // F0 = o1 + coef (F1 - o0);  Fm = om1 + coef (Fm1 - om)
+        const float l0 = A.lE[c][c0], lm = A.lE[c][cm];
+        A.T[c][c1] += coef * l0;
+        A.nE[c][c1] += coef * l0 + l0;
+        A.nE[c][c0] = -coef * l0;
+        A.T[c][cm1] += coef * lm;
+        A.nE[c][cm1] += coef * lm + lm;
+        A.nE[c][cm] = -coef * lm;
+    }
+}
+
+// (ii) part 3: lamB += dt curl_f(T); lamJ = -dt T; antenna a0 term.
+template <int DIM>
+__global__ void adj_e_curl_kernel(const Run *__restrict__ run, AdjPtrs A, int origin, double t_n, int laser_on,
+                                  double *la0)
+{
+    const Run &r = *run;
+    __shared__ double sh[32];
+    double acc = 0.0;
+    const int n0 = r.n[0], n1 = r.n[1], n2 = DIM == 3 ? r.n[2] : 1, nl = r.n[DIM - 1];
+    const float dt = r.dt;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < r.ncell; idx += gridDim.x * blockDim.x) {
+        const int i = idx % n0, j = (idx / n0) % n1, k = DIM == 3 ? idx / (n0 * n1) : 0;
+        const int cx = (i + 1 == n0 ? 0 : i + 1) + n0 * (j + n1 * k);
+        const int cy = i + n0 * ((j + 1 == n1 ? 0 : j + 1) + n1 * k);
+        const float tx = A.T[0][idx], ty = A.T[1][idx], tz = A.T[2][idx];
+        const float dTz_dy = (A.T[2][cy] - tz) * r.inv_d[1], dTz_dx = (A.T[2][cx] - tz) * r.inv_d[0];
+        const float dTy_dx = (A.T[1][cx] - ty) * r.inv_d[0], dTx_dy = (A.T[0][cy] - tx) * r.inv_d[1];
+        float dTy_dz = 0.f, dTx_dz = 0.f;
+        if (DIM == 3) {
+            const int cz = i + n0 * (j + n1 * (k + 1 == n2 ? 0 : k + 1));
+            dTy_dz = (A.T[1][cz] - ty) * r.inv_d[2];
+            dTx_dz = (A.T[0][cz] - tx) * r.inv_d[2];
+        }
+        A.lB[0][idx] += dt * (dTz_dy - dTy_dz);
+        A.lB[1][idx] += dt * (dTx_dz - dTz_dx);
+        A.lB[2][idx] += dt * (dTy_dx - dTx_dy);
+        A.lJ[0][idx] = -dt * tx;
+        A.lJ[1][idx] = -dt * ty;
+        A.lJ[2][idx] = -dt * tz;
+        if (laser_on) {
+            int il = (DIM == 3 ? k : j) - origin;
+            il = il < 0 ? il + nl : il;
+            if (il == r.laser_plane) {
+                const double xi = t_n + 0.5 * r.dt_d + 0.5 * r.d_last_d;
+                acc += (double)A.T[r.laser_pol][idx] * (double)dt * (double)r.inv_d[DIM - 1] *
+                       laser_unit(r, laser_r2_adj(r, i, j), xi);
+            }
+        }
+    }
+    double t = block_reduce(acc, sh);
+    if (threadIdx.x == 0 && t != 0.0) atomicAdd(la0, t);
+}
+
+// ---------------------------------------------------------------------------
+// Per-particle adjoint.
+// ---------------------------------------------------------------------------
+// Node / half shapes with derivatives d w / d(offset).
+template <int P>
+struct ShapeD;
+template <>
+struct ShapeD<1> {
+    static __device__ __forceinline__ void node(int c, float d, int &b, float *w, float *dw)
+    {
+        b = c;
+        w[0] = 1.f - d;
+        w[1] = d;
+        dw[0] = -1.f;
+        dw[1] = 1.f;
+    }
+    static __device__ __forceinline__ void half(int c, float d, int &b, float *w, float *dw)
+    {
+        bool hi = d >= 0.5f;
+        float t = hi ? d - 0.5f : d + 0.5f;
+        b = hi ? c : c - 1;
+        w[0] = 1.f - t;
+        w[1] = t;
+        dw[0] = -1.f;
+        dw[1] = 1.f;
+    }
+};
+template <>
+struct ShapeD<2> {
+    static __device__ __forceinline__ void q(float t, float *w, float *dw)
+    {
+        float a = 0.5f - t, b = 0.5f + t;
+        w[0] = 0.5f * a * a;
+        w[1] = 0.75f - t * t;
+        w[2] = 0.5f * b * b;
+        dw[0] = -a;
+        dw[1] = -2.f * t;
+        dw[2] = b;
+    }
+    static __device__ __forceinline__ void node(int c, float d, int &b, float *w, float *dw)
+    {
+        int h = d >= 0.5f ? 1 : 0;
+        b = c + h - 1;
+        q(d - (float)h, w, dw);
+    }
+    static __device__ __forceinline__ void half(int c, float d, int &b, float *w, float *dw)
+    {
+        b = c - 1;
+        q(d - 0.5f, w, dw);
+    }
+};
+template <>
+struct ShapeD<3> {
+    static __device__ __forceinline__ void cub(float f, float *w, float *dw)
+    {
+        const float s = 1.f / 6.f;
+        float g = 1.f - f, f2 = f * f, f3 = f2 * f;
+        w[0] = g * g * g * s;
+        w[1] = (4.f - 6.f * f2 + 3.f * f3) * s;
+        w[2] = (1.f + 3.f * f + 3.f * f2 - 3.f * f3) * s;
+        w[3] = f3 * s;
+        dw[0] = -0.5f * g * g;
+        dw[1] = -2.f * f + 1.5f * f2;
+        dw[2] = 0.5f + f - 1.5f * f2;
+        dw[3] = 0.5f * f2;
+    }
+    static __device__ __forceinline__ void node(int c, float d, int &b, float *w, float *dw)
+    {
+        b = c - 1;
+        cub(d, w, dw);
+    }
+    static __device__ __forceinline__ void half(int c, float d, int &b, float *w, float *dw)
+    {
+        bool hi = d >= 0.5f;
+        b = hi ? c - 1 : c - 2;
+        cub(hi ? d - 0.5f : d + 0.5f, w, dw);
+    }
+};
+
+struct GF {
+    const float *p[6];
+    int n0, n1, n2;
+    __device__ __forceinline__ int at(int i, int j, int k) const
+    {
+        return wrapi(i, n0) + n0 * (wrapi(j, n1) + n1 * (n2 > 1 ? wrapi(k, n2) : 0));
+    }
+};
+
+// Boris push keeping what its transpose needs.
+struct BorisTape {
+    float um[3], t[3], s[3], p[3], g, f;
+};
+
+__device__ __forceinline__ void cross(const float *a, const float *b, float *c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+__device__ __forceinline__ void boris_fwd(float h, const float *e, const float *b, const float *u, float *out,
+                                          BorisTape &tp)
+{
+    for (int a = 0; a < 3; ++a) tp.um[a] = fmaf(h, e[a], u[a]);
+    tp.g = rsqrtf(1.f + tp.um[0] * tp.um[0] + tp.um[1] * tp.um[1] + tp.um[2] * tp.um[2]);
+    for (int a = 0; a < 3; ++a) tp.t[a] = h * b[a] * tp.g;
+    tp.f = 2.f * __frcp_rn(1.f + tp.t[0] * tp.t[0] + tp.t[1] * tp.t[1] + tp.t[2] * tp.t[2]);
+    for (int a = 0; a < 3; ++a) tp.s[a] = tp.f * tp.t[a];
+    float c[3];
+    cross(tp.um, tp.t, c);
+    for (int a = 0; a < 3; ++a) tp.p[a] = tp.um[a] + c[a];
+    cross(tp.p, tp.s, c);
+    for (int a = 0; a < 3; ++a) out[a] = fmaf(h, e[a], tp.um[a] + c[a]);
+}
+
+// Transpose of boris_fwd: lam_out -> lam_u, lam_e, lam_b.
+__device__ __forceinline__ void boris_vjp(float h, const float *b, const BorisTape &tp, const float *lo, float *lu,
+                                          float *le, float *lb)
+{
+    float lum[3], lp[3], ls[3], lt[3], c[3];
+    for (int a = 0; a < 3; ++a) {
+        le[a] = h * lo[a];
+        lum[a] = lo[a];  // out = um + p x s + h e
+    }
+    cross(tp.s, lo, lp);  // d(p x s)/dp^T lo = s x lo
+    cross(lo, tp.p, ls);  // d(p x s)/ds^T lo = lo x p
+    // p = um + um x t
+    cross(tp.t, lp, c);
+    for (int a = 0; a < 3; ++a) lum[a] += lp[a] + c[a];
+    cross(lp, tp.um, lt);
+    // s = f t, f = 2/(1+|t|^2), df/dt = -f^2 t
+    const float lf = ls[0] * tp.t[0] + ls[1] * tp.t[1] + ls[2] * tp.t[2];
+    for (int a = 0; a < 3; ++a) lt[a] += tp.f * ls[a] - lf * tp.f * tp.f * tp.t[a];
+    // t = h b g, g = (1+|um|^2)^(-1/2), dg/dum = -g^3 um
+    float lg = 0.f;
+    for (int a = 0; a < 3; ++a) {
+        lb[a] = h * tp.g * lt[a];
+        lg += h * b[a] * lt[a];
+    }
+    const float g3 = tp.g * tp.g * tp.g;
+    for (int a = 0; a < 3; ++a) lum[a] -= lg * g3 * tp.um[a];
+    // um = u + h e
+    for (int a = 0; a < 3; ++a) {
+        lu[a] = lum[a];
+        le[a] += h * lum[a];
+    }
+}
+
+template <int DIM, int P>
+__global__ void adj_particles_kernel(const Run *__restrict__ run, AdjPtrs A, TrajStep ts, int origin)
+{
+    const Run &r = *run;
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= ts.n) return;
+    const int32_t pc = ts.cell[s];
+    if (pc < 0) return;
+    int c[3];
+    unpack_cell(r, pc, c[0], c[1], c[2]);
+    const int nl = r.n[DIM - 1];
+    if (r.open_last) {
+        int pl = c[DIM - 1] - origin;
+        pl = pl < 0 ? pl + nl : pl;
+        if (pl < r.margin || pl >= nl - r.margin) return;  // removed before this push
+    }
+    const int id = ts.id[s];
+    float d[3] = {0.f, 0.f, 0.f}, u[3];
+    for (int a = 0; a < DIM; ++a) d[a] = ts.off[a][s];
+    for (int a = 0; a < 3; ++a) u[a] = ts.u[a][s];
+    const float w = A.wid[id];
+    const GF gf{{ts.E[0], ts.E[1], ts.E[2], ts.B[0], ts.B[1], ts.B[2]}, r.n[0], r.n[1], DIM == 3 ? r.n[2] : 1};
+    // --- forward recompute: shapes and gather with position derivatives ---
+    int bn[3] = {0, 0, 0}, bh[3] = {0, 0, 0};
+    float wn[3][P + 1], wh[3][P + 1], dwn[3][P + 1], dwh[3][P + 1];
+    for (int a = 0; a < 3; ++a)
+        for (int q = 0; q <= P; ++q) wn[a][q] = wh[a][q] = dwn[a][q] = dwh[a][q] = 0.f;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        ShapeD<P>::node(c[a], d[a], bn[a], wn[a], dwn[a]);
+        ShapeD<P>::half(c[a], d[a], bh[a], wh[a], dwh[a]);
+    }
+    // half-integer flags per component (E0 E1 E2 B0 B1 B2) and axis
+    const unsigned hxm = 0x31u, hym = 0x2Au, hzm = 0x1Cu;
+    float eb[6], deb[6][3];
+#pragma unroll
+    for (int comp = 0; comp < 6; ++comp) {
+        const bool hx = (hxm >> comp) & 1u, hy = (hym >> comp) & 1u, hz = (hzm >> comp) & 1u;
+        const int b0 = hx ? bh[0] : bn[0], b1 = hy ? bh[1] : bn[1], b2 = hz ? bh[2] : bn[2];
+        float v = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+#pragma unroll
+        for (int kc = 0; kc < (DIM == 3 ? P + 1 : 1); ++kc) {
+            const float wz = DIM == 3 ? (hz ? wh[2][kc] : wn[2][kc]) : 1.f;
+            const float dwz = DIM == 3 ? (hz ? dwh[2][kc] : dwn[2][kc]) : 0.f;
+#pragma unroll
+            for (int kb = 0; kb <= P; ++kb) {
+                const float wy = hy ? wh[1][kb] : wn[1][kb], dwy = hy ? dwh[1][kb] : dwn[1][kb];
+#pragma unroll
+                for (int ka = 0; ka <= P; ++ka) {
+                    const float wx = hx ? wh[0][ka] : wn[0][ka], dwx = hx ? dwh[0][ka] : dwn[0][ka];
+                    const float F = __ldg(gf.p[comp] + gf.at(b0 + ka, b1 + kb, b2 + kc));
+                    v += wx * wy * wz * F;
+                    g0 += dwx * wy * wz * F;
+                    g1 += wx * dwy * wz * F;
+                    g2 += wx * wy * dwz * F;
+                }
+            }
+        }
+        eb[comp] = v;
+        deb[comp][0] = g0;
+        deb[comp][1] = g1;
+        deb[comp][2] = g2;
+    }
+    BorisTape tp;
+    float un[3];
+    boris_fwd(r.qm_half_dt, eb, eb + 3, u, un, tp);
+    const float ig = rsqrtf(1.f + un[0] * un[0] + un[1] * un[1] + un[2] * un[2]);
+    float d1[3] = {0.f, 0.f, 0.f};
+    int k[3] = {0, 0, 0};
+    bool ok = true;
+    for (int a = 0; a < DIM; ++a) {
+        float nd = d[a] + r.dt_over_d[a] * un[a] * ig;
+        ok = ok && nd > -1.f && nd < 2.f;
+        float kk = floorf(nd);
+        nd = nd - kk;
+        if (nd >= 1.f) {
+            nd = 0.f;
+            kk += 1.f;
+        }
+        d1[a] = nd;
+        k[a] = (int)kk;
+    }
+    if (!ok) return;
+    bool absorbed = false;
+    if (r.open_last) {
+        int cl = wrapi(c[DIM - 1] + k[DIM - 1], nl) - origin;
+        cl = cl < 0 ? cl + nl : cl;
+        absorbed = cl < r.margin || cl >= nl - r.margin;
+    }
+    // --- adjoint inputs: state adjoints of x^{n+1}, u^{n+1/2} ---
+    float lxn[3] = {0.f, 0.f, 0.f}, lun[3] = {0.f, 0.f, 0.f};
+    if (!absorbed) {
+        for (int a = 0; a < DIM; ++a) lxn[a] = A.lx[a][id];
+        for (int a = 0; a < 3; ++a) lun[a] = A.lu[a][id];
+    }
+    // --- deposit transpose (Esirkepov window, per unit weight) ---
+    constexpr int W = P + 2;
+    float S0[3][W], S1[3][W], dS0[3][W], dS1[3][W];
+    int wb[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a)
+        for (int q = 0; q < W; ++q) S0[a][q] = S1[a][q] = dS0[a][q] = dS1[a][q] = 0.f;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        int bo, bnw;
+        float so[P + 1], sn[P + 1], dso[P + 1], dsn[P + 1];
+        ShapeD<P>::node(c[a], d[a], bo, so, dso);
+        ShapeD<P>::node(c[a] + k[a], d1[a], bnw, sn, dsn);
+        const int sh = bnw - bo;
+        wb[a] = sh < 0 ? bnw : bo;
+        const int oo = sh < 0 ? 1 : 0, on = sh > 0 ? 1 : 0;
+#pragma unroll
+        for (int q = 0; q <= P; ++q) {
+            // compile-time q; the runtime offset selects between two slots
+            if (oo) {
+                S0[a][q + 1] = so[q];
+                dS0[a][q + 1] = dso[q];
+            } else {
+                S0[a][q] = so[q];
+                dS0[a][q] = dso[q];
+            }
+            if (on) {
+                S1[a][q + 1] = sn[q];
+                dS1[a][q + 1] = dsn[q];
+            } else {
+                S1[a][q] = sn[q];
+                dS1[a][q] = dsn[q];
+            }
+        }
+    }
+    float As[3][W], DS[3][W], Pr[3][W];
+    for (int a = 0; a < 3; ++a) {
+        float run_ = 0.f;
+        for (int q = 0; q < W; ++q) {
+            DS[a][q] = S1[a][q] - S0[a][q];
+            As[a][q] = S0[a][q] + 0.5f * DS[a][q];
+            run_ += DS[a][q];
+            Pr[a][q] = run_;
+        }
+    }
+    const float q_ = r.q;
+    const float vz = un[2] * ig;
+    float gA[3][W], gD[3][W];
+    for (int a = 0; a < 3; ++a)
+        for (int q = 0; q < W; ++q) gA[a][q] = gD[a][q] = 0.f;
+    float lw = 0.f, gvz = 0.f;
+    auto lam = [&](int comp, int i, int j, int kk) { return __ldg(A.lJ[comp] + gf.at(i, j, kk)); };
+    if (DIM == 2) {
+        const float cx = -q_ * r.d_over_dt[0], cy = -q_ * r.d_over_dt[1];
+        float Rx[W], Ry[W];
+        for (int q = 0; q < W; ++q) Rx[q] = Ry[q] = 0.f;
+        for (int qb = 0; qb < W; ++qb)
+            for (int qa = 0; qa < W; ++qa) {
+                const int i = wb[0] + qa, j = wb[1] + qb;
+                if (qa < W - 1) {  // J_x = cx P_x A_y
+                    const float L = lam(0, i, j, 0);
+                    lw += L * cx * Pr[0][qa] * As[1][qb];
+                    Rx[qa] += L * As[1][qb];
+                    gA[1][qb] += w * cx * L * Pr[0][qa];
+                }
+                if (qb < W - 1) {  // J_y = cy P_y A_x
+                    const float L = lam(1, i, j, 0);
+                    lw += L * cy * Pr[1][qb] * As[0][qa];
+                    Ry[qb] += L * As[0][qa];
+                    gA[0][qa] += w * cy * L * Pr[1][qb];
+                }
+                {  // J_z = q vz (A_x A_y + DS_x DS_y / 12)
+                    const float L = lam(2, i, j, 0);
+                    const float fz = As[0][qa] * As[1][qb] + DS[0][qa] * DS[1][qb] * (1.f / 12.f);
+                    lw += L * q_ * vz * fz;
+                    gvz += w * q_ * L * fz;
+                    gA[0][qa] += w * q_ * vz * L * As[1][qb];
+                    gA[1][qb] += w * q_ * vz * L * As[0][qa];
+                    gD[0][qa] += w * q_ * vz * L * DS[1][qb] * (1.f / 12.f);
+                    gD[1][qb] += w * q_ * vz * L * DS[0][qa] * (1.f / 12.f);
+                }
+            }
+        // prefix transposes: d/dDS[a'] of sum_a R[a] P[a] = sum_{a>=a'} R[a]
+        float sx = 0.f, sy = 0.f;
+        for (int q = W - 2; q >= 0; --q) {
+            sx += Rx[q];
+            sy += Ry[q];
+            gD[0][q] += w * cx * sx;
+            gD[1][q] += w * cy * sy;
+        }
+    } else {
+        for (int comp = 0; comp < 3; ++comp) {
+            const int a = comp, b = (comp + 1) % 3, cc = (comp + 2) % 3;
+            const float coef = -q_ * r.d_over_dt[a];
+            float R[W];
+            for (int q = 0; q < W; ++q) R[q] = 0.f;
+            for (int qc = 0; qc < W; ++qc)
+                for (int qb = 0; qb < W; ++qb) {
+                    const float fac = As[b][qb] * As[cc][qc] + DS[b][qb] * DS[cc][qc] * (1.f / 12.f);
+                    for (int qa = 0; qa < W - 1; ++qa) {
+                        int q3[3];
+                        q3[a] = qa;
+                        q3[b] = qb;
+                        q3[cc] = qc;
+                        const float L = lam(comp, wb[0] + q3[0], wb[1] + q3[1], wb[2] + q3[2]);
+                        lw += L * coef * Pr[a][qa] * fac;
+                        R[qa] += L * fac;
+                        const float lp = w * coef * L * Pr[a][qa];
+                        gA[b][qb] += lp * As[cc][qc];
+                        gA[cc][qc] += lp * As[b][qb];
+                        gD[b][qb] += lp * DS[cc][qc] * (1.f / 12.f);
+                        gD[cc][qc] += lp * DS[b][qb] * (1.f / 12.f);
+                    }
+                }
+            float sacc = 0.f;
+            for (int q = W - 2; q >= 0; --q) {
+                sacc += R[q];
+                gD[a][q] += w * coef * sacc;
+            }
+        }
+    }
+    // A = S0 + DS/2 = (S0 + S1)/2, DS = S1 - S0  ->  d/dS0 = gA/2 - gD, d/dS1 = gA/2 + gD
+    float lxo[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        float go = 0.f, gn = 0.f;
+        for (int q = 0; q < W; ++q) {
+            go += (0.5f * gA[a][q] - gD[a][q]) * dS0[a][q];
+            gn += (0.5f * gA[a][q] + gD[a][q]) * dS1[a][q];
+        }
+        lxo[a] = go;
+        lxn[a] += gn;
+    }
+    // --- move transpose: x1 = x0 + (dt/d) u/gamma ; vz = u_z / gamma ---
+    float lut[3] = {lun[0], lun[1], lun[2]};
+    float gv[3] = {0.f, 0.f, 0.f};  // d L / d v_a with v = u/gamma
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        gv[a] += lxn[a] * r.dt_over_d[a];
+        lxo[a] += lxn[a];
+    }
+    if (DIM == 2) gv[2] += gvz;
+    {
+        const float vv = gv[0] * un[0] + gv[1] * un[1] + gv[2] * un[2];
+        const float ig3 = ig * ig * ig;
+        for (int a = 0; a < 3; ++a) lut[a] += gv[a] * ig - vv * un[a] * ig3;
+    }
+    // --- Boris transpose ---
+    float lu0[3], le[3], lb[3];
+    boris_vjp(r.qm_half_dt, eb + 3, tp, lut, lu0, le, lb);
+    const float lebs[6] = {le[0], le[1], le[2], lb[0], lb[1], lb[2]};
+    // --- gather transpose: positions and scatter into lamE, lamB ---
+#pragma unroll
+    for (int comp = 0; comp < 6; ++comp) {
+        const float L = lebs[comp];
+        for (int a = 0; a < DIM; ++a) lxo[a] += L * deb[comp][a];
+        if (L == 0.f) continue;
+        const bool hx = (hxm >> comp) & 1u, hy = (hym >> comp) & 1u, hz = (hzm >> comp) & 1u;
+        const int b0 = hx ? bh[0] : bn[0], b1 = hy ? bh[1] : bn[1], b2 = hz ? bh[2] : bn[2];
+        float *dst = comp < 3 ? A.lE[comp] : A.lB[comp - 3];
+#pragma unroll
+        for (int kc = 0; kc < (DIM == 3 ? P + 1 : 1); ++kc) {
+            const float wz = DIM == 3 ? (hz ? wh[2][kc] : wn[2][kc]) : 1.f;
+#pragma unroll
+            for (int kb = 0; kb <= P; ++kb) {
+                const float wy = hy ? wh[1][kb] : wn[1][kb];
+#pragma unroll
+                for (int ka = 0; ka <= P; ++ka) {
+                    const float wx = hx ? wh[0][ka] : wn[0][ka];
+                    atomicAdd(dst + gf.at(b0 + ka, b1 + kb, b2 + kc), L * wx * wy * wz);
+                }
+            }
+        }
+    }
+    for (int a = 0; a < DIM; ++a) A.lx[a][id] = lxo[a];
+    for (int a = 0; a < 3; ++a) A.lu[a][id] = lu0[a];
+    A.lw[id] += (double)lw;
+}
+
+// ---------------------------------------------------------------------------
+// Objective: L = sum w K sigma / sum w sigma, K = m (gamma - 1),
+// sigma(z) = logistic((z - z_lo)/width) logistic((z_hi - z)/width), z the
+// last-axis position in cells (window frame).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float logistic(float x) { return 1.f / (1.f + __expf(-x)); }
+
+__device__ __forceinline__ bool obj_particle(const Run &r, const ParticleBuf &pb, long long i, int origin,
+                                             const ObjArgs &o, float &w, float &z, float &sig, float &dsig)
+{
+    const int32_t pc = pb.cell[i];
+    if (pc < 0) return false;
+    int c[3];
+    unpack_cell(r, pc, c[0], c[1], c[2]);
+    const int nl = r.n[r.dim - 1];
+    int cl = c[r.dim - 1] - (r.open_last ? origin : 0);
+    cl = cl < 0 ? cl + nl : cl;
+    if (r.open_last && (cl < r.margin || cl >= nl - r.margin)) return false;
+    z = (float)cl + pb.off[r.dim - 1][i];
+    const float a = logistic((z - o.z_lo) / o.width), b = logistic((o.z_hi - z) / o.width);
+    sig = a * b;
+    dsig = (a * (1.f - a) * b - a * b * (1.f - b)) / o.width;
+    w = pb.w ? pb.w[i] : r.w_const;
+    return true;
+}
+
+__global__ void obj_reduce_kernel(const Run *__restrict__ run, int origin, ObjArgs o, double *out)
+{
+    const Run &r = *run;
+    const RunState &s = *r.state;
+    const ParticleBuf pb = r.P[s.buf];
+    __shared__ double sh[32];
+    double num = 0.0, den = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < s.n_total;
+         i += (long long)gridDim.x * blockDim.x) {
+        float w, z, sig, dsig;
+        if (!obj_particle(r, pb, i, origin, o, w, z, sig, dsig)) continue;
+        const double ux = pb.u[0][i], uy = pb.u[1][i], uz = pb.u[2][i];
+        const double K = (double)r.m * (sqrt(1.0 + ux * ux + uy * uy + uz * uz) - 1.0);
+        num += (double)w * K * sig;
+        den += (double)w * sig;
+    }
+    double a = block_reduce(num, sh), b = block_reduce(den, sh);
+    if (threadIdx.x == 0) {
+        atomicAdd(out + 0, a);
+        atomicAdd(out + 1, b);
+    }
+}
+
+__global__ void obj_seed_kernel(const Run *__restrict__ run, int origin, ObjArgs o, const double *red, AdjPtrs A)
+{
+    const Run &r = *run;
+    const RunState &s = *r.state;
+    const ParticleBuf pb = r.P[s.buf];
+    const double den = red[1];
+    const double L = den > 0.0 ? red[0] / den : 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < s.n_total;
+         i += (long long)gridDim.x * blockDim.x) {
+        float w, z, sig, dsig;
+        if (!obj_particle(r, pb, i, origin, o, w, z, sig, dsig)) continue;
+        const int id = pb.id[i];
+        const float ux = pb.u[0][i], uy = pb.u[1][i], uz = pb.u[2][i];
+        const float gam = sqrtf(1.f + ux * ux + uy * uy + uz * uz);
+        const float K = r.m * (gam - 1.f);
+        const float sc = (float)(den > 0.0 ? 1.0 / den : 0.0);
+        A.lu[0][id] = w * sig * r.m * ux / gam * sc;
+        A.lu[1][id] = w * sig * r.m * uy / gam * sc;
+        A.lu[2][id] = w * sig * r.m * uz / gam * sc;
+        for (int a = 0; a < r.dim - 1; ++a) A.lx[a][id] = 0.f;
+        A.lx[r.dim - 1][id] = w * dsig * (K - (float)L) * sc;
+        A.lw[id] = (double)(sig * (K - (float)L) * sc);
+    }
+}
+
+// dL/dknot_k = sum_id dL/dw_id * phi_k(z_birth) / ppc_total (hat functions on
+// equally spaced knots over [z0, z1], clamped outside).
+__global__ void knots_kernel(const double *lw, const float *zb, long long n, int n_knots, double z0, double z1,
+                             double ppc_t, double *out)
+{
+    for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < n;
+         id += (long long)gridDim.x * blockDim.x) {
+        const double g = lw[id] / ppc_t;
+        if (g == 0.0) continue;
+        double f = ((double)zb[id] - z0) / (z1 - z0) * (n_knots - 1);
+        if (n_knots == 1 || f <= 0.0) {
+            atomicAdd(out, g);
+        } else if (f >= n_knots - 1) {
+            atomicAdd(out + n_knots - 1, g);
+        } else {
+            const int i = (int)floor(f);
+            const double t = f - i;
+            atomicAdd(out + i, g * (1.0 - t));
+            atomicAdd(out + i + 1, g * t);
+        }
+    }
+}
+
+// weights and birth positions by id (the load order, before any sort)
+__global__ void adj_init_kernel(const Run *__restrict__ run, float *wid, float *zb, long long n)
+{
+    const Run &r = *run;
+    const RunState &s = *r.state;
+    const ParticleBuf pb = r.P[s.buf];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int id = pb.id[i];
+        if (id < 0 || id >= n) continue;
+        wid[id] = pb.w ? pb.w[i] : r.w_const;
+        int c[3];
+        unpack_cell(r, pb.cell[i] < 0 ? 0 : pb.cell[i], c[0], c[1], c[2]);
+        zb[id] = ((float)c[r.dim - 1] + pb.off[r.dim - 1][i]) * (float)r.d_last_d;
+    }
+}
+
+// Copy the live buffer's first n slots to / from a side buffer (the
+// current buffer index is read from the device state).
+__global__ void part_copy_kernel(const Run *__restrict__ run, PartCopy pc, long long n, int restore)
+{
+    const Run &r = *run;
+    const RunState &s = *r.state;
+    const ParticleBuf pb = r.P[s.buf];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (!restore) {
+            pc.cell[i] = i < s.n_total ? pb.cell[i] : -1;
+            for (int a = 0; a < r.dim; ++a) pc.off[a][i] = pb.off[a][i];
+            for (int a = 0; a < 3; ++a) pc.u[a][i] = pb.u[a][i];
+            if (pc.w && pb.w) pc.w[i] = pb.w[i];
+            if (pc.id) pc.id[i] = pb.id ? pb.id[i] : -1;
+        } else {
+            pb.cell[i] = pc.cell[i];
+            for (int a = 0; a < r.dim; ++a) pb.off[a][i] = pc.off[a][i];
+            for (int a = 0; a < 3; ++a) pb.u[a][i] = pc.u[a][i];
+            if (pc.w && pb.w) pb.w[i] = pc.w[i];
+            if (pc.id && pb.id) pb.id[i] = pc.id[i];
+        }
+    }
+}
+
+unsigned blocks_for(long long n)
+{
+    long long b = (n + kBlock - 1) / kBlock;
+    return (unsigned)(b < 1 ? 1 : (b > 65535 * 4 ? 65535 * 4 : b));
+}
+
+}  // namespace
+
+cudaError_t launch_adj_fields(int dim, const Run *run, const AdjPtrs &A, int ncell, int plane, int origin, double t_n,
+                              double dt, int laser_on, double *la0, cudaStream_t st)
+{
+    const unsigned g = blocks_for(ncell), gp = blocks_for(plane);
+    if (dim == 2) {
+        adj_b_kernel<2><<<g, kBlock, 0, st>>>(run, A, origin, t_n + dt, laser_on, la0);
+        adj_e_mask_kernel<2><<<g, kBlock, 0, st>>>(run, A, origin);
+        adj_mur_kernel<2><<<gp, kBlock, 0, st>>>(run, A, origin);
+        adj_e_curl_kernel<2><<<g, kBlock, 0, st>>>(run, A, origin, t_n, laser_on, la0);
+    } else {
+        adj_b_kernel<3><<<g, kBlock, 0, st>>>(run, A, origin, t_n + dt, laser_on, la0);
+        adj_e_mask_kernel<3><<<g, kBlock, 0, st>>>(run, A, origin);
+        adj_mur_kernel<3><<<gp, kBlock, 0, st>>>(run, A, origin);
+        adj_e_curl_kernel<3><<<g, kBlock, 0, st>>>(run, A, origin, t_n, laser_on, la0);
+    }
+    // lamE <- newE, then (iii)
+    cudaError_t e = cudaMemcpyAsync(A.lE[0], A.nE[0], sizeof(float) * ncell, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(A.lE[1], A.nE[1], sizeof(float) * ncell, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(A.lE[2], A.nE[2], sizeof(float) * ncell, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    if (dim == 2) adj_b_kernel<2><<<g, kBlock, 0, st>>>(run, A, origin, t_n, laser_on, la0);
+    else adj_b_kernel<3><<<g, kBlock, 0, st>>>(run, A, origin, t_n, laser_on, la0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_particles(int dim, int order, const Run *run, const AdjPtrs &A, const TrajStep &ts, int origin,
+                                 cudaStream_t st)
+{
+    if (ts.n <= 0) return cudaSuccess;
+    const unsigned g = (unsigned)((ts.n + kBlock - 1) / kBlock);
+    if (dim == 2) {
+        if (order == 1) adj_particles_kernel<2, 1><<<g, kBlock, 0, st>>>(run, A, ts, origin);
+        else if (order == 2) adj_particles_kernel<2, 2><<<g, kBlock, 0, st>>>(run, A, ts, origin);
+        else adj_particles_kernel<2, 3><<<g, kBlock, 0, st>>>(run, A, ts, origin);
+    } else {
+        if (order == 1) adj_particles_kernel<3, 1><<<g, kBlock, 0, st>>>(run, A, ts, origin);
+        else if (order == 2) adj_particles_kernel<3, 2><<<g, kBlock, 0, st>>>(run, A, ts, origin);
+        else adj_particles_kernel<3, 3><<<g, kBlock, 0, st>>>(run, A, ts, origin);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_objective(const Run *run, int origin, const ObjArgs &o, double *red, long long cap, int seed,
+                             const AdjPtrs &A, cudaStream_t st)
+{
+    const unsigned g = blocks_for(cap) < 1024 ? blocks_for(cap) : 1024;
+    if (!seed) {
+        obj_reduce_kernel<<<g, kBlock, 0, st>>>(run, origin, o, red);
+    } else {
+        obj_seed_kernel<<<blocks_for(cap), kBlock, 0, st>>>(run, origin, o, red, A);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_knots(const double *lw, const float *zb, long long n, int n_knots, double z0, double z1,
+                         double ppc_t, double *out, cudaStream_t st)
+{
+    knots_kernel<<<blocks_for(n), kBlock, 0, st>>>(lw, zb, n, n_knots, z0, z1, ppc_t, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_part_copy(const Run *run, const PartCopy &pc, long long n, int restore, cudaStream_t st)
+{
+    part_copy_kernel<<<blocks_for(n), kBlock, 0, st>>>(run, pc, n, restore);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_init(const Run *run, float *wid, float *zb, long long n, cudaStream_t st)
+{
+    adj_init_kernel<<<blocks_for(n), kBlock, 0, st>>>(run, wid, zb, n);
+    return cudaGetLastError();
+}
+
+}  // namespace pic

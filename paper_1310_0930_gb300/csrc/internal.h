@@ -57,4 +57,43 @@ cudaError_t launch_unpack(const Run *run, long long cap, int dim, int32_t *cell,
 // max particles in a tile, occupied tiles.
 cudaError_t launch_diag(int dim, const Run *run, const double *rho, long long cap, double *out, cudaStream_t st);
 
+// adjoint.cu -- reverse sweep of the timestep
+struct AdjPtrs {
+    float *lE[3], *lB[3], *lJ[3], *T[3], *nE[3];  // field adjoints and scratch
+    float *lx[3], *lu[3];                         // particle adjoints by id
+    double *lw;                                   // dL/dw by id
+    float *wid;                                   // weight by id
+};
+// one recorded step: the particles and fields the push of that step read
+struct TrajStep {
+    const int32_t *cell;
+    const float *off[3];
+    const float *u[3];
+    const int32_t *id;
+    long long n;
+    const float *E[3];
+    const float *B[3];
+};
+struct ObjArgs {
+    float z_lo, z_hi, width;
+};
+cudaError_t launch_adj_fields(int dim, const Run *run, const AdjPtrs &A, int ncell, int plane, int origin, double t_n,
+                              double dt, int laser_on, double *la0, cudaStream_t st);
+cudaError_t launch_adj_particles(int dim, int order, const Run *run, const AdjPtrs &A, const TrajStep &ts, int origin,
+                                 cudaStream_t st);
+// seed == 0: reduce sum w K sigma and sum w sigma into red[0..1]; seed == 1: seed the adjoints
+cudaError_t launch_objective(const Run *run, int origin, const ObjArgs &o, double *red, long long cap, int seed,
+                             const AdjPtrs &A, cudaStream_t st);
+cudaError_t launch_knots(const double *lw, const float *zb, long long n, int n_knots, double z0, double z1,
+                         double ppc_t, double *out, cudaStream_t st);
+cudaError_t launch_adj_init(const Run *run, float *wid, float *zb, long long n, cudaStream_t st);
+struct PartCopy {
+    int32_t *cell;
+    float *off[3];
+    float *u[3];
+    float *w;    // may be null
+    int32_t *id; // may be null
+};
+cudaError_t launch_part_copy(const Run *run, const PartCopy &pc, long long n, int restore, cudaStream_t st);
+
 }  // namespace pic

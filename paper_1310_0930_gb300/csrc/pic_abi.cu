@@ -31,6 +31,30 @@ struct HostRun {
     float *rho32 = nullptr; // FP32 copy for pic_read_fields(PIC_RHO)
 };
 
+// Reverse-mode state: checkpoints, one recorded segment, adjoint arrays.
+struct Ckpt {
+    PartCopy pc;
+    float *E[3], *B[3];
+    RunState *st;
+    double time;
+};
+struct Rec {
+    PartCopy pc;
+    float *E[3], *B[3];
+    double time;
+};
+struct Adj {
+    int K = 1, total = 0, nck = 0;
+    long long nid = 0;
+    AdjPtrs A{};
+    float *zb = nullptr;
+    double *la0 = nullptr, *red = nullptr, *dk = nullptr;
+    std::vector<Ckpt> ck;
+    std::vector<Rec> rec;
+    bool rec_on = false, save_ckpt = true, spent = false;
+    int rec_base = 0;
+};
+
 }  // namespace
 
 struct pic_s {
@@ -64,6 +88,9 @@ struct pic_s {
     int prof_max = 0, prof_steps = 0;
     bool prof_on = false;
     long long prof_launches = 0;  // kernels enqueued during profiled steps
+    long long steps_done = 0;     // host mirror of the step counter
+    double time_host = 0.0;       // host mirror of the device time (same additions)
+    Adj *adj = nullptr;
 };
 
 namespace {
@@ -294,6 +321,18 @@ int enqueue_step(pic_s *h, bool sort)
     };
     mark(PIC_PH_SORT);
     if (sort) e = launch_sort(R, h->nruns, h->seg_parts, h->max_tiles, st);
+    if (e == cudaSuccess && h->adj && h->adj->rec_on) {
+        // the push of this step reads these particles and fields
+        Rec &rc = h->adj->rec[h->steps_done - h->adj->rec_base];
+        const Run &r0 = h->runs[0].r;
+        rc.time = h->time_host;
+        e = launch_part_copy(R, rc.pc, h->adj->nid, 0, st);
+        for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+            e = cudaMemcpyAsync(rc.E[c], r0.E[c], sizeof(float) * r0.ncell, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(rc.B[c], r0.B[c], sizeof(float) * r0.ncell, cudaMemcpyDeviceToDevice, st);
+        }
+    }
     mark(PIC_PH_ZERO_J);
     if (e == cudaSuccess) e = launch_zero_j(R, h->seg_cells, st);
     mark(PIC_PH_PUSH);
@@ -607,7 +646,24 @@ int pic_step(pic_t *h, int32_t nsteps)
         int rc = first_step_setup(h);
         if (rc) return rc;
     }
+    if (h->adj && h->adj->spent) return PIC_ESTATE;
     for (int s = 0; s < nsteps; ++s) {
+        if (h->adj && h->adj->save_ckpt && h->steps_done % h->adj->K == 0 &&
+            h->steps_done / h->adj->K < h->adj->nck) {
+            Ckpt &ck = h->adj->ck[h->steps_done / h->adj->K];
+            const Run &r0 = h->runs[0].r;
+            cudaError_t e = launch_part_copy(h->d_runs, ck.pc, h->adj->nid, 0, h->stream);
+            for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+                e = cudaMemcpyAsync(ck.E[c], r0.E[c], sizeof(float) * r0.ncell, cudaMemcpyDeviceToDevice, h->stream);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(ck.B[c], r0.B[c], sizeof(float) * r0.ncell, cudaMemcpyDeviceToDevice,
+                                        h->stream);
+            }
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(ck.st, h->d_states, sizeof(RunState), cudaMemcpyDeviceToDevice, h->stream);
+            if (e != cudaSuccess) return PIC_ECUDA;
+            ck.time = h->time_host;
+        }
         bool sort = h->need_sort || h->since_sort >= h->sort_interval;
         int kind = sort ? 1 : 0;
         if (h->use_graph && !h->prof_on) {
@@ -634,6 +690,8 @@ int pic_step(pic_t *h, int32_t nsteps)
             h->since_sort = 0;
         }
         h->since_sort += 1;
+        h->steps_done += 1;
+        h->time_host += h->runs[0].cfg.grid.dt;
     }
     return PIC_OK;
 }
@@ -818,6 +876,7 @@ int pic_profile_begin(pic_t *h, int32_t max_steps)
 {
     if (!h || max_steps < 1) return PIC_EINVAL;
     for (cudaEvent_t ev : h->prof_events) cudaEventDestroy(ev);
+    delete h->adj;
     h->prof_events.assign((size_t)max_steps * (PIC_NUM_PHASES + 1), nullptr);
     for (auto &ev : h->prof_events)
         if (cudaEventCreate(&ev) != cudaSuccess) return PIC_ECUDA;
@@ -845,6 +904,258 @@ int pic_profile_end(pic_t *h, double *ms, int32_t n_phases, int64_t *launches)
     if (launches) *launches = h->prof_launches;
     h->prof_on = false;
     return PIC_OK;
+}
+
+int pic_adjoint_begin(pic_t *h, int32_t total_steps, int32_t checkpoint_every)
+{
+    if (!h || total_steps < 1 || checkpoint_every < 1) return PIC_EINVAL;
+    if (h->started || h->adj || h->nruns != 1) return PIC_ESTATE;
+    HostRun &hr = h->runs[0];
+    if (!hr.cfg.track_ids || !hr.sp.per_particle_weight || hr.r.window_on || !hr.r.P[0].cell) return PIC_EINVAL;
+    RunState st;
+    int rc = read_state(h, 0, &st);
+    if (rc) return rc;
+    if (st.n_total <= 0) return PIC_EINVAL;
+    Adj *a = new (std::nothrow) Adj();
+    if (!a) return PIC_ENOMEM;
+    h->adj = a;
+    const Run &r = hr.r;
+    const long long n = st.n_total, nc = r.ncell;
+    const int dim = r.dim;
+    a->K = checkpoint_every;
+    a->total = total_steps;
+    a->nck = (total_steps + checkpoint_every - 1) / checkpoint_every;
+    a->nid = n;
+    auto F = [&](long long cnt) { return (float *)dev_alloc(h, sizeof(float) * cnt); };
+    bool ok = true;
+    for (int c = 0; c < 3; ++c) {
+        a->A.lE[c] = F(nc);
+        a->A.lB[c] = F(nc);
+        a->A.lJ[c] = F(nc);
+        a->A.T[c] = F(nc);
+        a->A.nE[c] = F(nc);
+        a->A.lu[c] = F(n);
+        a->A.lx[c] = c < dim ? F(n) : nullptr;
+        ok = ok && a->A.lE[c] && a->A.lB[c] && a->A.lJ[c] && a->A.T[c] && a->A.nE[c] && a->A.lu[c] &&
+             (c >= dim || a->A.lx[c]);
+    }
+    a->A.lw = (double *)dev_alloc(h, sizeof(double) * n);
+    a->A.wid = F(n);
+    a->zb = F(n);
+    a->la0 = (double *)dev_alloc(h, sizeof(double) * 4);
+    a->red = (double *)dev_alloc(h, sizeof(double) * 4);
+    a->dk = (double *)dev_alloc(h, sizeof(double) * 1024);
+    ok = ok && a->A.lw && a->A.wid && a->zb && a->la0 && a->red && a->dk;
+    auto part = [&](bool with_w) {
+        PartCopy pc{};
+        pc.cell = (int32_t *)dev_alloc(h, sizeof(int32_t) * n);
+        for (int c = 0; c < dim; ++c) pc.off[c] = F(n);
+        for (int c = 0; c < 3; ++c) pc.u[c] = F(n);
+        pc.w = with_w ? F(n) : nullptr;
+        pc.id = (int32_t *)dev_alloc(h, sizeof(int32_t) * n);
+        ok = ok && pc.cell && pc.id && pc.u[2] && (!with_w || pc.w);
+        for (int c = 0; c < dim; ++c) ok = ok && pc.off[c];
+        return pc;
+    };
+    a->ck.resize(a->nck);
+    for (Ckpt &ck : a->ck) {
+        ck.pc = part(true);
+        for (int c = 0; c < 3; ++c) {
+            ck.E[c] = F(nc);
+            ck.B[c] = F(nc);
+            ok = ok && ck.E[c] && ck.B[c];
+        }
+        ck.st = (RunState *)dev_alloc(h, sizeof(RunState));
+        ok = ok && ck.st;
+    }
+    a->rec.resize(a->K);
+    for (Rec &rc2 : a->rec) {
+        rc2.pc = part(false);
+        for (int c = 0; c < 3; ++c) {
+            rc2.E[c] = F(nc);
+            rc2.B[c] = F(nc);
+            ok = ok && rc2.E[c] && rc2.B[c];
+        }
+    }
+    if (!ok) return PIC_ENOMEM;
+    rc = upload_runs(h);
+    if (rc) return rc;
+    cudaError_t e = launch_adj_init(h->d_runs, a->A.wid, a->zb, n, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return PIC_ECUDA;
+    h->use_graph = false;  // recording and checkpoints interleave with the steps
+    return PIC_OK;
+}
+
+static int objective_reduce(pic_t *h, const pic_objective *obj, double *L)
+{
+    if (!h || !obj || !L || !(obj->width > 0.0)) return PIC_EINVAL;
+    if (!h->started) {
+        int rc = first_step_setup(h);
+        if (rc) return rc;
+    }
+    HostRun &hr = h->runs[0];
+    RunState st;
+    int rc = read_state(h, h->cur, &st);
+    if (rc) return rc;
+    double *red = h->adj ? h->adj->red : h->d_diag;
+    const ObjArgs o{(float)obj->z_lo, (float)obj->z_hi, (float)obj->width};
+    AdjPtrs none{};
+    cudaError_t e = cudaMemsetAsync(red, 0, sizeof(double) * 2, h->stream);
+    if (e == cudaSuccess)
+        e = launch_objective(h->d_runs + h->cur, st.origin, o, red, hr.r.capacity, 0, none, h->stream);
+    double hv[2] = {0.0, 0.0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hv, red, sizeof(hv), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return PIC_ECUDA;
+    *L = hv[1] > 0.0 ? hv[0] / hv[1] : 0.0;
+    return PIC_OK;
+}
+
+int pic_objective_value(pic_t *h, const pic_objective *obj, double *L)
+{
+    return objective_reduce(h, obj, L);
+}
+
+int pic_adjoint_backward(pic_t *h, const pic_objective *obj, double *L, double *dL_da0, double *dL_dknots,
+                         int32_t n_knots, double *dL_dw)
+{
+    if (!h || !h->adj || h->adj->spent) return PIC_ESTATE;
+    Adj &a = *h->adj;
+    if (h->steps_done != a.total) return PIC_ESTATE;
+    if (n_knots < 0 || n_knots > 1024 || (n_knots > 0 && !dL_dknots)) return PIC_EINVAL;
+    HostRun &hr = h->runs[0];
+    const Run &r = hr.r;
+    double Lv = 0.0;
+    int rc = objective_reduce(h, obj, &Lv);
+    if (rc) return rc;
+    if (L) *L = Lv;
+    const long long n = a.nid, nc = r.ncell;
+    const int dim = r.dim;
+    cudaStream_t st = h->stream;
+    cudaError_t e = cudaSuccess;
+    for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+        e = cudaMemsetAsync(a.A.lE[c], 0, sizeof(float) * nc, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(a.A.lB[c], 0, sizeof(float) * nc, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(a.A.lu[c], 0, sizeof(float) * n, st);
+        if (e == cudaSuccess && c < dim) e = cudaMemsetAsync(a.A.lx[c], 0, sizeof(float) * n, st);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.A.lw, 0, sizeof(double) * n, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.la0, 0, sizeof(double), st);
+    const ObjArgs o{(float)obj->z_lo, (float)obj->z_hi, (float)obj->width};
+    RunState cur;
+    rc = read_state(h, 0, &cur);
+    if (rc) return rc;
+    if (e == cudaSuccess) e = launch_objective(h->d_runs, cur.origin, o, a.red, r.capacity, 1, a.A, st);
+    if (e != cudaSuccess) return PIC_ECUDA;
+    const int plane = r.ncell / r.n[dim - 1];
+    for (int seg = a.nck - 1; seg >= 0; --seg) {
+        const int s0 = seg * a.K, s1 = s0 + a.K < a.total ? s0 + a.K : a.total;
+        Ckpt &ck = a.ck[seg];
+        // restore the segment's start state and recompute it, recording each step
+        e = cudaMemcpyAsync(h->d_states, ck.st, sizeof(RunState), cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = launch_part_copy(h->d_runs, ck.pc, n, 1, st);
+        for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+            e = cudaMemcpyAsync(r.E[c], ck.E[c], sizeof(float) * nc, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(r.B[c], ck.B[c], sizeof(float) * nc, cudaMemcpyDeviceToDevice, st);
+        }
+        if (e != cudaSuccess) return PIC_ECUDA;
+        h->steps_done = s0;
+        h->time_host = ck.time;
+        h->need_sort = true;
+        a.save_ckpt = false;
+        a.rec_on = true;
+        a.rec_base = s0;
+        rc = pic_step(h, s1 - s0);
+        a.rec_on = false;
+        if (rc) return rc;
+        for (int s = s1 - 1; s >= s0; --s) {
+            const Rec &rc2 = a.rec[s - s0];
+            e = launch_adj_fields(dim, h->d_runs, a.A, (int)nc, plane, 0, rc2.time, r.dt_d, r.laser_on, a.la0, st);
+            TrajStep ts{};
+            ts.cell = rc2.pc.cell;
+            for (int c = 0; c < 3; ++c) {
+                ts.off[c] = rc2.pc.off[c];
+                ts.u[c] = rc2.pc.u[c];
+                ts.E[c] = rc2.E[c];
+                ts.B[c] = rc2.B[c];
+            }
+            ts.id = rc2.pc.id;
+            ts.n = n;
+            if (e == cudaSuccess) e = launch_adj_particles(dim, r.order, h->d_runs, a.A, ts, 0, st);
+            if (e != cudaSuccess) return PIC_ECUDA;
+        }
+    }
+    a.spent = true;  // the handle now holds a recomputed intermediate state
+    double la0 = 0.0;
+    e = cudaMemcpyAsync(&la0, a.la0, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && n_knots > 0) {
+        e = cudaMemsetAsync(a.dk, 0, sizeof(double) * n_knots, st);
+        const double ppc_t = (double)r.ppc[0] * r.ppc[1] * (dim == 3 ? r.ppc[2] : 1);
+        if (e == cudaSuccess)
+            e = launch_knots(a.A.lw, a.zb, n, n_knots, hr.sp.profile_z0, hr.sp.profile_z1, ppc_t, a.dk, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dL_dknots, a.dk, sizeof(double) * n_knots, cudaMemcpyDeviceToHost, st);
+    }
+    if (e == cudaSuccess && dL_dw) e = cudaMemcpyAsync(dL_dw, a.A.lw, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return PIC_ECUDA;
+    if (dL_da0) *dL_da0 = la0;
+    return PIC_OK;
+}
+
+int pic_adjoint_fields(pic_t *h, float *lam, float *lam_j, double t)
+{
+    if (!h || !lam) return PIC_EINVAL;
+    if (!h->started) {
+        int rc = first_step_setup(h);
+        if (rc) return rc;
+    }
+    HostRun &hr = h->runs[h->cur];
+    const Run &r = hr.r;
+    const size_t nc = (size_t)r.ncell;
+    RunState st;
+    int rc = read_state(h, h->cur, &st);
+    if (rc) return rc;
+    std::vector<float *> bufs;
+    AdjPtrs A{};
+    bool ok = true;
+    auto F = [&]() {
+        float *p = (float *)dev_alloc(h, sizeof(float) * nc);
+        ok = ok && p;
+        bufs.push_back(p);
+        return p;
+    };
+    for (int c = 0; c < 3; ++c) {
+        A.lE[c] = F();
+        A.lB[c] = F();
+        A.lJ[c] = F();
+        A.T[c] = F();
+        A.nE[c] = F();
+    }
+    double *la0 = (double *)dev_alloc(h, sizeof(double));
+    cudaError_t e = (ok && la0) ? cudaSuccess : cudaErrorMemoryAllocation;
+    for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+        e = cudaMemcpyAsync(A.lE[c], lam + c * nc, sizeof(float) * nc, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(A.lB[c], lam + (3 + c) * nc, sizeof(float) * nc, cudaMemcpyHostToDevice, h->stream);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(la0, 0, sizeof(double), h->stream);
+    if (e == cudaSuccess)
+        e = launch_adj_fields(r.dim, h->d_runs + h->cur, A, (int)nc, (int)(nc / r.n[r.dim - 1]), st.origin, t,
+                              r.dt_d, r.laser_on && st.shifts == 0, la0, h->stream);
+    for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+        e = cudaMemcpyAsync(lam + c * nc, A.lE[c], sizeof(float) * nc, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(lam + (3 + c) * nc, A.lB[c], sizeof(float) * nc, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess && lam_j)
+            e = cudaMemcpyAsync(lam_j + c * nc, A.lJ[c], sizeof(float) * nc, cudaMemcpyDeviceToHost, h->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    for (float *p : bufs) dev_free(h, p);
+    dev_free(h, la0);
+    if (!ok) return PIC_ENOMEM;
+    return e == cudaSuccess ? PIC_OK : PIC_ECUDA;
 }
 
 void pic_destroy(pic_t *h)

@@ -163,6 +163,33 @@ class Simulation:
     def sync(self):
         abi.pic_sync(self.h)
 
+    # -- adjoint ------------------------------------------------------------
+    def adjoint_begin(self, total_steps: int, checkpoint_every: int):
+        abi.check(abi.lib().pic_adjoint_begin(self.h, int(total_steps), int(checkpoint_every)), "pic_adjoint_begin")
+
+    def objective(self, z_lo: float, z_hi: float, width: float) -> float:
+        o = abi.pic_objective(z_lo, z_hi, width)
+        L = ctypes.c_double()
+        abi.check(abi.lib().pic_objective_value(self.h, ctypes.byref(o), ctypes.byref(L)), "pic_objective_value")
+        return L.value
+
+    def adjoint_backward(self, z_lo: float, z_hi: float, width: float, n_knots: int = 0, n_ids: int = 0) -> dict:
+        o = abi.pic_objective(z_lo, z_hi, width)
+        L, da0 = ctypes.c_double(), ctypes.c_double()
+        dk = np.zeros(max(n_knots, 1), np.float64)
+        dw = np.zeros(n_ids, np.float64) if n_ids else None
+        abi.check(abi.lib().pic_adjoint_backward(self.h, ctypes.byref(o), ctypes.byref(L), ctypes.byref(da0),
+                                                 _ptr(dk) if n_knots else None, int(n_knots), _ptr(dw)),
+                  "pic_adjoint_backward")
+        return {"L": L.value, "dL_da0": da0.value, "dL_dknots": dk[:n_knots], "dL_dw": dw}
+
+    def adjoint_fields(self, lam: np.ndarray, t: float):
+        """Transpose of one step's field update applied to lam[6][...]."""
+        lam = np.ascontiguousarray(lam, dtype=np.float32).copy()
+        lj = np.zeros((3,) + lam.shape[1:], np.float32)
+        abi.check(abi.lib().pic_adjoint_fields(self.h, _ptr(lam), _ptr(lj), float(t)), "pic_adjoint_fields")
+        return lam, lj
+
     def profile_begin(self, max_steps: int):
         abi.pic_profile_begin(self.h, int(max_steps))
 
