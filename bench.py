@@ -39,7 +39,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="lwfa_3d", choices=["lwfa_3d", "thermal_2d", "bunch_3d", "scan_2d"])
+    ap.add_argument("--workload", default="lwfa_3d",
+                    choices=["lwfa_3d", "thermal_2d", "bunch_3d", "scan_2d", "adjoint_2d"])
+    ap.add_argument("--adjoint-steps", type=int, default=2000)
     ap.add_argument("--scan-runs", type=int, default=64)
     ap.add_argument("--autotune", action="store_true", help="choose the tuning with the autotuner first")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink every grid axis (debug runs only)")
@@ -255,6 +257,59 @@ def scan_bench(args):
     return 0
 
 
+def adjoint_bench(args):
+    """Gradient of the trailing-window kinetic energy with respect to 32
+    density knots and a0 on the 2D LWFA box 256 x 1024 cells (dx=1, dz=0.3,
+    dt=0.28), 16 ppc, checkpoints every 100 steps: forward alone against
+    forward with checkpoints plus the reverse sweep."""
+    import torch
+    from paper_1310_0930_gb300 import inputs
+    from paper_1310_0930_gb300.sim import Simulation, TorchMemory
+
+    torch.cuda.set_device(0)
+    S = args.adjoint_steps
+    w = inputs.adjoint_2d(steps=S)
+    w.window = None
+    w.knot_z = (0.0, w.n[-1] * w.d[-1])
+    parts = inputs.background(w)
+    obj = (100.0, 300.0, 2.0)
+
+    def wall(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, out
+
+    plain = Simulation(w, per_particle_weight=True, memory=TorchMemory())
+    plain.load(parts)
+    plain.step(args.warmup)
+    plain.sync()
+    t_fwd, _ = wall(lambda: (plain.step(S), plain.sync()))
+    plain.close()
+    sim = Simulation(w, track_ids=True, per_particle_weight=True, memory=TorchMemory())
+    sim.load(parts)
+    sim.adjoint_begin(S, 100)
+    t_fwd_ck, _ = wall(lambda: (sim.step(S), sim.sync()))
+    t_bwd, res = wall(lambda: sim.adjoint_backward(*obj, n_knots=len(w.knots)))
+    sim.close()
+    n = parts.n
+    line = {"metric": METRIC, "value": n * S / (t_fwd_ck + t_bwd), "unit": UNIT, "n_gpus": 1, "steps": S,
+            "warmup": args.warmup, "ms_per_step": 1e3 * (t_fwd_ck + t_bwd) / S, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "adjoint_2d: 2D LWFA 256x1024 cells, 16 ppc, 32 density knots, a0=3, "
+                                   "%d steps, checkpoint every 100, gradient w.r.t. knots and a0" % S,
+                       "particles": n},
+            "forward_s": t_fwd, "forward_with_checkpoints_s": t_fwd_ck, "reverse_s": t_bwd,
+            "gradient_over_forward": (t_fwd_ck + t_bwd) / t_fwd,
+            "L": res["L"], "dL_da0": res["dL_da0"], "dL_dknots_norm": float(np.linalg.norm(res["dL_dknots"]))}
+    print(json.dumps(line), flush=True)
+    if args.out:
+        with open(args.out, "w") as f:
+            f.write(json.dumps(line) + "\n")
+    return 0
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -278,6 +333,8 @@ def main():
         return reference_arm(args)
     if args.workload == "scan_2d":
         return scan_bench(args)
+    if args.workload == "adjoint_2d":
+        return adjoint_bench(args)
     import torch
     import torch.distributed as dist
 

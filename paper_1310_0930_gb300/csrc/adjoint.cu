@@ -370,33 +370,46 @@ __device__ __forceinline__ void boris_vjp(float h, const float *b, const BorisTa
     }
 }
 
-template <int DIM, int P>
-__global__ void adj_particles_kernel(const Run *__restrict__ run, AdjPtrs A, TrajStep ts, int origin)
-{
-    const Run &r = *run;
-    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= ts.n) return;
-    const int32_t pc = ts.cell[s];
-    if (pc < 0) return;
-    int c[3];
-    unpack_cell(r, pc, c[0], c[1], c[2]);
-    const int nl = r.n[DIM - 1];
-    if (r.open_last) {
-        int pl = c[DIM - 1] - origin;
-        pl = pl < 0 ? pl + nl : pl;
-        if (pl < r.margin || pl >= nl - r.margin) return;  // removed before this push
+// Recorded fields / current adjoint read through global memory (absolute,
+// wrapped indices) or from a tile staged in shared memory (tile-relative).
+struct GlobalRead {
+    const float *p[9];  // E0..2, B0..2 (recorded) then lamJ0..2
+    int n0, n1, n2;
+    __device__ __forceinline__ float operator()(int comp, int i, int j, int k) const
+    {
+        return __ldg(p[comp] + wrapi(i, n0) + n0 * (wrapi(j, n1) + n1 * (n2 > 1 ? wrapi(k, n2) : 0)));
     }
-    const int id = ts.id[s];
+};
+struct SmemRead {
+    const float *f;  // 6 field components, region fvol each
+    const float *l;  // 3 current-adjoint components, region jvol each
+    int fvol, fh0, fh1, fh2, fs0, fs01;
+    int jvol, jh0, jh1, jh2, js0, js01;
+    __device__ __forceinline__ float operator()(int comp, int i, int j, int k) const
+    {
+        return comp < 6 ? f[comp * fvol + (i + fh0) + fs0 * (j + fh1) + fs01 * (k + fh2)]
+                        : l[(comp - 6) * jvol + (i + jh0) + js0 * (j + jh1) + js01 * (k + jh2)];
+    }
+};
+
+// One recorded particle's adjoint.  c: cell in the reader's frame; org:
+// offset from that frame to absolute cells (scatter and absorption use
+// absolute cells); rd(comp 0..5, ...) reads the recorded fields,
+// rd(6 + comp, ...) the current adjoint.
+template <int DIM, int P, class RD>
+__device__ __forceinline__ void adj_one(const Run &r, const AdjPtrs &A, const TrajStep &ts, long long s,
+                                        int origin, const int *c, const int *org, const RD &rd)
+{
+    const int nl = r.n[DIM - 1];
     float d[3] = {0.f, 0.f, 0.f}, u[3];
     for (int a = 0; a < DIM; ++a) d[a] = ts.off[a][s];
     for (int a = 0; a < 3; ++a) u[a] = ts.u[a][s];
-    const float w = A.wid[id];
+    const float w = ts.w[s];
     const GF gf{{ts.E[0], ts.E[1], ts.E[2], ts.B[0], ts.B[1], ts.B[2]}, r.n[0], r.n[1], DIM == 3 ? r.n[2] : 1};
+    const int ox = org[0], oy = org[1], oz = org[2];
     // --- forward recompute: shapes and gather with position derivatives ---
     int bn[3] = {0, 0, 0}, bh[3] = {0, 0, 0};
-    float wn[3][P + 1], wh[3][P + 1], dwn[3][P + 1], dwh[3][P + 1];
-    for (int a = 0; a < 3; ++a)
-        for (int q = 0; q <= P; ++q) wn[a][q] = wh[a][q] = dwn[a][q] = dwh[a][q] = 0.f;
+    float wn[DIM][P + 1], wh[DIM][P + 1], dwn[DIM][P + 1], dwh[DIM][P + 1];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
         ShapeD<P>::node(c[a], d[a], bn[a], wn[a], dwn[a]);
@@ -404,7 +417,7 @@ __global__ void adj_particles_kernel(const Run *__restrict__ run, AdjPtrs A, Tra
     }
     // half-integer flags per component (E0 E1 E2 B0 B1 B2) and axis
     const unsigned hxm = 0x31u, hym = 0x2Au, hzm = 0x1Cu;
-    float eb[6], deb[6][3];
+    float eb[6], deb[6][DIM];
 #pragma unroll
     for (int comp = 0; comp < 6; ++comp) {
         const bool hx = (hxm >> comp) & 1u, hy = (hym >> comp) & 1u, hz = (hzm >> comp) & 1u;
@@ -412,26 +425,30 @@ __global__ void adj_particles_kernel(const Run *__restrict__ run, AdjPtrs A, Tra
         float v = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
 #pragma unroll
         for (int kc = 0; kc < (DIM == 3 ? P + 1 : 1); ++kc) {
-            const float wz = DIM == 3 ? (hz ? wh[2][kc] : wn[2][kc]) : 1.f;
-            const float dwz = DIM == 3 ? (hz ? dwh[2][kc] : dwn[2][kc]) : 0.f;
+            const float wz = DIM == 3 ? (hz ? wh[DIM - 1][kc] : wn[DIM - 1][kc]) : 1.f;
+            const float dwz = DIM == 3 ? (hz ? dwh[DIM - 1][kc] : dwn[DIM - 1][kc]) : 0.f;
 #pragma unroll
             for (int kb = 0; kb <= P; ++kb) {
                 const float wy = hy ? wh[1][kb] : wn[1][kb], dwy = hy ? dwh[1][kb] : dwn[1][kb];
+                const float wyz = wy * wz;
+                float sx = 0.f, sdx = 0.f;
 #pragma unroll
                 for (int ka = 0; ka <= P; ++ka) {
                     const float wx = hx ? wh[0][ka] : wn[0][ka], dwx = hx ? dwh[0][ka] : dwn[0][ka];
-                    const float F = __ldg(gf.p[comp] + gf.at(b0 + ka, b1 + kb, b2 + kc));
-                    v += wx * wy * wz * F;
-                    g0 += dwx * wy * wz * F;
-                    g1 += wx * dwy * wz * F;
-                    g2 += wx * wy * dwz * F;
+                    const float F = rd(comp, b0 + ka, b1 + kb, b2 + kc);
+                    sx = fmaf(wx, F, sx);
+                    sdx = fmaf(dwx, F, sdx);
                 }
+                v = fmaf(wyz, sx, v);
+                g0 = fmaf(wyz, sdx, g0);
+                g1 = fmaf(dwy * wz, sx, g1);
+                g2 = fmaf(wy * dwz, sx, g2);
             }
         }
         eb[comp] = v;
         deb[comp][0] = g0;
         deb[comp][1] = g1;
-        deb[comp][2] = g2;
+        if (DIM == 3) deb[comp][DIM - 1] = g2;
     }
     BorisTape tp;
     float un[3];
@@ -455,21 +472,23 @@ __global__ void adj_particles_kernel(const Run *__restrict__ run, AdjPtrs A, Tra
     if (!ok) return;
     bool absorbed = false;
     if (r.open_last) {
-        int cl = wrapi(c[DIM - 1] + k[DIM - 1], nl) - origin;
+        int cl = wrapi(c[DIM - 1] + org[DIM - 1] + k[DIM - 1], nl) - origin;
         cl = cl < 0 ? cl + nl : cl;
         absorbed = cl < r.margin || cl >= nl - r.margin;
     }
     // --- adjoint inputs: state adjoints of x^{n+1}, u^{n+1/2} ---
     float lxn[3] = {0.f, 0.f, 0.f}, lun[3] = {0.f, 0.f, 0.f};
     if (!absorbed) {
-        for (int a = 0; a < DIM; ++a) lxn[a] = A.lx[a][id];
-        for (int a = 0; a < 3; ++a) lun[a] = A.lu[a][id];
+        for (int a = 0; a < DIM; ++a) lxn[a] = A.sx[a][s];
+        for (int a = 0; a < 3; ++a) lun[a] = A.su[a][s];
     }
     // --- deposit transpose (Esirkepov window, per unit weight) ---
     constexpr int W = P + 2;
-    float S0[3][W], S1[3][W], dS0[3][W], dS1[3][W];
+    float S0[DIM][W], S1[DIM][W], dS0[DIM][W], dS1[DIM][W];
     int wb[3] = {0, 0, 0};
-    for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
         for (int q = 0; q < W; ++q) S0[a][q] = S1[a][q] = dS0[a][q] = dS1[a][q] = 0.f;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
@@ -499,9 +518,11 @@ __global__ void adj_particles_kernel(const Run *__restrict__ run, AdjPtrs A, Tra
             }
         }
     }
-    float As[3][W], DS[3][W], Pr[3][W];
-    for (int a = 0; a < 3; ++a) {
+    float As[DIM][W], DS[DIM][W], Pr[DIM][W];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
         float run_ = 0.f;
+#pragma unroll
         for (int q = 0; q < W; ++q) {
             DS[a][q] = S1[a][q] - S0[a][q];
             As[a][q] = S0[a][q] + 0.5f * DS[a][q];
@@ -511,16 +532,21 @@ __global__ void adj_particles_kernel(const Run *__restrict__ run, AdjPtrs A, Tra
     }
     const float q_ = r.q;
     const float vz = un[2] * ig;
-    float gA[3][W], gD[3][W];
-    for (int a = 0; a < 3; ++a)
+    float gA[DIM][W], gD[DIM][W];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
         for (int q = 0; q < W; ++q) gA[a][q] = gD[a][q] = 0.f;
     float lw = 0.f, gvz = 0.f;
-    auto lam = [&](int comp, int i, int j, int kk) { return __ldg(A.lJ[comp] + gf.at(i, j, kk)); };
+    auto lam = [&](int comp, int i, int j, int kk) { return rd(6 + comp, i, j, kk); };
     if (DIM == 2) {
         const float cx = -q_ * r.d_over_dt[0], cy = -q_ * r.d_over_dt[1];
         float Rx[W], Ry[W];
+#pragma unroll
         for (int q = 0; q < W; ++q) Rx[q] = Ry[q] = 0.f;
+#pragma unroll
         for (int qb = 0; qb < W; ++qb)
+#pragma unroll
             for (int qa = 0; qa < W; ++qa) {
                 const int i = wb[0] + qa, j = wb[1] + qb;
                 if (qa < W - 1) {  // J_x = cx P_x A_y
@@ -548,6 +574,7 @@ __global__ void adj_particles_kernel(const Run *__restrict__ run, AdjPtrs A, Tra
             }
         // prefix transposes: d/dDS[a'] of sum_a R[a] P[a] = sum_{a>=a'} R[a]
         float sx = 0.f, sy = 0.f;
+#pragma unroll
         for (int q = W - 2; q >= 0; --q) {
             sx += Rx[q];
             sy += Ry[q];
@@ -555,8 +582,9 @@ __global__ void adj_particles_kernel(const Run *__restrict__ run, AdjPtrs A, Tra
             gD[1][q] += w * cy * sy;
         }
     } else {
+#pragma unroll
         for (int comp = 0; comp < 3; ++comp) {
-            const int a = comp, b = (comp + 1) % 3, cc = (comp + 2) % 3;
+            const int a = comp % DIM, b = (comp + 1) % DIM, cc = (comp + 2) % DIM;
             const float coef = -q_ * r.d_over_dt[a];
             float R[W];
             for (int q = 0; q < W; ++q) R[q] = 0.f;
@@ -590,6 +618,7 @@ __global__ void adj_particles_kernel(const Run *__restrict__ run, AdjPtrs A, Tra
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
         float go = 0.f, gn = 0.f;
+#pragma unroll
         for (int q = 0; q < W; ++q) {
             go += (0.5f * gA[a][q] - gD[a][q]) * dS0[a][q];
             gn += (0.5f * gA[a][q] + gD[a][q]) * dS1[a][q];
@@ -626,21 +655,134 @@ __global__ void adj_particles_kernel(const Run *__restrict__ run, AdjPtrs A, Tra
         float *dst = comp < 3 ? A.lE[comp] : A.lB[comp - 3];
 #pragma unroll
         for (int kc = 0; kc < (DIM == 3 ? P + 1 : 1); ++kc) {
-            const float wz = DIM == 3 ? (hz ? wh[2][kc] : wn[2][kc]) : 1.f;
+            const float wz = DIM == 3 ? (hz ? wh[DIM - 1][kc] : wn[DIM - 1][kc]) : 1.f;
 #pragma unroll
             for (int kb = 0; kb <= P; ++kb) {
                 const float wy = hy ? wh[1][kb] : wn[1][kb];
 #pragma unroll
                 for (int ka = 0; ka <= P; ++ka) {
                     const float wx = hx ? wh[0][ka] : wn[0][ka];
-                    atomicAdd(dst + gf.at(b0 + ka, b1 + kb, b2 + kc), L * wx * wy * wz);
+                    atomicAdd(dst + gf.at(b0 + ka + ox, b1 + kb + oy, b2 + kc + oz), L * wx * wy * wz);
                 }
             }
         }
     }
-    for (int a = 0; a < DIM; ++a) A.lx[a][id] = lxo[a];
-    for (int a = 0; a < 3; ++a) A.lu[a][id] = lu0[a];
-    A.lw[id] += (double)lw;
+    for (int a = 0; a < DIM; ++a) A.sx[a][s] = lxo[a];
+    for (int a = 0; a < 3; ++a) A.su[a][s] = lu0[a];
+    A.sw[s] += (double)lw;
+}
+
+template <int DIM>
+__device__ __forceinline__ bool adj_live(const Run &r, int32_t pc, int origin, int *c)
+{
+    if (pc < 0) return false;
+    unpack_cell(r, pc, c[0], c[1], c[2]);
+    if (r.open_last) {
+        const int nl = r.n[DIM - 1];
+        int pl = c[DIM - 1] - origin;
+        pl = pl < 0 ? pl + nl : pl;
+        if (pl < r.margin || pl >= nl - r.margin) return false;  // removed before this push
+    }
+    return true;
+}
+
+// Flat form: one thread per recorded slot, everything through global memory.
+template <int DIM, int P>
+__global__ void __launch_bounds__(128, 3) adj_particles_kernel(const Run *__restrict__ run, AdjPtrs A, TrajStep ts,
+                                                               int origin)
+{
+    const Run &r = *run;
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= ts.n) return;
+    int c[3] = {0, 0, 0};
+    if (!adj_live<DIM>(r, ts.cell[s], origin, c)) return;
+    const GlobalRead g{{ts.E[0], ts.E[1], ts.E[2], ts.B[0], ts.B[1], ts.B[2], A.lJ[0], A.lJ[1], A.lJ[2]},
+                       r.n[0], r.n[1], DIM == 3 ? r.n[2] : 1};
+    const int org[3] = {0, 0, 0};
+    adj_one<DIM, P>(r, A, ts, s, origin, c, org, g);
+}
+
+// Tiled form: one CTA per tile of the sort recorded with the step; the
+// tile's recorded fields and current adjoint (plus halos wide enough for
+// particles within `drift` cells of the tile) are staged in shared memory.
+template <int DIM, int P>
+__global__ void __launch_bounds__(128, 3) adj_particles_tiled_kernel(const Run *__restrict__ run, AdjPtrs A,
+                                                                     TrajStep ts, int origin)
+{
+    extern __shared__ float sm[];
+    const Run &r = *run;
+    const int t = blockIdx.x;
+    const long long p0 = ts.tile_off[t], p1 = ts.tile_off[t + 1];
+    if (p0 >= p1) return;
+    const int D = r.drift;
+    const int n0 = r.n[0], n1 = r.n[1], n2 = DIM == 3 ? r.n[2] : 1;
+    int org[3] = {0, 0, 0}, T[3] = {1, 1, 1}, fh[3] = {0, 0, 0}, fs[3] = {1, 1, 1}, jh[3] = {0, 0, 0},
+        js[3] = {1, 1, 1};
+    org[0] = (t % r.nt[0]) << r.tlog[0];
+    org[1] = ((t / r.nt[0]) % r.nt[1]) << r.tlog[1];
+    if (DIM == 3) org[2] = (t / (r.nt[0] * r.nt[1])) << r.tlog[2];
+    for (int a = 0; a < DIM; ++a) {
+        T[a] = 1 << r.tlog[a];
+        fh[a] = D + Reach<P>::GLO;
+        fs[a] = T[a] + 2 * D + Reach<P>::GLO + Reach<P>::GHI;
+        jh[a] = D + Reach<P>::DLO;
+        js[a] = T[a] + 2 * D + Reach<P>::DLO + Reach<P>::DHI;
+    }
+    const int fvol = fs[0] * fs[1] * fs[2], jvol = js[0] * js[1] * js[2];
+    float *F = sm, *L = sm + 6 * fvol;
+    for (int l = threadIdx.x; l < fvol; l += blockDim.x) {
+        const int lx = l % fs[0], ly = (l / fs[0]) % fs[1], lz = l / (fs[0] * fs[1]);
+        const int g = modi(org[0] - fh[0] + lx, n0) +
+                      n0 * (modi(org[1] - fh[1] + ly, n1) + n1 * (DIM == 3 ? modi(org[2] - fh[2] + lz, n2) : 0));
+        for (int c = 0; c < 3; ++c) {
+            F[c * fvol + l] = __ldg(ts.E[c] + g);
+            F[(3 + c) * fvol + l] = __ldg(ts.B[c] + g);
+        }
+    }
+    for (int l = threadIdx.x; l < jvol; l += blockDim.x) {
+        const int lx = l % js[0], ly = (l / js[0]) % js[1], lz = l / (js[0] * js[1]);
+        const int g = modi(org[0] - jh[0] + lx, n0) +
+                      n0 * (modi(org[1] - jh[1] + ly, n1) + n1 * (DIM == 3 ? modi(org[2] - jh[2] + lz, n2) : 0));
+        for (int c = 0; c < 3; ++c) L[c * jvol + l] = __ldg(A.lJ[c] + g);
+    }
+    __syncthreads();
+    const SmemRead sr{F, L, fvol, fh[0], fh[1], fh[2], fs[0], fs[0] * fs[1],
+                      jvol, jh[0], jh[1], jh[2], js[0], js[0] * js[1]};
+    const GlobalRead g{{ts.E[0], ts.E[1], ts.E[2], ts.B[0], ts.B[1], ts.B[2], A.lJ[0], A.lJ[1], A.lJ[2]},
+                       n0, n1, n2};
+    const int zero[3] = {0, 0, 0};
+    for (long long s = p0 + threadIdx.x; s < p1; s += blockDim.x) {
+        int c[3] = {0, 0, 0};
+        if (!adj_live<DIM>(r, ts.cell[s], origin, c)) continue;
+        int rel[3] = {0, 0, 0};
+        bool fast = true;
+        for (int a = 0; a < DIM; ++a) {
+            int v = c[a] - org[a];
+            if (v < -D) v += r.n[a];
+            else if (v >= T[a] + D) v -= r.n[a];
+            rel[a] = v;
+            fast = fast && v >= -D && v < T[a] + D;
+        }
+        if (fast) adj_one<DIM, P>(r, A, ts, s, origin, rel, org, sr);
+        else adj_one<DIM, P>(r, A, ts, s, origin, c, zero, g);
+    }
+}
+
+__global__ void adj_perm_kernel(AdjPtrs A, const int32_t *__restrict__ id, long long n, int dim, int to_slots)
+{
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        const int i = id[s];
+        if (i < 0 || i >= n) continue;
+        if (to_slots) {
+            for (int a = 0; a < dim; ++a) A.sx[a][s] = A.lx[a][i];
+            for (int a = 0; a < 3; ++a) A.su[a][s] = A.lu[a][i];
+            A.sw[s] = A.lw[i];
+        } else {
+            for (int a = 0; a < dim; ++a) A.lx[a][i] = A.sx[a][s];
+            for (int a = 0; a < 3; ++a) A.lu[a][i] = A.su[a][s];
+            A.lw[i] = A.sw[s];
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -722,22 +864,28 @@ __global__ void obj_seed_kernel(const Run *__restrict__ run, int origin, ObjArgs
 __global__ void knots_kernel(const double *lw, const float *zb, long long n, int n_knots, double z0, double z1,
                              double ppc_t, double *out)
 {
+    __shared__ double acc[1024];  // per-block partial sums, one atomic per knot per block
+    for (int k = threadIdx.x; k < n_knots; k += blockDim.x) acc[k] = 0.0;
+    __syncthreads();
     for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < n;
          id += (long long)gridDim.x * blockDim.x) {
         const double g = lw[id] / ppc_t;
         if (g == 0.0) continue;
         double f = ((double)zb[id] - z0) / (z1 - z0) * (n_knots - 1);
         if (n_knots == 1 || f <= 0.0) {
-            atomicAdd(out, g);
+            atomicAdd(acc, g);
         } else if (f >= n_knots - 1) {
-            atomicAdd(out + n_knots - 1, g);
+            atomicAdd(acc + n_knots - 1, g);
         } else {
             const int i = (int)floor(f);
             const double t = f - i;
-            atomicAdd(out + i, g * (1.0 - t));
-            atomicAdd(out + i + 1, g * t);
+            atomicAdd(acc + i, g * (1.0 - t));
+            atomicAdd(acc + i + 1, g * t);
         }
     }
+    __syncthreads();
+    for (int k = threadIdx.x; k < n_knots; k += blockDim.x)
+        if (acc[k] != 0.0) atomicAdd(out + k, acc[k]);
 }
 
 // weights and birth positions by id (the load order, before any sort)
@@ -815,21 +963,46 @@ cudaError_t launch_adj_fields(int dim, const Run *run, const AdjPtrs &A, int nce
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_particles(int dim, int order, const Run *run, const AdjPtrs &A, const TrajStep &ts, int origin,
-                                 cudaStream_t st)
+template <int DIM, int P>
+cudaError_t launch_adj_t(const Run *run, const Run &hr, const AdjPtrs &A, const TrajStep &ts, int origin,
+                         cudaStream_t st)
+{
+    constexpr int kAdjBlock = 128;  // matches the kernels' launch bounds
+    if (!ts.tile_off) {
+        const unsigned g = (unsigned)((ts.n + kAdjBlock - 1) / kAdjBlock);
+        adj_particles_kernel<DIM, P><<<g, kAdjBlock, 0, st>>>(run, A, ts, origin);
+        return cudaGetLastError();
+    }
+    size_t fv = 1, jv = 1;
+    for (int a = 0; a < DIM; ++a) {
+        const int T = 1 << hr.tlog[a];
+        fv *= (size_t)(T + 2 * hr.drift + Reach<P>::GLO + Reach<P>::GHI);
+        jv *= (size_t)(T + 2 * hr.drift + Reach<P>::DLO + Reach<P>::DHI);
+    }
+    const size_t smem = sizeof(float) * (6 * fv + 3 * jv);
+    auto k = adj_particles_tiled_kernel<DIM, P>;
+    static size_t attr = 0;
+    if (smem > attr) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = smem;
+    }
+    k<<<hr.ntiles, kAdjBlock, smem, st>>>(run, A, ts, origin);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_particles(int dim, int order, const Run *run, const Run &hr, const AdjPtrs &A,
+                                 const TrajStep &ts, int origin, cudaStream_t st)
 {
     if (ts.n <= 0) return cudaSuccess;
-    const unsigned g = (unsigned)((ts.n + kBlock - 1) / kBlock);
     if (dim == 2) {
-        if (order == 1) adj_particles_kernel<2, 1><<<g, kBlock, 0, st>>>(run, A, ts, origin);
-        else if (order == 2) adj_particles_kernel<2, 2><<<g, kBlock, 0, st>>>(run, A, ts, origin);
-        else adj_particles_kernel<2, 3><<<g, kBlock, 0, st>>>(run, A, ts, origin);
-    } else {
-        if (order == 1) adj_particles_kernel<3, 1><<<g, kBlock, 0, st>>>(run, A, ts, origin);
-        else if (order == 2) adj_particles_kernel<3, 2><<<g, kBlock, 0, st>>>(run, A, ts, origin);
-        else adj_particles_kernel<3, 3><<<g, kBlock, 0, st>>>(run, A, ts, origin);
+        if (order == 1) return launch_adj_t<2, 1>(run, hr, A, ts, origin, st);
+        if (order == 2) return launch_adj_t<2, 2>(run, hr, A, ts, origin, st);
+        return launch_adj_t<2, 3>(run, hr, A, ts, origin, st);
     }
-    return cudaGetLastError();
+    if (order == 1) return launch_adj_t<3, 1>(run, hr, A, ts, origin, st);
+    if (order == 2) return launch_adj_t<3, 2>(run, hr, A, ts, origin, st);
+    return launch_adj_t<3, 3>(run, hr, A, ts, origin, st);
 }
 
 cudaError_t launch_objective(const Run *run, int origin, const ObjArgs &o, double *red, long long cap, int seed,
@@ -844,10 +1017,17 @@ cudaError_t launch_objective(const Run *run, int origin, const ObjArgs &o, doubl
     return cudaGetLastError();
 }
 
+cudaError_t launch_adj_perm(int dim, const AdjPtrs &A, const int32_t *id, long long n, int to_slots, cudaStream_t st)
+{
+    adj_perm_kernel<<<blocks_for(n), kBlock, 0, st>>>(A, id, n, dim, to_slots);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_knots(const double *lw, const float *zb, long long n, int n_knots, double z0, double z1,
                          double ppc_t, double *out, cudaStream_t st)
 {
-    knots_kernel<<<blocks_for(n), kBlock, 0, st>>>(lw, zb, n, n_knots, z0, z1, ppc_t, out);
+    const unsigned g = blocks_for(n) < 608 ? blocks_for(n) : 608;
+    knots_kernel<<<g, kBlock, 0, st>>>(lw, zb, n, n_knots, z0, z1, ppc_t, out);
     return cudaGetLastError();
 }
 

@@ -63,13 +63,17 @@ struct AdjPtrs {
     float *lx[3], *lu[3];                         // particle adjoints by id
     double *lw;                                   // dL/dw by id
     float *wid;                                   // weight by id
+    float *sx[3], *su[3];                         // particle adjoints by slot of the current record
+    double *sw;
 };
 // one recorded step: the particles and fields the push of that step read
 struct TrajStep {
     const int32_t *cell;
     const float *off[3];
     const float *u[3];
+    const float *w;
     const int32_t *id;
+    const int32_t *tile_off;  // tile offsets of the sort these slots follow (null: flat kernel)
     long long n;
     const float *E[3];
     const float *B[3];
@@ -79,8 +83,8 @@ struct ObjArgs {
 };
 cudaError_t launch_adj_fields(int dim, const Run *run, const AdjPtrs &A, int ncell, int plane, int origin, double t_n,
                               double dt, int laser_on, double *la0, cudaStream_t st);
-cudaError_t launch_adj_particles(int dim, int order, const Run *run, const AdjPtrs &A, const TrajStep &ts, int origin,
-                                 cudaStream_t st);
+cudaError_t launch_adj_particles(int dim, int order, const Run *run, const Run &host_run, const AdjPtrs &A,
+                                 const TrajStep &ts, int origin, cudaStream_t st);
 // seed == 0: reduce sum w K sigma and sum w sigma into red[0..1]; seed == 1: seed the adjoints
 cudaError_t launch_objective(const Run *run, int origin, const ObjArgs &o, double *red, long long cap, int seed,
                              const AdjPtrs &A, cudaStream_t st);
@@ -95,5 +99,7 @@ struct PartCopy {
     int32_t *id; // may be null
 };
 cudaError_t launch_part_copy(const Run *run, const PartCopy &pc, long long n, int restore, cudaStream_t st);
+// move the particle adjoints between id order and the slot order of a record
+cudaError_t launch_adj_perm(int dim, const AdjPtrs &A, const int32_t *id, long long n, int to_slots, cudaStream_t st);
 
 }  // namespace pic

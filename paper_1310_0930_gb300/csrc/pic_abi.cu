@@ -41,7 +41,9 @@ struct Ckpt {
 struct Rec {
     PartCopy pc;
     float *E[3], *B[3];
+    int32_t *tile_off;  // tile offsets of the last sort (the slots' grouping)
     double time;
+    bool sorted;  // a tile sort ran just before this record (slot order changed)
 };
 struct Adj {
     int K = 1, total = 0, nck = 0;
@@ -326,7 +328,11 @@ int enqueue_step(pic_s *h, bool sort)
         Rec &rc = h->adj->rec[h->steps_done - h->adj->rec_base];
         const Run &r0 = h->runs[0].r;
         rc.time = h->time_host;
+        rc.sorted = sort;
         e = launch_part_copy(R, rc.pc, h->adj->nid, 0, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(rc.tile_off, r0.tile_off, sizeof(int32_t) * (r0.ntiles + 1), cudaMemcpyDeviceToDevice,
+                                st);
         for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
             e = cudaMemcpyAsync(rc.E[c], r0.E[c], sizeof(float) * r0.ncell, cudaMemcpyDeviceToDevice, st);
             if (e == cudaSuccess)
@@ -936,10 +942,14 @@ int pic_adjoint_begin(pic_t *h, int32_t total_steps, int32_t checkpoint_every)
         a->A.nE[c] = F(nc);
         a->A.lu[c] = F(n);
         a->A.lx[c] = c < dim ? F(n) : nullptr;
+        a->A.su[c] = F(n);
+        a->A.sx[c] = c < dim ? F(n) : nullptr;
         ok = ok && a->A.lE[c] && a->A.lB[c] && a->A.lJ[c] && a->A.T[c] && a->A.nE[c] && a->A.lu[c] &&
-             (c >= dim || a->A.lx[c]);
+             (c >= dim || a->A.lx[c]) && a->A.su[c] && (c >= dim || a->A.sx[c]);
     }
     a->A.lw = (double *)dev_alloc(h, sizeof(double) * n);
+    a->A.sw = (double *)dev_alloc(h, sizeof(double) * n);
+    ok = ok && a->A.sw;
     a->A.wid = F(n);
     a->zb = F(n);
     a->la0 = (double *)dev_alloc(h, sizeof(double) * 4);
@@ -970,7 +980,9 @@ int pic_adjoint_begin(pic_t *h, int32_t total_steps, int32_t checkpoint_every)
     }
     a->rec.resize(a->K);
     for (Rec &rc2 : a->rec) {
-        rc2.pc = part(false);
+        rc2.pc = part(true);
+        rc2.tile_off = (int32_t *)dev_alloc(h, sizeof(int32_t) * (r.ntiles + 1));
+        ok = ok && rc2.tile_off;
         for (int c = 0; c < 3; ++c) {
             rc2.E[c] = F(nc);
             rc2.B[c] = F(nc);
@@ -1069,6 +1081,10 @@ int pic_adjoint_backward(pic_t *h, const pic_objective *obj, double *L, double *
         rc = pic_step(h, s1 - s0);
         a.rec_on = false;
         if (rc) return rc;
+        // particle adjoints follow the slot order of each record; they pass
+        // through id order where that order changes (sorts, segment ends)
+        e = launch_adj_perm(dim, a.A, a.rec[s1 - 1 - s0].pc.id, n, 1, st);
+        if (e != cudaSuccess) return PIC_ECUDA;
         for (int s = s1 - 1; s >= s0; --s) {
             const Rec &rc2 = a.rec[s - s0];
             e = launch_adj_fields(dim, h->d_runs, a.A, (int)nc, plane, 0, rc2.time, r.dt_d, r.laser_on, a.la0, st);
@@ -1081,8 +1097,13 @@ int pic_adjoint_backward(pic_t *h, const pic_objective *obj, double *L, double *
                 ts.B[c] = rc2.B[c];
             }
             ts.id = rc2.pc.id;
+            ts.w = rc2.pc.w;
+            ts.tile_off = rc2.tile_off;
             ts.n = n;
-            if (e == cudaSuccess) e = launch_adj_particles(dim, r.order, h->d_runs, a.A, ts, 0, st);
+            if (e == cudaSuccess) e = launch_adj_particles(dim, r.order, h->d_runs, r, a.A, ts, 0, st);
+            if (e == cudaSuccess && (s == s0 || rc2.sorted)) e = launch_adj_perm(dim, a.A, rc2.pc.id, n, 0, st);
+            if (e == cudaSuccess && s > s0 && rc2.sorted)
+                e = launch_adj_perm(dim, a.A, a.rec[s - 1 - s0].pc.id, n, 1, st);
             if (e != cudaSuccess) return PIC_ECUDA;
         }
     }
