@@ -281,13 +281,14 @@ def adjoint_bench(args):
         torch.cuda.synchronize()
         return time.perf_counter() - t0, out
 
-    plain = Simulation(w, per_particle_weight=True, memory=TorchMemory())
+    tuning = json.loads(args.tuning) if args.tuning else None
+    plain = Simulation(w, per_particle_weight=True, tuning=tuning, memory=TorchMemory())
     plain.load(parts)
     plain.step(args.warmup)
     plain.sync()
     t_fwd, _ = wall(lambda: (plain.step(S), plain.sync()))
     plain.close()
-    sim = Simulation(w, track_ids=True, per_particle_weight=True, memory=TorchMemory())
+    sim = Simulation(w, track_ids=True, per_particle_weight=True, tuning=tuning, memory=TorchMemory())
     sim.load(parts)
     sim.adjoint_begin(S, 100)
     t_fwd_ck, _ = wall(lambda: (sim.step(S), sim.sync()))
@@ -300,7 +301,7 @@ def adjoint_bench(args):
             "config": {"workload": "adjoint_2d: 2D LWFA 256x1024 cells, 16 ppc, 32 density knots, a0=3, "
                                    "%d steps, checkpoint every 100, gradient w.r.t. knots and a0" % S,
                        "particles": n},
-            "forward_s": t_fwd, "forward_with_checkpoints_s": t_fwd_ck, "reverse_s": t_bwd,
+            "tuning": tuning, "forward_s": t_fwd, "forward_with_checkpoints_s": t_fwd_ck, "reverse_s": t_bwd,
             "gradient_over_forward": (t_fwd_ck + t_bwd) / t_fwd,
             "L": res["L"], "dL_da0": res["dL_da0"], "dL_dknots_norm": float(np.linalg.norm(res["dL_dknots"]))}
     print(json.dumps(line), flush=True)
