@@ -21,6 +21,12 @@ struct Seg {
 
 constexpr int kBlock = 256;
 
+// Tile sort (sort.cu): one CTA of kSortThreads threads ranks a chunk of
+// kSortChunk particle slots in a shared-memory key table of kSortHash
+// entries; the particle segments of the sort are in units of chunks.
+constexpr int kSortThreads = 256, kSortItems = 8, kSortGroup = 4, kSortChunk = kSortThreads * kSortItems;
+constexpr int kSortHashLog = 9, kSortHash = 1 << kSortHashLog, kSortProbe = 32;
+
 // Particle kernel (push.cuh) over the compiled tile menu (push_menu.h).
 // push_smem_bytes returns 0 for a (tile, drift) pair that is not compiled.
 int push_default_drift(int dim, const int *tile);

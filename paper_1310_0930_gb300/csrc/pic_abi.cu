@@ -201,11 +201,11 @@ int upload_runs(pic_s *h)
     return cuda_fail(e);
 }
 
-int set_seg(pic_s *h, int which, Seg &seg, const std::vector<long long> &items_per_run)
+int set_seg(pic_s *h, int which, Seg &seg, const std::vector<long long> &items_per_run, int unit = kBlock)
 {
     std::vector<int> start(h->nruns + 1, 0);
     for (int i = 0; i < h->nruns; ++i)
-        start[i + 1] = start[i] + (int)((items_per_run[i] + kBlock - 1) / kBlock);
+        start[i + 1] = start[i] + (int)((items_per_run[i] + unit - 1) / unit);
     int *dst = h->d_seg + which * (h->nruns + 1);
     cudaError_t e = cudaMemcpyAsync(dst, start.data(), sizeof(int) * (h->nruns + 1), cudaMemcpyHostToDevice,
                                     h->stream);
@@ -378,7 +378,7 @@ int first_step_setup(pic_s *h)
         inj[i] = hr.inject_per_shift;
     }
     int rc = upload_runs(h);
-    if (!rc) rc = set_seg(h, 2, h->seg_parts, parts);
+    if (!rc) rc = set_seg(h, 2, h->seg_parts, parts, kSortChunk);
     if (!rc) rc = set_seg(h, 3, h->seg_inject, inj);
     if (!rc) rc = build_items(h);
     if (rc) return rc;

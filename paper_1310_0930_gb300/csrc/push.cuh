@@ -12,13 +12,18 @@
 // reduction of the copies).
 //
 // The J tile holds each value as two int32 words (hi, lo) of a fixed-point
-// number with a per-tile scale S = 2^30 / (1.01 sum |q w|): every single
-// contribution c satisfies |c| <= |q w| |v| <= |q w|, so |sum hi| < 2^31;
-// lo carries 12 more bits of the remainder.  Native int32 shared-memory
-// atomics replace FP32 ones (which the hardware emulates with a
-// compare-and-swap loop), integer sums are order-independent, and the
-// resolution, 2^-42 of the tile's total |q w|, is finer than FP32 rounding
-// of the per-node sums.
+// number with a per-tile scale S = min(2^30 / (1.01 sum |q w|),
+// 4e6 / max |q w|): every single contribution c satisfies
+// |c| <= |q w| |v| <= |q w|, so |sum hi| < 2^31 and every scaled
+// contribution is below 2^22 in magnitude; lo carries 12 more bits of the
+// remainder.  Native int32 shared-memory atomics replace FP32 ones (which
+// the hardware emulates with a compare-and-swap loop), integer sums are
+// order-independent, and the resolution (2^-42 of the tile's total |q w|
+// for tiles of 256 or more equal-weight particles) is finer than FP32
+// rounding of the per-node sums.  Because scaled values stay below 2^22,
+// both words are rounded to integers by the floating-point add of
+// 1.5 * 2^23 (which leaves round-to-nearest(v) in the low mantissa bits)
+// instead of conversion instructions.
 //
 // Tile geometry and the drift allowance are template parameters, so every
 // shared-memory address in a particle's stencil is a base register plus an
@@ -34,6 +39,9 @@ namespace pic {
 namespace push_detail {
 
 constexpr float kLoScale = 4096.f;  // 12 bits for the lo word
+constexpr float kRound = 12582912.f;  // 1.5 * 2^23: v + kRound = 2^23 + 2^22 + rint(v) for |v| < 2^22
+constexpr int kRoundBits = 0x4B400000;  // bit pattern of kRound
+constexpr float kMaxScaled = 4.0e6f;  // bound on one scaled contribution (< 2^22, with margin)
 
 template <int DIM, int P, int TX, int TY, int TZ, int D>
 struct Geo {
@@ -274,17 +282,18 @@ struct SmemGather {
     }
 };
 
-// Add one value to the fixed-point J tile: x = value * S split into the
-// rounded integer part (hi) and 12 bits of remainder (lo).  x is computed as
-// ps * fac with ps already scaled by S.
+// Add one value to the fixed-point J tile: x = value * S (|x| < 2^22) split
+// into its nearest integer (hi) and 12 bits of the remainder (lo).  x is
+// computed as ps * fac with ps already scaled by S.
 __device__ __forceinline__ void fix_add(int *hi_base, int *lo_base, int off, float ps, float fac)
 {
     const float x = ps * fac;
     if (x == 0.f) return;
-    const float h = rintf(x);  // exact integer (|x| <= 2^30; above 2^24 x is already integral)
-    const float rem = fmaf(ps, fac, -h);
-    atomicAdd(hi_base + off, (int)h);
-    atomicAdd(lo_base + off, __float2int_rn(rem * kLoScale));
+    const float t = x + kRound;                 // kRound + rint(x), exact
+    const float rem = fmaf(ps, fac, kRound - t);  // x - rint(x), |rem| <= 1/2
+    const float tl = fmaf(rem, kLoScale, kRound);
+    atomicAdd(hi_base + off, __float_as_int(t) - kRoundBits);
+    atomicAdd(lo_base + off, __float_as_int(tl) - kRoundBits);
 }
 
 // 3D Esirkepov deposit into the shared-memory J tile: a loop over the three
@@ -302,7 +311,7 @@ __device__ __forceinline__ void deposit3_smem(const Axis<P> *ax, float S, int *J
                f2 = __any_sync(act, ax[2].shift != 0);
     const int base = (ax[0].wb + G::JHX) + G::JX * ((ax[1].wb + G::JHY) + G::JY * (ax[2].wb + G::JHZ));
     constexpr int s0 = 1, s1 = G::JX, s2 = G::JX * G::JY;
-#pragma unroll 1
+#pragma unroll
     for (int comp = 0; comp < 3; ++comp) {
         float pa[W - 1], Ab[W], Db[W], Ac[W], Dc[W];
 #pragma unroll
@@ -457,7 +466,7 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
     extern __shared__ __align__(16) float smem[];
     __shared__ Run rs;
     __shared__ unsigned slow_cnt;
-    __shared__ float wsum[32];
+    __shared__ float wsum[32], wmaxs[32];
     {
         const int *src = reinterpret_cast<const int *>(runs + it.run);
         int *dst = reinterpret_cast<int *>(&rs);
@@ -510,21 +519,36 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
             for (int c = 0; c < 6; ++c) Fs[c * G::FVOL + l] = v[c];
         }
         for (int q = threadIdx.x; q < 6 * G::JVOL; q += blockDim.x) Jhi[q] = 0;
-        // scale bound: sum of |q w| over the tile's particles
-        float wtot;
+        // scale bounds: sum and maximum of |q w| over the tile's particles
+        float wtot, wmax;
         if (pb.w) {
-            float acc = 0.f;
-            for (long long i = p0 + threadIdx.x; i < p1; i += blockDim.x) acc += fabsf(pb.w[i]);
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
+            float acc = 0.f, mx = 0.f;
+            for (long long i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
+                const float a = fabsf(pb.w[i]);
+                acc += a;
+                mx = fmaxf(mx, a);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            }
+            if ((threadIdx.x & 31) == 0) {
+                wsum[threadIdx.x >> 5] = acc;
+                wmaxs[threadIdx.x >> 5] = mx;
+            }
             __syncthreads();
             wtot = 0.f;
-            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) wtot += wsum[q];
+            wmax = 0.f;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+                wtot += wsum[q];
+                wmax = fmaxf(wmax, wmaxs[q]);
+            }
         } else {
             wtot = fabsf(r.w_const) * (float)(p1 - p0);
+            wmax = fabsf(r.w_const);
         }
-        const float B = 1.01f * fabsf(r.q) * wtot;
-        S = B > 0.f ? 1073741824.f / B : 1.f;
+        const float B = 1.01f * fabsf(r.q) * wtot, M = fabsf(r.q) * wmax;
+        S = B > 0.f ? fminf(1073741824.f / B, kMaxScaled / M) : 1.f;
         __syncthreads();
     }
 
@@ -643,16 +667,22 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
     if (threadIdx.x == 0 && slow_cnt) atomicAdd(&stp->slow, (unsigned long long)slow_cnt);
 }
 
-// One CTA per item (queue == nullptr), or a persistent grid whose CTAs take
-// items from a device work queue (items ordered largest first).
+// One CTA per item.  The persistent schedule is a kernel of its own so that
+// its loop state does not compete with the item body for registers.
 template <int DIM, int P, int TX, int TY, int TZ, int D>
 __global__ void __launch_bounds__(512) push_kernel(const Run *__restrict__ runs, const Item *__restrict__ items,
-                                                   int nitems, int tail_block, int *queue)
+                                                   int tail_block)
 {
-    if (queue == nullptr) {
-        process_item<DIM, P, TX, TY, TZ, D>(runs, items[blockIdx.x], tail_block);
-        return;
-    }
+    process_item<DIM, P, TX, TY, TZ, D>(runs, items[blockIdx.x], tail_block);
+}
+
+// Persistent grid: CTAs take items from the device work queue (items
+// ordered largest first) until it is empty.
+template <int DIM, int P, int TX, int TY, int TZ, int D>
+__global__ void __launch_bounds__(512) push_queue_kernel(const Run *__restrict__ runs,
+                                                         const Item *__restrict__ items, int nitems, int tail_block,
+                                                         int *queue)
+{
     __shared__ int s_item;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
@@ -671,24 +701,27 @@ cudaError_t launch_t(const Run *runs, const Item *items, int nitems, int block, 
 {
     using G = Geo<DIM, P, TX, TY, TZ, D>;
     auto k = push_kernel<DIM, P, TX, TY, TZ, D>;
+    auto kq = push_queue_kernel<DIM, P, TX, TY, TZ, D>;
     static bool attr_set = false;  // raise the opt-in shared-memory limit once
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     if (nitems == 0) return cudaSuccess;
     if (queue) {
         int per_sm = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, G::SMEM);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kq, block, G::SMEM);
         if (e != cudaSuccess) return e;
         int grid = persistent_ctas * (per_sm > 0 ? per_sm : 1);
         grid = grid < nitems ? grid : nitems;
         e = cudaMemsetAsync(queue, 0, sizeof(int), st);
         if (e != cudaSuccess) return e;
-        k<<<grid, block, G::SMEM, st>>>(runs, items, nitems, tail_block, queue);
+        kq<<<grid, block, G::SMEM, st>>>(runs, items, nitems, tail_block, queue);
     } else {
-        k<<<nitems, block, G::SMEM, st>>>(runs, items, nitems, tail_block, nullptr);
+        k<<<nitems, block, G::SMEM, st>>>(runs, items, tail_block);
     }
     return cudaGetLastError();
 }

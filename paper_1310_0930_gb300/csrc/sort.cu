@@ -5,11 +5,13 @@
 // now owns them, dead slots (absorbed particles) are dropped, and the tail
 // of freshly injected plasma is merged.  Steps, per run:
 //   1. zero the tile counters;
-//   2. histogram of tile keys (warp-aggregated atomics: neighbouring
-//      particles mostly share a tile);
+//   2. histogram of tile keys, aggregated per warp (match on the key) and
+//      per CTA (a shared-memory key table over a chunk of kSortChunk slots),
+//      so that the global counters see a few atomics per chunk;
 //   3. exclusive scan of the counts into tile offsets (one CTA per run);
 //   4. scatter every live particle into the alternate buffer at
-//      offset[key] + rank (rank from warp-aggregated cursor atomics);
+//      offset[key] + rank: ranks within the chunk come from the CTA's key
+//      table, and one cursor atomic per (chunk, key) reserves the range;
 //   5. flip the buffer and set the sorted count.
 // Order within a tile is not stable (cursor atomics); nothing downstream
 // depends on it.
@@ -31,19 +33,46 @@ __device__ __forceinline__ int seg_run(const Seg &s, int b)
     return lo;
 }
 
-// tile key of slot i, or -1 for a dead slot / a particle outside the window
-__device__ __forceinline__ int key_of(const Run &r, const RunState &s, const ParticleBuf &pb, long long i)
+// What the tile key of a packed cell depends on, held in registers.
+struct KeyCtx {
+    int b0, b1, m0, m1, t0, t1, t2, nt0, nt1, dim, open_last, origin, nl, lo, hi;
+    long long n_total;
+};
+
+__device__ __forceinline__ KeyCtx key_ctx(const Run &r, const RunState &s)
 {
-    if (i >= s.n_total) return -1;
-    int32_t c = pb.cell[i];
+    KeyCtx k;
+    k.b0 = r.bits[0];
+    k.b1 = r.bits[1];
+    k.m0 = (1 << r.bits[0]) - 1;
+    k.m1 = (1 << r.bits[1]) - 1;
+    k.t0 = r.tlog[0];
+    k.t1 = r.tlog[1];
+    k.t2 = r.tlog[2];
+    k.nt0 = r.nt[0];
+    k.nt1 = r.nt[1];
+    k.dim = r.dim;
+    k.open_last = r.open_last;
+    k.origin = s.origin;
+    k.nl = r.n[r.dim - 1];
+    k.lo = r.margin;
+    k.hi = r.n[r.dim - 1] - r.margin;
+    k.n_total = s.n_total;
+    return k;
+}
+
+// tile key of a packed cell, or -1 for a dead slot / a particle outside the
+// kept part of the window
+__device__ __forceinline__ int key_of_cell(const KeyCtx &k, int32_t c)
+{
     if (c < 0) return -1;
-    int cx, cy, cz;
-    unpack_cell(r, c, cx, cy, cz);
-    if (r.open_last) {
-        int pl = phys_last(r, s, r.dim == 3 ? cz : cy);
-        if (pl < r.margin || pl >= r.n[r.dim - 1] - r.margin) return -1;
+    const int cx = c & k.m0, cy = (c >> k.b0) & k.m1, cz = k.dim == 3 ? (c >> (k.b0 + k.b1)) : 0;
+    if (k.open_last) {
+        int pl = (k.dim == 3 ? cz : cy) - k.origin;
+        pl = pl < 0 ? pl + k.nl : pl;
+        if (pl < k.lo || pl >= k.hi) return -1;
     }
-    return tile_of(r, cx, cy, cz);
+    return (cx >> k.t0) + k.nt0 * ((cy >> k.t1) + k.nt1 * (k.dim == 3 ? (cz >> k.t2) : 0));
 }
 
 __global__ void sort_zero_kernel(const Run *__restrict__ runs, int nruns, int max_tiles)
@@ -55,18 +84,79 @@ __global__ void sort_zero_kernel(const Run *__restrict__ runs, int nruns, int ma
         r.tile_cnt[t] = 0;
 }
 
-__global__ void sort_count_kernel(const Run *__restrict__ runs, Seg seg)
+// Lanes of this warp holding the same key; a warp whose 32 keys agree (the
+// common case: particles are still grouped by tile) skips the match.
+__device__ __forceinline__ unsigned key_peers(int key)
 {
+    const int k0 = __shfl_sync(0xffffffffu, key, 0);
+    if (__all_sync(0xffffffffu, key == k0)) return 0xffffffffu;
+    return __match_any_sync(0xffffffffu, key);
+}
+
+// Per-CTA table of the keys seen in one chunk (open addressing with a
+// bounded probe).  A key that finds no slot returns -1 and its warp falls
+// back to a direct global atomic.
+struct KeyTable {
+    int key[kSortHash];
+    int cnt[kSortHash];
+    int base[kSortHash];
+};
+
+__device__ __forceinline__ void table_init(KeyTable &t)
+{
+    for (int e = threadIdx.x; e < kSortHash; e += blockDim.x) {
+        t.key[e] = -1;
+        t.cnt[e] = 0;
+    }
+}
+
+__device__ __forceinline__ int table_slot(KeyTable &t, int key)
+{
+    unsigned h = ((unsigned)key * 2654435761u) >> (32 - kSortHashLog);
+#pragma unroll 1
+    for (int p = 0; p < kSortProbe; ++p) {
+        const int e = (int)((h + p) & (kSortHash - 1));
+        const int prev = atomicCAS(&t.key[e], -1, key);
+        if (prev == -1 || prev == key) return e;
+    }
+    return -1;
+}
+
+// Tile histogram: each CTA counts a chunk of kSortChunk slots in shared
+// memory (one shared atomic per warp and key), then adds its per-key totals
+// to the global counters: a handful of global atomics per chunk.  All the
+// chunk's cells are loaded before the first use, for memory parallelism.
+__global__ void __launch_bounds__(kSortThreads) sort_count_kernel(const Run *__restrict__ runs, Seg seg)
+{
+    __shared__ KeyTable t;
     const int ri = seg_run(seg, blockIdx.x);
     const Run &r = runs[ri];
-    const RunState &s = *r.state;
-    const long long i = (long long)(blockIdx.x - seg.start[ri]) * blockDim.x + threadIdx.x;
-    const ParticleBuf pb = r.P[s.buf];
-    const int key = key_of(r, s, pb, i);
-    const unsigned act = __activemask();
-    const unsigned peers = __match_any_sync(act, key);
+    const KeyCtx kc = key_ctx(r, *r.state);
+    const long long i0 = (long long)(blockIdx.x - seg.start[ri]) * kSortChunk;
+    if (i0 >= kc.n_total) return;  // CTA-uniform
+    const int32_t *cells = r.P[r.state->buf].cell;
+    int32_t cell[kSortItems];
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const long long i = i0 + j * kSortThreads + threadIdx.x;
+        cell[j] = i < kc.n_total ? cells[i] : -1;
+    }
+    table_init(t);
+    __syncthreads();
     const int lane = threadIdx.x & 31;
-    if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(&r.tile_cnt[key], __popc(peers));
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const int key = key_of_cell(kc, cell[j]);
+        const unsigned peers = key_peers(key);
+        if (key >= 0 && lane == __ffs(peers) - 1) {
+            const int e = table_slot(t, key);
+            if (e >= 0) atomicAdd(&t.cnt[e], __popc(peers));
+            else atomicAdd(&r.tile_cnt[key], __popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kSortHash; e += blockDim.x)
+        if (t.key[e] >= 0 && t.cnt[e] > 0) atomicAdd(&r.tile_cnt[t.key[e]], t.cnt[e]);
 }
 
 // One CTA per run: tile_off = exclusive scan of tile_cnt; tile_cnt becomes
@@ -102,31 +192,90 @@ __global__ void __launch_bounds__(1024) sort_scan_kernel(const Run *__restrict__
     if (threadIdx.x == blockDim.x - 1) r.tile_off[nt] = (int32_t)part[blockDim.x - 1];
 }
 
-__global__ void sort_scatter_kernel(const Run *__restrict__ runs, Seg seg)
+// Scatter: each CTA ranks its chunk's particles per key in shared memory,
+// reserves one contiguous range per key in the destination with one global
+// atomic on the tile cursor, then copies every live particle to
+// range start + rank.  Warps whose keys agree write 32 consecutive slots.
+// Cells, table slots and ranks stay in registers; the copy loads a group of
+// kSortGroup particles per thread before storing them.
+__global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(const Run *__restrict__ runs, Seg seg)
 {
+    __shared__ KeyTable t;
     const int ri = seg_run(seg, blockIdx.x);
     const Run &r = runs[ri];
-    const RunState &s = *r.state;
-    const long long i = (long long)(blockIdx.x - seg.start[ri]) * blockDim.x + threadIdx.x;
-    const ParticleBuf src = r.P[s.buf];
-    const ParticleBuf dst = r.P[s.buf ^ 1];
-    const int key = key_of(r, s, src, i);
-    const unsigned act = __activemask();
-    const unsigned peers = __match_any_sync(act, key);
+    const KeyCtx kc = key_ctx(r, *r.state);
+    const long long i0 = (long long)(blockIdx.x - seg.start[ri]) * kSortChunk;
+    if (i0 >= kc.n_total) return;  // CTA-uniform
+    const int buf = r.state->buf;
+    const ParticleBuf src = r.P[buf];
+    const ParticleBuf dst = r.P[buf ^ 1];
+    int32_t cell[kSortItems];
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const long long i = i0 + j * kSortThreads + threadIdx.x;
+        cell[j] = i < kc.n_total ? src.cell[i] : -1;
+    }
+    table_init(t);
+    __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int leader = __ffs(peers) - 1;
-    int base = 0;
-    if (key >= 0 && lane == leader) base = atomicAdd(&r.tile_cnt[key], __popc(peers));
-    base = __shfl_sync(act, base, leader);
-    if (key < 0) return;
-    const long long o = base + __popc(peers & ((1u << lane) - 1));
-    dst.cell[o] = src.cell[i];
-    for (int a = 0; a < r.dim; ++a) dst.off[a][o] = src.off[a][i];
-    dst.u[0][o] = src.u[0][i];
-    dst.u[1][o] = src.u[1][i];
-    dst.u[2][o] = src.u[2][i];
-    if (src.w) dst.w[o] = src.w[i];
-    if (src.id) dst.id[o] = src.id[i];
+    const unsigned below = (1u << lane) - 1u;
+    int slot[kSortItems], rank[kSortItems];
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const int key = key_of_cell(kc, cell[j]);
+        const unsigned peers = key_peers(key);
+        const int leader = __ffs(peers) - 1;
+        int e = -2, off = 0;
+        if (key >= 0 && lane == leader) {
+            e = table_slot(t, key);
+            off = e >= 0 ? atomicAdd(&t.cnt[e], __popc(peers)) : atomicAdd(&r.tile_cnt[key], __popc(peers));
+        }
+        e = __shfl_sync(0xffffffffu, e, leader);
+        off = __shfl_sync(0xffffffffu, off, leader);
+        slot[j] = key >= 0 ? e : -2;  // -2: dead or outside the window, -1: rank is absolute
+        rank[j] = off + __popc(peers & below);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kSortHash; e += blockDim.x)
+        if (t.key[e] >= 0 && t.cnt[e] > 0) t.base[e] = atomicAdd(&r.tile_cnt[t.key[e]], t.cnt[e]);
+    __syncthreads();
+    const bool d3 = kc.dim == 3;
+#pragma unroll
+    for (int g = 0; g < kSortItems; g += kSortGroup) {
+        float v[kSortGroup][6];
+        float wv[kSortGroup];
+        int32_t idv[kSortGroup];
+#pragma unroll
+        for (int q = 0; q < kSortGroup; ++q) {
+            const int j = g + q;
+            const long long i = i0 + j * kSortThreads + threadIdx.x;
+            if (slot[j] != -2) {
+                v[q][0] = src.off[0][i];
+                v[q][1] = src.off[1][i];
+                v[q][2] = d3 ? src.off[2][i] : 0.f;
+                v[q][3] = src.u[0][i];
+                v[q][4] = src.u[1][i];
+                v[q][5] = src.u[2][i];
+                wv[q] = src.w ? src.w[i] : 0.f;
+                idv[q] = src.id ? src.id[i] : 0;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kSortGroup; ++q) {
+            const int j = g + q;
+            if (slot[j] == -2) continue;
+            const long long o = slot[j] >= 0 ? (long long)t.base[slot[j]] + rank[j] : (long long)rank[j];
+            dst.cell[o] = cell[j];
+            dst.off[0][o] = v[q][0];
+            dst.off[1][o] = v[q][1];
+            if (d3) dst.off[2][o] = v[q][2];
+            dst.u[0][o] = v[q][3];
+            dst.u[1][o] = v[q][4];
+            dst.u[2][o] = v[q][5];
+            if (src.w) dst.w[o] = wv[q];
+            if (src.id) dst.id[o] = idv[q];
+        }
+    }
 }
 
 __global__ void sort_finish_kernel(const Run *__restrict__ runs, int nruns)
@@ -146,9 +295,9 @@ cudaError_t launch_sort(const Run *runs, int nruns, Seg parts, int max_tiles, cu
 {
     dim3 zg((max_tiles + kBlock - 1) / kBlock < 4096 ? (max_tiles + kBlock - 1) / kBlock : 4096, nruns);
     sort_zero_kernel<<<zg, kBlock, 0, st>>>(runs, nruns, max_tiles);
-    sort_count_kernel<<<parts.nblocks, kBlock, 0, st>>>(runs, parts);
+    sort_count_kernel<<<parts.nblocks, kSortThreads, 0, st>>>(runs, parts);
     sort_scan_kernel<<<nruns, 1024, 0, st>>>(runs, nruns);
-    sort_scatter_kernel<<<parts.nblocks, kBlock, 0, st>>>(runs, parts);
+    sort_scatter_kernel<<<parts.nblocks, kSortThreads, 0, st>>>(runs, parts);
     sort_finish_kernel<<<(nruns + 127) / 128, 128, 0, st>>>(runs, nruns);
     return cudaGetLastError();
 }
