@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="lwfa_3d",
-                    choices=["lwfa_3d", "thermal_2d", "bunch_3d", "scan_2d", "adjoint_2d"])
+                    choices=["lwfa_3d", "warm_3d", "thermal_2d", "bunch_3d", "scan_2d", "adjoint_2d"])
+    ap.add_argument("--order", type=int, default=0, help="shape order override (warm_3d)")
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     ap.add_argument("--scan-runs", type=int, default=64)
     ap.add_argument("--autotune", action="store_true", help="choose the tuning with the autotuner first")
@@ -53,7 +54,7 @@ def parse():
     return ap.parse_args()
 
 
-def workload(name, scale):
+def workload(name, scale, order=0):
     from paper_1310_0930_gb300 import inputs
     if name == "lwfa_3d":
         n = (256, 256, 1024)
@@ -62,6 +63,14 @@ def workload(name, scale):
         return inputs.lwfa_3d(n=n)
     if name == "bunch_3d":
         return inputs.bunch_3d()
+    if name == "warm_3d":
+        # uniform warm plasma (u_th = 0.1, the paper's throughput benchmark,
+        # Sec. 4), 256^3 cells at 8 ppc: every particle moves and deposits
+        n = tuple(max(16, int(round(256 * scale / 8)) * 8) for _ in range(3))
+        w = inputs.thermal_3d(n=n, order=order or 2)
+        w.name = "warm_3d"
+        w.uth = 0.1
+        return w
     return inputs.thermal_2d()
 
 
@@ -315,7 +324,7 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    w = workload(args.workload, args.scale)
+    w = workload(args.workload, args.scale, args.order)
     per_step_budget = 60.0 / max(1, args.steps + args.warmup)
     cb = cpu_baseline(w, per_step_budget * (args.steps + args.warmup), steps_hint=args.steps + args.warmup)
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
@@ -353,7 +362,7 @@ def main():
     from paper_1310_0930_gb300.sim import Simulation, TorchMemory
     from paper_1310_0930_gb300 import inputs
 
-    w = workload(args.workload, args.scale)
+    w = workload(args.workload, args.scale, args.order)
     tuning = json.loads(args.tuning) if args.tuning else None
     chunks = particle_chunks(w)
     n0 = sum(c.n for c in chunks)

@@ -596,13 +596,22 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
                     float d1[3] = {0.f, 0.f, 0.f}, ig;
                     ok = push_move<DIM, P>(r, sgather, rel, d, u, d1, k, ig);
                     if (ok) {
-                        const float qw = r.q * cur.w;
-                        Axis<P> ax[DIM];
+                        // A particle that did not move (and, in 2D, has v_z = 0)
+                        // deposits exactly zero; a warp of such particles skips
+                        // the deposit.
+                        bool moves = DIM == 2 && u[2] != 0.f;
 #pragma unroll
-                        for (int a = 0; a < DIM; ++a)
-                            axis_window<P>(rel[a], d[a], k[a], d1[a], -qw * r.d_over_dt[a], ax[a]);
-                        if (DIM == 3) deposit3_smem<P, G>(reinterpret_cast<const Axis<P> *>(ax), S, Jhi, Jlo);
-                        else deposit2_smem<P, G>(reinterpret_cast<const Axis<P> *>(ax), S, qw * u[2] * ig, Jhi, Jlo);
+                        for (int a = 0; a < DIM; ++a) moves = moves || k[a] != 0 || d1[a] != d[a];
+                        if (__any_sync(__activemask(), moves)) {
+                            const float qw = r.q * cur.w;
+                            Axis<P> ax[DIM];
+#pragma unroll
+                            for (int a = 0; a < DIM; ++a)
+                                axis_window<P>(rel[a], d[a], k[a], d1[a], -qw * r.d_over_dt[a], ax[a]);
+                            if (DIM == 3) deposit3_smem<P, G>(reinterpret_cast<const Axis<P> *>(ax), S, Jhi, Jlo);
+                            else
+                                deposit2_smem<P, G>(reinterpret_cast<const Axis<P> *>(ax), S, qw * u[2] * ig, Jhi, Jlo);
+                        }
 #pragma unroll
                         for (int a = 0; a < DIM; ++a) d[a] = d1[a];
                     }
