@@ -150,9 +150,13 @@ typedef void (*pic_free_fn)(void *ptr, void *ctx);
  * otherwise), 1 = one persistent grid whose CTAs take tiles from a device
  * work queue, largest runs first, 2 = one CTA per tile.
  * Compiled (tile, drift) pairs: 2D 16x16 with drift 1, 2 (default) or 3,
- * 8x8 with 1, 32x32 with 2; 3D 8x8x8 with 1 (default) or 2; any other pair
+ * 8x8 with 1, 32x32 with 2; 3D 8x8x8 with 1 (default) or 2, 8x8x4 with 1; any other pair
  * is PIC_EINVAL.
- * use_graph: capture each step kind in a CUDA graph and replay it. */
+ * use_graph: capture each step kind in a CUDA graph and replay it.
+ * sort_sub: sub-buckets per tile in the sort, 0 = default (1 = none),
+ * else a power of two <= 32: slot i of a tile's particles goes to sub-bucket
+ * i mod sort_sub, so that the particles one warp pushes together come from
+ * different cells (fewer shared-memory bank conflicts in the deposit). */
 typedef struct {
     int32_t tile[3];
     int32_t sort_interval;
@@ -160,6 +164,7 @@ typedef struct {
     int32_t block;
     int32_t use_graph;
     int32_t persistent;
+    int32_t sort_sub;
 } pic_tuning;
 
 typedef struct {
@@ -279,8 +284,9 @@ typedef struct {
 /* Arm the reverse mode for a forward run of total_steps steps: allocates the
  * adjoint arrays, ceil(total/checkpoint_every) checkpoints (particle state and
  * E, B) and one segment of per-step records; the following pic_step calls
- * save a checkpoint every checkpoint_every steps (steps then run without
- * graph replay). */
+ * save a checkpoint every checkpoint_every steps (copied between step graph
+ * replays; the recomputation inside pic_adjoint_backward runs without graphs
+ * because it records each step). */
 PIC_API int pic_adjoint_begin(pic_t *h, int32_t total_steps, int32_t checkpoint_every);
 
 /* L of the current state (no adjoint). */

@@ -392,19 +392,45 @@ struct SmemRead {
     }
 };
 
+// Inputs of one recorded particle's adjoint: its recorded state and the
+// adjoints of its state after the step (slot order).
+struct AdjIn {
+    int32_t cell;
+    float d[3], u[3], w;
+    float lx[3], lu[3];
+    double lw;  // accumulated weight adjoint of the slot
+};
+
+template <int DIM>
+__device__ __forceinline__ void adj_load(const TrajStep &ts, const AdjPtrs &A, long long s, AdjIn &in)
+{
+    in.cell = ts.cell[s];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        in.d[a] = a < DIM ? ts.off[a][s] : 0.f;
+        in.lx[a] = a < DIM ? A.sx[a][s] : 0.f;
+        in.u[a] = ts.u[a][s];
+        in.lu[a] = A.su[a][s];
+    }
+    in.w = ts.w[s];
+    in.lw = A.sw[s];
+}
+
 // One recorded particle's adjoint.  c: cell in the reader's frame; org:
 // offset from that frame to absolute cells (scatter and absorption use
 // absolute cells); rd(comp 0..5, ...) reads the recorded fields,
 // rd(6 + comp, ...) the current adjoint.
 template <int DIM, int P, class RD>
 __device__ __forceinline__ void adj_one(const Run &r, const AdjPtrs &A, const TrajStep &ts, long long s,
-                                        int origin, const int *c, const int *org, const RD &rd)
+                                        const AdjIn &in, int origin, const int *c, const int *org, const RD &rd)
 {
     const int nl = r.n[DIM - 1];
     float d[3] = {0.f, 0.f, 0.f}, u[3];
-    for (int a = 0; a < DIM; ++a) d[a] = ts.off[a][s];
-    for (int a = 0; a < 3; ++a) u[a] = ts.u[a][s];
-    const float w = ts.w[s];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) d[a] = in.d[a];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u[a] = in.u[a];
+    const float w = in.w;
     const GF gf{{ts.E[0], ts.E[1], ts.E[2], ts.B[0], ts.B[1], ts.B[2]}, r.n[0], r.n[1], DIM == 3 ? r.n[2] : 1};
     const int ox = org[0], oy = org[1], oz = org[2];
     // --- forward recompute: shapes and gather with position derivatives ---
@@ -479,13 +505,16 @@ __device__ __forceinline__ void adj_one(const Run &r, const AdjPtrs &A, const Tr
     // --- adjoint inputs: state adjoints of x^{n+1}, u^{n+1/2} ---
     float lxn[3] = {0.f, 0.f, 0.f}, lun[3] = {0.f, 0.f, 0.f};
     if (!absorbed) {
-        for (int a = 0; a < DIM; ++a) lxn[a] = A.sx[a][s];
-        for (int a = 0; a < 3; ++a) lun[a] = A.su[a][s];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) lxn[a] = in.lx[a];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) lun[a] = in.lu[a];
     }
     // --- deposit transpose (Esirkepov window, per unit weight) ---
     constexpr int W = P + 2;
     float S0[DIM][W], S1[DIM][W], dS0[DIM][W], dS1[DIM][W];
     int wb[3] = {0, 0, 0};
+    bool moved[3] = {false, false, false};  // nearest node changed along the axis
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
 #pragma unroll
@@ -497,6 +526,7 @@ __device__ __forceinline__ void adj_one(const Run &r, const AdjPtrs &A, const Tr
         ShapeD<P>::node(c[a], d[a], bo, so, dso);
         ShapeD<P>::node(c[a] + k[a], d1[a], bnw, sn, dsn);
         const int sh = bnw - bo;
+        moved[a] = sh != 0;
         wb[a] = sh < 0 ? bnw : bo;
         const int oo = sh < 0 ? 1 : 0, on = sh > 0 ? 1 : 0;
 #pragma unroll
@@ -529,7 +559,16 @@ __device__ __forceinline__ void adj_one(const Run &r, const AdjPtrs &A, const Tr
             run_ += DS[a][q];
             Pr[a][q] = run_;
         }
+        // as in the forward deposit: without a node change the last prefix
+        // is exactly zero (and carries no derivative)
+        if (!moved[a]) Pr[a][W - 2] = 0.f;
     }
+    // the forward skips the last window node of an axis along which no lane
+    // of the warp changed node (all its terms are zero); so does the adjoint
+    const unsigned act = __activemask();
+    bool fa[3] = {true, true, true};
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) fa[a] = __any_sync(act, moved[a]);
     const float q_ = r.q;
     const float vz = un[2] * ig;
     float gA[DIM][W], gD[DIM][W];
@@ -548,14 +587,15 @@ __device__ __forceinline__ void adj_one(const Run &r, const AdjPtrs &A, const Tr
         for (int qb = 0; qb < W; ++qb)
 #pragma unroll
             for (int qa = 0; qa < W; ++qa) {
+                if ((qb == W - 1 && !fa[1]) || (qa == W - 1 && !fa[0])) continue;
                 const int i = wb[0] + qa, j = wb[1] + qb;
-                if (qa < W - 1) {  // J_x = cx P_x A_y
+                if (qa < W - 1 && !(qa == W - 2 && !fa[0])) {  // J_x = cx P_x A_y
                     const float L = lam(0, i, j, 0);
                     lw += L * cx * Pr[0][qa] * As[1][qb];
                     Rx[qa] += L * As[1][qb];
                     gA[1][qb] += w * cx * L * Pr[0][qa];
                 }
-                if (qb < W - 1) {  // J_y = cy P_y A_x
+                if (qb < W - 1 && !(qb == W - 2 && !fa[1])) {  // J_y = cy P_y A_x
                     const float L = lam(1, i, j, 0);
                     lw += L * cy * Pr[1][qb] * As[0][qa];
                     Ry[qb] += L * As[0][qa];
@@ -573,6 +613,9 @@ __device__ __forceinline__ void adj_one(const Run &r, const AdjPtrs &A, const Tr
                 }
             }
         // prefix transposes: d/dDS[a'] of sum_a R[a] P[a] = sum_{a>=a'} R[a]
+        // (a prefix forced to zero passes no derivative)
+        if (!moved[0]) Rx[W - 2] = 0.f;
+        if (!moved[1]) Ry[W - 2] = 0.f;
         float sx = 0.f, sy = 0.f;
 #pragma unroll
         for (int q = W - 2; q >= 0; --q) {
@@ -590,8 +633,10 @@ __device__ __forceinline__ void adj_one(const Run &r, const AdjPtrs &A, const Tr
             for (int q = 0; q < W; ++q) R[q] = 0.f;
             for (int qc = 0; qc < W; ++qc)
                 for (int qb = 0; qb < W; ++qb) {
+                    if ((qc == W - 1 && !fa[cc]) || (qb == W - 1 && !fa[b])) continue;
                     const float fac = As[b][qb] * As[cc][qc] + DS[b][qb] * DS[cc][qc] * (1.f / 12.f);
                     for (int qa = 0; qa < W - 1; ++qa) {
+                        if (qa == W - 2 && !fa[a]) continue;
                         int q3[3];
                         q3[a] = qa;
                         q3[b] = qb;
@@ -606,6 +651,7 @@ __device__ __forceinline__ void adj_one(const Run &r, const AdjPtrs &A, const Tr
                         gD[cc][qc] += lp * DS[b][qb] * (1.f / 12.f);
                     }
                 }
+            if (!moved[a]) R[W - 2] = 0.f;
             float sacc = 0.f;
             for (int q = W - 2; q >= 0; --q) {
                 sacc += R[q];
@@ -669,7 +715,7 @@ __device__ __forceinline__ void adj_one(const Run &r, const AdjPtrs &A, const Tr
     }
     for (int a = 0; a < DIM; ++a) A.sx[a][s] = lxo[a];
     for (int a = 0; a < 3; ++a) A.su[a][s] = lu0[a];
-    A.sw[s] += (double)lw;
+    A.sw[s] = in.lw + (double)lw;
 }
 
 template <int DIM>
@@ -696,22 +742,25 @@ __global__ void __launch_bounds__(128, 3) adj_particles_kernel(const Run *__rest
     if (s >= ts.n) return;
     int c[3] = {0, 0, 0};
     if (!adj_live<DIM>(r, ts.cell[s], origin, c)) return;
+    AdjIn in;
+    adj_load<DIM>(ts, A, s, in);
     const GlobalRead g{{ts.E[0], ts.E[1], ts.E[2], ts.B[0], ts.B[1], ts.B[2], A.lJ[0], A.lJ[1], A.lJ[2]},
                        r.n[0], r.n[1], DIM == 3 ? r.n[2] : 1};
     const int org[3] = {0, 0, 0};
-    adj_one<DIM, P>(r, A, ts, s, origin, c, org, g);
+    adj_one<DIM, P>(r, A, ts, s, in, origin, c, org, g);
 }
 
-// Tiled form: one CTA per tile of the sort recorded with the step; the
-// tile's recorded fields and current adjoint (plus halos wide enough for
-// particles within `drift` cells of the tile) are staged in shared memory.
+// Tiled form: nsplit CTAs per tile of the sort recorded with the step (each
+// takes every nsplit-th group of blockDim particles); the tile's recorded
+// fields and current adjoint (plus halos wide enough for particles within
+// `drift` cells of the tile) are staged in shared memory.
 template <int DIM, int P>
 __global__ void __launch_bounds__(128, 3) adj_particles_tiled_kernel(const Run *__restrict__ run, AdjPtrs A,
-                                                                     TrajStep ts, int origin)
+                                                                     TrajStep ts, int origin, int nsplit)
 {
     extern __shared__ float sm[];
     const Run &r = *run;
-    const int t = blockIdx.x;
+    const int t = blockIdx.x / nsplit, part = blockIdx.x - t * nsplit;
     const long long p0 = ts.tile_off[t], p1 = ts.tile_off[t + 1];
     if (p0 >= p1) return;
     const int D = r.drift;
@@ -739,32 +788,53 @@ __global__ void __launch_bounds__(128, 3) adj_particles_tiled_kernel(const Run *
             F[(3 + c) * fvol + l] = __ldg(ts.B[c] + g);
         }
     }
+    int lj_any = 0;  // some current adjoint in reach of the tile is nonzero
     for (int l = threadIdx.x; l < jvol; l += blockDim.x) {
         const int lx = l % js[0], ly = (l / js[0]) % js[1], lz = l / (js[0] * js[1]);
         const int g = modi(org[0] - jh[0] + lx, n0) +
                       n0 * (modi(org[1] - jh[1] + ly, n1) + n1 * (DIM == 3 ? modi(org[2] - jh[2] + lz, n2) : 0));
-        for (int c = 0; c < 3; ++c) L[c * jvol + l] = __ldg(A.lJ[c] + g);
+        for (int c = 0; c < 3; ++c) {
+            const float v = __ldg(A.lJ[c] + g);
+            L[c * jvol + l] = v;
+            lj_any |= v != 0.f;
+        }
     }
-    __syncthreads();
+    lj_any = __syncthreads_or(lj_any);
     const SmemRead sr{F, L, fvol, fh[0], fh[1], fh[2], fs[0], fs[0] * fs[1],
                       jvol, jh[0], jh[1], jh[2], js[0], js[0] * js[1]};
     const GlobalRead g{{ts.E[0], ts.E[1], ts.E[2], ts.B[0], ts.B[1], ts.B[2], A.lJ[0], A.lJ[1], A.lJ[2]},
                        n0, n1, n2};
     const int zero[3] = {0, 0, 0};
-    for (long long s = p0 + threadIdx.x; s < p1; s += blockDim.x) {
+    // the next particle's inputs are loaded before the current one is done
+    AdjIn cur, nxt;
+    const long long stride = (long long)blockDim.x * nsplit;
+    long long s = p0 + (long long)part * blockDim.x + threadIdx.x;
+    if (s < p1) adj_load<DIM>(ts, A, s, cur);
+    for (; s < p1; s += stride) {
+        if (s + stride < p1) adj_load<DIM>(ts, A, s + stride, nxt);
         int c[3] = {0, 0, 0};
-        if (!adj_live<DIM>(r, ts.cell[s], origin, c)) continue;
-        int rel[3] = {0, 0, 0};
-        bool fast = true;
-        for (int a = 0; a < DIM; ++a) {
-            int v = c[a] - org[a];
-            if (v < -D) v += r.n[a];
-            else if (v >= T[a] + D) v -= r.n[a];
-            rel[a] = v;
-            fast = fast && v >= -D && v < T[a] + D;
+        bool skip = !adj_live<DIM>(r, cur.cell, origin, c);
+        if (!skip && !lj_any) {
+            // zero state adjoints and a zero current adjoint give zero outputs
+            bool zero = cur.lu[0] == 0.f && cur.lu[1] == 0.f && cur.lu[2] == 0.f;
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) zero = zero && cur.lx[a] == 0.f;
+            skip = zero;
         }
-        if (fast) adj_one<DIM, P>(r, A, ts, s, origin, rel, org, sr);
-        else adj_one<DIM, P>(r, A, ts, s, origin, c, zero, g);
+        if (!skip) {
+            int rel[3] = {0, 0, 0};
+            bool fast = true;
+            for (int a = 0; a < DIM; ++a) {
+                int v = c[a] - org[a];
+                if (v < -D) v += r.n[a];
+                else if (v >= T[a] + D) v -= r.n[a];
+                rel[a] = v;
+                fast = fast && v >= -D && v < T[a] + D;
+            }
+            if (fast) adj_one<DIM, P>(r, A, ts, s, cur, origin, rel, org, sr);
+            else adj_one<DIM, P>(r, A, ts, s, cur, origin, c, zero, g);
+        }
+        cur = nxt;
     }
 }
 
@@ -907,25 +977,82 @@ __global__ void adj_init_kernel(const Run *__restrict__ run, float *wid, float *
 
 // Copy the live buffer's first n slots to / from a side buffer (the
 // current buffer index is read from the device state).
-__global__ void part_copy_kernel(const Run *__restrict__ run, PartCopy pc, long long n, int restore)
+// Copy of the particle state to (restore = 0) or from (restore = 1) a
+// record; each thread moves 4 consecutive slots with 16-byte accesses (the
+// buffers are 256-byte aligned), the last n % 4 slots one by one.
+template <int DIM>
+__device__ __forceinline__ void copy4(int32_t *dc, float *const *doff, float *const *du, float *dw, int32_t *did,
+                                      const int32_t *sc, const float *const *soff, const float *const *su,
+                                      const float *sw, const int32_t *sid, long long i, long long n,
+                                      long long n_live, bool fill_dead, bool vec)
+{
+    if (vec && i + 3 < n) {
+        int4 c = *reinterpret_cast<const int4 *>(sc + i);
+        if (fill_dead) {
+            c.x = i < n_live ? c.x : -1;
+            c.y = i + 1 < n_live ? c.y : -1;
+            c.z = i + 2 < n_live ? c.z : -1;
+            c.w = i + 3 < n_live ? c.w : -1;
+        }
+        *reinterpret_cast<int4 *>(dc + i) = c;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a)
+            *reinterpret_cast<float4 *>(doff[a] + i) = *reinterpret_cast<const float4 *>(soff[a] + i);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            *reinterpret_cast<float4 *>(du[a] + i) = *reinterpret_cast<const float4 *>(su[a] + i);
+        if (dw && sw) *reinterpret_cast<float4 *>(dw + i) = *reinterpret_cast<const float4 *>(sw + i);
+        if (did) {
+            if (sid) *reinterpret_cast<int4 *>(did + i) = *reinterpret_cast<const int4 *>(sid + i);
+            else *reinterpret_cast<int4 *>(did + i) = make_int4(-1, -1, -1, -1);
+        }
+        return;
+    }
+    for (long long j = i; j < n; ++j) {
+        dc[j] = (!fill_dead || j < n_live) ? sc[j] : -1;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) doff[a][j] = soff[a][j];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) du[a][j] = su[a][j];
+        if (dw && sw) dw[j] = sw[j];
+        if (did) did[j] = sid ? sid[j] : -1;
+    }
+}
+
+template <int DIM>
+__global__ void part_copy_kernel(const Run *__restrict__ run, PartCopy pc, long long n, int restore, FieldCopy fc)
 {
     const Run &r = *run;
     const RunState &s = *r.state;
     const ParticleBuf pb = r.P[s.buf];
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        if (!restore) {
-            pc.cell[i] = i < s.n_total ? pb.cell[i] : -1;
-            for (int a = 0; a < r.dim; ++a) pc.off[a][i] = pb.off[a][i];
-            for (int a = 0; a < 3; ++a) pc.u[a][i] = pb.u[a][i];
-            if (pc.w && pb.w) pc.w[i] = pb.w[i];
-            if (pc.id) pc.id[i] = pb.id ? pb.id[i] : -1;
+    const long long nq = (n + 3) / 4;
+    // 16-byte accesses only if every buffer allows them
+    uintptr_t al = (uintptr_t)pb.cell | (uintptr_t)pc.cell | (uintptr_t)pb.w | (uintptr_t)pc.w | (uintptr_t)pb.id |
+                   (uintptr_t)pc.id;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) al |= (uintptr_t)pb.u[a] | (uintptr_t)pc.u[a];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) al |= (uintptr_t)pb.off[a] | (uintptr_t)pc.off[a];
+    const bool vec = (al & 15u) == 0;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nq;
+         q += (long long)gridDim.x * blockDim.x) {
+        if (!restore)
+            copy4<DIM>(pc.cell, pc.off, pc.u, pc.w, pc.id, pb.cell, pb.off, pb.u, pb.w, pb.id, 4 * q, n, s.n_total,
+                       true, vec);
+        else
+            copy4<DIM>(pb.cell, pb.off, pb.u, pb.w, pc.id ? pb.id : nullptr, pc.cell, pc.off, pc.u, pc.w, pc.id,
+                       4 * q, n, 0, false, vec);
+    }
+    // fields and tile offsets of a record
+    const long long nf = (long long)fc.nf * fc.cells;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < nf + fc.nt;
+         j += (long long)gridDim.x * blockDim.x) {
+        if (j < nf) {
+            const int c = (int)(j / fc.cells);
+            const long long i = j - c * fc.cells;
+            fc.dst[c][i] = fc.src[c][i];
         } else {
-            pb.cell[i] = pc.cell[i];
-            for (int a = 0; a < r.dim; ++a) pb.off[a][i] = pc.off[a][i];
-            for (int a = 0; a < 3; ++a) pb.u[a][i] = pc.u[a][i];
-            if (pc.w && pb.w) pb.w[i] = pc.w[i];
-            if (pc.id && pb.id) pb.id[i] = pc.id[i];
+            fc.toff_dst[j - nf] = fc.toff_src[j - nf];
         }
     }
 }
@@ -987,7 +1114,16 @@ cudaError_t launch_adj_t(const Run *run, const Run &hr, const AdjPtrs &A, const 
         if (e != cudaSuccess) return e;
         attr = smem;
     }
-    k<<<hr.ntiles, kAdjBlock, smem, st>>>(run, A, ts, origin);
+    // enough CTAs for about four waves of three CTAs per SM
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 1;
+    }
+    int nsplit = (int)((4ll * 3 * sms + hr.ntiles - 1) / hr.ntiles);
+    nsplit = nsplit < 1 ? 1 : (nsplit > 8 ? 8 : nsplit);
+    k<<<(unsigned)((long long)hr.ntiles * nsplit), kAdjBlock, smem, st>>>(run, A, ts, origin, nsplit);
     return cudaGetLastError();
 }
 
@@ -1031,9 +1167,22 @@ cudaError_t launch_knots(const double *lw, const float *zb, long long n, int n_k
     return cudaGetLastError();
 }
 
-cudaError_t launch_part_copy(const Run *run, const PartCopy &pc, long long n, int restore, cudaStream_t st)
+cudaError_t launch_part_copy(int dim, const Run *run, const PartCopy &pc, long long n, int restore, cudaStream_t st)
 {
-    part_copy_kernel<<<blocks_for(n), kBlock, 0, st>>>(run, pc, n, restore);
+    const long long nq = (n + 3) / 4;
+    const FieldCopy none{};
+    if (dim == 2) part_copy_kernel<2><<<blocks_for(nq), kBlock, 0, st>>>(run, pc, n, restore, none);
+    else part_copy_kernel<3><<<blocks_for(nq), kBlock, 0, st>>>(run, pc, n, restore, none);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_record(int dim, const Run *run, const PartCopy &pc, long long n, const FieldCopy &fc,
+                          cudaStream_t st)
+{
+    const long long nq = (n + 3) / 4;
+    const long long work = nq > fc.nf * fc.cells + fc.nt ? nq : fc.nf * fc.cells + fc.nt;
+    if (dim == 2) part_copy_kernel<2><<<blocks_for(work), kBlock, 0, st>>>(run, pc, n, 0, fc);
+    else part_copy_kernel<3><<<blocks_for(work), kBlock, 0, st>>>(run, pc, n, 0, fc);
     return cudaGetLastError();
 }
 

@@ -69,7 +69,8 @@ struct Run {
     float *mur;        // saved tangential E planes for Mur: [2][4][plane]
     ParticleBuf P[2];
     int32_t *tile_off; // [ntiles + 1] particle offsets per tile
-    int32_t *tile_cnt; // [ntiles] scratch counters for the sort
+    int32_t *tile_cnt; // [ntiles * nsub] sort counters / cursors per (tile, sub-bucket)
+    int nsub;          // sort sub-buckets per tile (power of two): slot i goes to sub-bucket i % nsub
     long long capacity;
     // laser antenna
     int laser_on, laser_pol, laser_plane;

@@ -26,6 +26,9 @@ constexpr int kBlock = 256;
 // entries; the particle segments of the sort are in units of chunks.
 constexpr int kSortThreads = 256, kSortItems = 8, kSortGroup = 4, kSortChunk = kSortThreads * kSortItems;
 constexpr int kSortHashLog = 9, kSortHash = 1 << kSortHashLog, kSortProbe = 32;
+// The exclusive scan of the (tile, sub-bucket) counters runs in blocks of
+// kScanChunk keys (kScanThreads threads x kScanItems consecutive keys).
+constexpr int kScanThreads = 256, kScanItems = 16, kScanChunk = kScanThreads * kScanItems;
 
 // Particle kernel (push.cuh) over the compiled tile menu (push_menu.h).
 // push_smem_bytes returns 0 for a (tile, drift) pair that is not compiled.
@@ -46,7 +49,9 @@ cudaError_t launch_end_step(const Run *runs, int nruns, cudaStream_t st);
 cudaError_t launch_window(const Run *runs, Seg planes, Seg inject, cudaStream_t st);
 
 // sort.cu
-cudaError_t launch_sort(const Run *runs, int nruns, Seg parts, int max_tiles, cudaStream_t st);
+// keys: segments of kScanChunk (tile, sub-bucket) keys; scan_sums: one int
+// per key block.
+cudaError_t launch_sort(const Run *runs, int nruns, Seg parts, Seg keys, int *scan_sums, cudaStream_t st);
 
 // diag.cu
 cudaError_t launch_pack(const Run *run, long long base, long long n, int dim, const int32_t *cell,
@@ -104,7 +109,20 @@ struct PartCopy {
     float *w;    // may be null
     int32_t *id; // may be null
 };
-cudaError_t launch_part_copy(const Run *run, const PartCopy &pc, long long n, int restore, cudaStream_t st);
+cudaError_t launch_part_copy(int dim, const Run *run, const PartCopy &pc, long long n, int restore, cudaStream_t st);
+// Extra arrays copied by the same launch as a particle record (may be empty):
+// nf field arrays of `cells` floats and `nt` ints of tile offsets.
+struct FieldCopy {
+    const float *src[6];
+    float *dst[6];
+    int nf;
+    long long cells;
+    const int32_t *toff_src;
+    int32_t *toff_dst;
+    long long nt;
+};
+cudaError_t launch_record(int dim, const Run *run, const PartCopy &pc, long long n, const FieldCopy &fc,
+                          cudaStream_t st);
 // move the particle adjoints between id order and the slot order of a record
 cudaError_t launch_adj_perm(int dim, const AdjPtrs &A, const int32_t *id, long long n, int to_slots, cudaStream_t st);
 

@@ -71,8 +71,10 @@ struct pic_s {
     RunState *d_states = nullptr;
     Item *d_items = nullptr;
     int n_items = 0;
-    int *d_seg = nullptr;  // 4 segment tables of nruns+1 ints
-    Seg seg_cells{}, seg_planes{}, seg_parts{}, seg_inject{};
+    int *d_seg = nullptr;  // 5 segment tables of nruns+1 ints
+    int *d_scan = nullptr; // per-block sums of the sort's key scan
+    Seg seg_cells{}, seg_planes{}, seg_parts{}, seg_inject{}, seg_keys{};
+    int sort_sub = 1;
     size_t push_smem = 0;
     int block = 256, sort_interval = 4, drift = 1, tile[3] = {16, 16, 1};
     bool use_graph = true;
@@ -322,22 +324,27 @@ int enqueue_step(pic_s *h, bool sort)
         if (ev && e == cudaSuccess) e = cudaEventRecord(ev[ph], st);
     };
     mark(PIC_PH_SORT);
-    if (sort) e = launch_sort(R, h->nruns, h->seg_parts, h->max_tiles, st);
+    if (sort) e = launch_sort(R, h->nruns, h->seg_parts, h->seg_keys, h->d_scan, st);
     if (e == cudaSuccess && h->adj && h->adj->rec_on) {
         // the push of this step reads these particles and fields
         Rec &rc = h->adj->rec[h->steps_done - h->adj->rec_base];
         const Run &r0 = h->runs[0].r;
         rc.time = h->time_host;
         rc.sorted = sort;
-        e = launch_part_copy(R, rc.pc, h->adj->nid, 0, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(rc.tile_off, r0.tile_off, sizeof(int32_t) * (r0.ntiles + 1), cudaMemcpyDeviceToDevice,
-                                st);
-        for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
-            e = cudaMemcpyAsync(rc.E[c], r0.E[c], sizeof(float) * r0.ncell, cudaMemcpyDeviceToDevice, st);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(rc.B[c], r0.B[c], sizeof(float) * r0.ncell, cudaMemcpyDeviceToDevice, st);
+        // one launch records particles, fields and tile offsets
+        FieldCopy fc{};
+        for (int c = 0; c < 3; ++c) {
+            fc.src[c] = r0.E[c];
+            fc.dst[c] = rc.E[c];
+            fc.src[3 + c] = r0.B[c];
+            fc.dst[3 + c] = rc.B[c];
         }
+        fc.nf = 6;
+        fc.cells = r0.ncell;
+        fc.toff_src = r0.tile_off;
+        fc.toff_dst = rc.tile_off;
+        fc.nt = r0.ntiles + 1;
+        e = launch_record(h->dim, R, rc.pc, h->adj->nid, fc, st);
     }
     mark(PIC_PH_ZERO_J);
     if (e == cudaSuccess) e = launch_zero_j(R, h->seg_cells, st);
@@ -359,7 +366,7 @@ int enqueue_step(pic_s *h, bool sort)
     mark(PIC_NUM_PHASES);
     if (ev) {
         h->prof_steps += 1;
-        h->prof_launches += (sort ? 5 : 0) + 6 + (h->any_open ? 2 : 0) + (h->any_window ? 3 : 0);
+        h->prof_launches += (sort ? 6 : 0) + 6 + (h->any_open ? 2 : 0) + (h->any_window ? 3 : 0);
     }
     return cuda_fail(e);
 }
@@ -379,6 +386,15 @@ int first_step_setup(pic_s *h)
     }
     int rc = upload_runs(h);
     if (!rc) rc = set_seg(h, 2, h->seg_parts, parts, kSortChunk);
+    if (!rc) {
+        std::vector<long long> keys(h->nruns);
+        for (int i = 0; i < h->nruns; ++i) keys[i] = (long long)h->runs[i].r.ntiles * h->runs[i].r.nsub;
+        rc = set_seg(h, 4, h->seg_keys, keys, kScanChunk);
+    }
+    if (!rc && !h->d_scan) {
+        h->d_scan = (int *)dev_alloc(h, sizeof(int) * (h->seg_keys.nblocks + 1));
+        if (!h->d_scan) rc = PIC_ENOMEM;
+    }
     if (!rc) rc = set_seg(h, 3, h->seg_inject, inj);
     if (!rc) rc = build_items(h);
     if (rc) return rc;
@@ -444,7 +460,9 @@ int init_run(pic_s *h, HostRun &hr, int idx)
     hr.rho32 = (float *)dev_alloc(h, sizeof(float) * ncell);
     r.mur = (float *)dev_alloc(h, sizeof(float) * 8 * plane);
     r.tile_off = (int32_t *)dev_alloc(h, sizeof(int32_t) * (r.ntiles + 1));
-    r.tile_cnt = (int32_t *)dev_alloc(h, sizeof(int32_t) * (r.ntiles + 1));
+    r.nsub = h->sort_sub;
+    if ((long long)r.ntiles * r.nsub > (1ll << 30)) return PIC_EINVAL;
+    r.tile_cnt = (int32_t *)dev_alloc(h, sizeof(int32_t) * ((size_t)r.ntiles * r.nsub + 1));
     if (!r.rho0 || !hr.rho || !hr.rho32 || !r.mur || !r.tile_off || !r.tile_cnt) return PIC_ENOMEM;
     cudaError_t e = cudaSuccess;
     for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
@@ -519,6 +537,11 @@ int create_common(const pic_config *cfgs, int n, pic_t **out)
     h->sort_interval = t.sort_interval ? t.sort_interval : 4;
     h->use_graph = t.use_graph != 0 && h->stream != nullptr;
     h->persistent = t.persistent == 1 || (t.persistent == 0 && n > 1);
+    h->sort_sub = t.sort_sub ? t.sort_sub : 1;
+    if (h->sort_sub < 1 || h->sort_sub > 32 || (h->sort_sub & (h->sort_sub - 1))) {
+        delete h;
+        return PIC_EINVAL;
+    }
     h->push_smem = push_smem_bytes(h->dim, h->order, h->tile, h->drift);
     if (h->push_smem == 0) {  // (tile, drift) not among the compiled configurations
         delete h;
@@ -538,7 +561,7 @@ int create_common(const pic_config *cfgs, int n, pic_t **out)
     h->runs.resize(n);
     h->d_runs = (Run *)dev_alloc(h, sizeof(Run) * n);
     h->d_states = (RunState *)dev_alloc(h, sizeof(RunState) * n);
-    h->d_seg = (int *)dev_alloc(h, sizeof(int) * 4 * (n + 1));
+    h->d_seg = (int *)dev_alloc(h, sizeof(int) * 5 * (n + 1));
     h->d_diag = (double *)dev_alloc(h, sizeof(double) * 16);
     h->d_count = (unsigned long long *)dev_alloc(h, sizeof(unsigned long long));
     h->d_queue = (int *)dev_alloc(h, sizeof(int));
@@ -658,7 +681,7 @@ int pic_step(pic_t *h, int32_t nsteps)
             h->steps_done / h->adj->K < h->adj->nck) {
             Ckpt &ck = h->adj->ck[h->steps_done / h->adj->K];
             const Run &r0 = h->runs[0].r;
-            cudaError_t e = launch_part_copy(h->d_runs, ck.pc, h->adj->nid, 0, h->stream);
+            cudaError_t e = launch_part_copy(h->dim, h->d_runs, ck.pc, h->adj->nid, 0, h->stream);
             for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
                 e = cudaMemcpyAsync(ck.E[c], r0.E[c], sizeof(float) * r0.ncell, cudaMemcpyDeviceToDevice, h->stream);
                 if (e == cudaSuccess)
@@ -672,7 +695,7 @@ int pic_step(pic_t *h, int32_t nsteps)
         }
         bool sort = h->need_sort || h->since_sort >= h->sort_interval;
         int kind = sort ? 1 : 0;
-        if (h->use_graph && !h->prof_on) {
+        if (h->use_graph && !h->prof_on && !(h->adj && h->adj->rec_on)) {
             if (!h->graph[kind]) {
                 cudaGraph_t g = nullptr;
                 if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PIC_ECUDA;
@@ -882,7 +905,6 @@ int pic_profile_begin(pic_t *h, int32_t max_steps)
 {
     if (!h || max_steps < 1) return PIC_EINVAL;
     for (cudaEvent_t ev : h->prof_events) cudaEventDestroy(ev);
-    delete h->adj;
     h->prof_events.assign((size_t)max_steps * (PIC_NUM_PHASES + 1), nullptr);
     for (auto &ev : h->prof_events)
         if (cudaEventCreate(&ev) != cudaSuccess) return PIC_ECUDA;
@@ -995,7 +1017,8 @@ int pic_adjoint_begin(pic_t *h, int32_t total_steps, int32_t checkpoint_every)
     cudaError_t e = launch_adj_init(h->d_runs, a->A.wid, a->zb, n, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return PIC_ECUDA;
-    h->use_graph = false;  // recording and checkpoints interleave with the steps
+    // checkpoints are taken between graph replays; the recording steps of
+    // the reverse sweep run without graphs (their record buffers change)
     return PIC_OK;
 }
 
@@ -1066,7 +1089,7 @@ int pic_adjoint_backward(pic_t *h, const pic_objective *obj, double *L, double *
         Ckpt &ck = a.ck[seg];
         // restore the segment's start state and recompute it, recording each step
         e = cudaMemcpyAsync(h->d_states, ck.st, sizeof(RunState), cudaMemcpyDeviceToDevice, st);
-        if (e == cudaSuccess) e = launch_part_copy(h->d_runs, ck.pc, n, 1, st);
+        if (e == cudaSuccess) e = launch_part_copy(h->dim, h->d_runs, ck.pc, n, 1, st);
         for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
             e = cudaMemcpyAsync(r.E[c], ck.E[c], sizeof(float) * nc, cudaMemcpyDeviceToDevice, st);
             if (e == cudaSuccess) e = cudaMemcpyAsync(r.B[c], ck.B[c], sizeof(float) * nc, cudaMemcpyDeviceToDevice, st);
@@ -1191,6 +1214,7 @@ void pic_destroy(pic_t *h)
         if (h->free) h->free(p, h->ctx);
         else cudaFree(p);
     }
+    delete h->adj;
     delete h;
 }
 

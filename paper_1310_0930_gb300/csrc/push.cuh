@@ -52,7 +52,17 @@ struct Geo {
     static constexpr int JX = TX + 2 * D + DLO + DHI, JY = TY + 2 * D + DLO + DHI;
     static constexpr int JZ = DIM == 3 ? TZ + 2 * D + DLO + DHI : 1;
     static constexpr int JHX = D + DLO, JHY = D + DLO, JHZ = DIM == 3 ? D + DLO : 0;
-    static constexpr int FVOL = FX * FY * FZ, JVOL = JX * JY * JZ;
+    // 3D plane strides padded to 8 or 24 (mod 32) words, whichever needs
+    // less padding: stencil rows one plane apart then fall in different
+    // shared-memory banks (4 consecutive planes cover 4 distinct bank groups).
+    static constexpr int plane(int a)
+    {
+        return DIM == 3 ? a + ((8 - a % 32 + 32) % 32 < (24 - a % 32 + 32) % 32 ? (8 - a % 32 + 32) % 32
+                                                                                : (24 - a % 32 + 32) % 32)
+                        : a;
+    }
+    static constexpr int FPL = plane(FX * FY), JPL = plane(JX * JY);
+    static constexpr int FVOL = FPL * FZ, JVOL = JPL * JZ;
     static __host__ __device__ constexpr int tile(int a) { return a == 0 ? TX : (a == 1 ? TY : (DIM == 3 ? TZ : 1)); }
     static constexpr size_t SMEM = sizeof(float) * 6 * FVOL + sizeof(int) * 2 * 3 * JVOL;
 };
@@ -63,7 +73,7 @@ template <int DIM, int P, class G, int C>
 __device__ __forceinline__ float gather_s(const float *Fs, int bx, int by, int bz, const float *wx,
                                           const float *wy, const float *wz)
 {
-    const float *p = Fs + C * G::FVOL + (bx + G::FHX) + G::FX * ((by + G::FHY) + G::FY * (bz + G::FHZ));
+    const float *p = Fs + C * G::FVOL + (bx + G::FHX) + G::FX * (by + G::FHY) + G::FPL * (bz + G::FHZ);
     float s = 0.f;
 #pragma unroll
     for (int c = 0; c < (DIM == 3 ? P + 1 : 1); ++c) {
@@ -72,7 +82,7 @@ __device__ __forceinline__ float gather_s(const float *Fs, int bx, int by, int b
         for (int b = 0; b <= P; ++b) {
             float sx = 0.f;
 #pragma unroll
-            for (int a = 0; a <= P; ++a) sx = fmaf(wx[a], p[a + G::FX * (b + G::FY * c)], sx);
+            for (int a = 0; a <= P; ++a) sx = fmaf(wx[a], p[a + G::FX * b + G::FPL * c], sx);
             sy = fmaf(wy[b], sx, sy);
         }
         s = DIM == 3 ? fmaf(wz[c], sy, s) : sy;
@@ -309,8 +319,8 @@ __device__ __forceinline__ void deposit3_smem(const Axis<P> *ax, float S, int *J
     const unsigned act = __activemask();
     const bool f0 = __any_sync(act, ax[0].shift != 0), f1 = __any_sync(act, ax[1].shift != 0),
                f2 = __any_sync(act, ax[2].shift != 0);
-    const int base = (ax[0].wb + G::JHX) + G::JX * ((ax[1].wb + G::JHY) + G::JY * (ax[2].wb + G::JHZ));
-    constexpr int s0 = 1, s1 = G::JX, s2 = G::JX * G::JY;
+    const int base = (ax[0].wb + G::JHX) + G::JX * (ax[1].wb + G::JHY) + G::JPL * (ax[2].wb + G::JHZ);
+    constexpr int s0 = 1, s1 = G::JX, s2 = G::JPL;
 #pragma unroll
     for (int comp = 0; comp < 3; ++comp) {
         float pa[W - 1], Ab[W], Db[W], Ac[W], Dc[W];
@@ -504,7 +514,8 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
     float S = 1.f;  // fixed-point scale of this tile's J
     if (tile_item) {
         for (int l = threadIdx.x; l < G::FVOL; l += blockDim.x) {
-            const int lx = l % G::FX, ly = (l / G::FX) % G::FY, lz = l / (G::FX * G::FY);
+            const int lz = l / G::FPL, lxy = l - lz * G::FPL, ly = lxy / G::FX, lx = lxy - ly * G::FX;
+            if (ly >= G::FY) continue;  // plane padding
             const int gx = modi(org[0] - G::FHX + lx, n0);
             const int gy = modi(org[1] - G::FHY + ly, n1);
             const int gz = DIM == 3 ? modi(org[2] - G::FHZ + lz, n2) : 0;
@@ -662,8 +673,8 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
                 hi[c] = Jhi[c * G::JVOL + l];
                 lo[c] = Jlo[c * G::JVOL + l];
             }
-            if (((hi[0] | lo[0]) | (hi[1] | lo[1]) | (hi[2] | lo[2])) == 0) continue;
-            const int lx = l % G::JX, ly = (l / G::JX) % G::JY, lz = l / (G::JX * G::JY);
+            if (((hi[0] | lo[0]) | (hi[1] | lo[1]) | (hi[2] | lo[2])) == 0) continue;  // (plane padding too)
+            const int lz = l / G::JPL, lxy = l - lz * G::JPL, ly = lxy / G::JX, lx = lxy - ly * G::JX;
             const int gx = modi(org[0] - G::JHX + lx, n0);
             const int gy = modi(org[1] - G::JHY + ly, n1);
             const int gz = DIM == 3 ? modi(org[2] - G::JHZ + lz, n2) : 0;

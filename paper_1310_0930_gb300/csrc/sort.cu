@@ -3,17 +3,25 @@
 // The GPU counterpart of the paper's particle migration between nodes after
 // the push (Sec. 3): particles that moved are regrouped with the tile that
 // now owns them, dead slots (absorbed particles) are dropped, and the tail
-// of freshly injected plasma is merged.  Steps, per run:
-//   1. zero the tile counters;
-//   2. histogram of tile keys, aggregated per warp (match on the key) and
-//      per CTA (a shared-memory key table over a chunk of kSortChunk slots),
-//      so that the global counters see a few atomics per chunk;
-//   3. exclusive scan of the counts into tile offsets (one CTA per run);
+// of freshly injected plasma is merged.  The key of slot i is
+// (tile, i mod nsub): each tile's particles are split into nsub sub-buckets
+// by slot index, which interleaves the particles of one cell across the
+// tile's range, so that the 32 particles a warp pushes together come from
+// different cells and their deposits hit different shared-memory banks.
+// Steps, per run:
+//   1. zero the key counters;
+//   2. histogram of keys, aggregated per warp (match on the key) and per CTA
+//      (a shared-memory key table over a chunk of kSortChunk slots), so that
+//      the global counters see a few atomics per chunk;
+//   3. exclusive scan of the counters in blocks of kScanChunk keys (block
+//      sums, then each block adds the sum of the blocks before it); the
+//      counters become the scatter cursors and tile_off[t] the offset of
+//      key (t, 0);
 //   4. scatter every live particle into the alternate buffer at
 //      offset[key] + rank: ranks within the chunk come from the CTA's key
 //      table, and one cursor atomic per (chunk, key) reserves the range;
 //   5. flip the buffer and set the sorted count.
-// Order within a tile is not stable (cursor atomics); nothing downstream
+// Order within a key is not stable (cursor atomics); nothing downstream
 // depends on it.
 #include "common.cuh"
 #include "internal.h"
@@ -35,7 +43,7 @@ __device__ __forceinline__ int seg_run(const Seg &s, int b)
 
 // What the tile key of a packed cell depends on, held in registers.
 struct KeyCtx {
-    int b0, b1, m0, m1, t0, t1, t2, nt0, nt1, dim, open_last, origin, nl, lo, hi;
+    int b0, b1, m0, m1, t0, t1, t2, nt0, nt1, dim, open_last, origin, nl, lo, hi, nsub;
     long long n_total;
 };
 
@@ -58,7 +66,14 @@ __device__ __forceinline__ KeyCtx key_ctx(const Run &r, const RunState &s)
     k.lo = r.margin;
     k.hi = r.n[r.dim - 1] - r.margin;
     k.n_total = s.n_total;
+    k.nsub = r.nsub;
     return k;
+}
+
+// (tile, sub-bucket) key of slot i
+__device__ __forceinline__ int sub_key(const KeyCtx &k, int tile, long long i)
+{
+    return tile < 0 ? -1 : tile * k.nsub + (int)(i & (k.nsub - 1));
 }
 
 // tile key of a packed cell, or -1 for a dead slot / a particle outside the
@@ -75,12 +90,13 @@ __device__ __forceinline__ int key_of_cell(const KeyCtx &k, int32_t c)
     return (cx >> k.t0) + k.nt0 * ((cy >> k.t1) + k.nt1 * (k.dim == 3 ? (cz >> k.t2) : 0));
 }
 
-__global__ void sort_zero_kernel(const Run *__restrict__ runs, int nruns, int max_tiles)
+__global__ void sort_zero_kernel(const Run *__restrict__ runs, int nruns)
 {
     const int ri = blockIdx.y;
     if (ri >= nruns) return;
     const Run &r = runs[ri];
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < r.ntiles; t += gridDim.x * blockDim.x)
+    const long long nk = (long long)r.ntiles * r.nsub;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nk; t += (long long)gridDim.x * blockDim.x)
         r.tile_cnt[t] = 0;
 }
 
@@ -146,7 +162,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_count_kernel(const Run *__r
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
-        const int key = key_of_cell(kc, cell[j]);
+        const int key = sub_key(kc, key_of_cell(kc, cell[j]), i0 + j * kSortThreads + threadIdx.x);
         const unsigned peers = key_peers(key);
         if (key >= 0 && lane == __ffs(peers) - 1) {
             const int e = table_slot(t, key);
@@ -159,37 +175,75 @@ __global__ void __launch_bounds__(kSortThreads) sort_count_kernel(const Run *__r
         if (t.key[e] >= 0 && t.cnt[e] > 0) atomicAdd(&r.tile_cnt[t.key[e]], t.cnt[e]);
 }
 
-// One CTA per run: tile_off = exclusive scan of tile_cnt; tile_cnt becomes
-// the scatter cursor (= tile_off).
-__global__ void __launch_bounds__(1024) sort_scan_kernel(const Run *__restrict__ runs, int nruns)
+// Exclusive scan of the key counters, pass 1: block b of a run scans its
+// kScanChunk keys in place (exclusive, block-local) and stores its total.
+// Thread t owns kScanItems consecutive keys.
+__global__ void __launch_bounds__(kScanThreads) sort_scan_local_kernel(const Run *__restrict__ runs, Seg seg,
+                                                                       int *__restrict__ sums)
 {
-    const int ri = blockIdx.x;
-    if (ri >= nruns) return;
+    __shared__ int warp_tot[kScanThreads / 32];
+    const int ri = seg_run(seg, blockIdx.x);
     const Run &r = runs[ri];
-    const int nt = r.ntiles;
-    const int per = (nt + blockDim.x - 1) / blockDim.x;
-    const int lo = threadIdx.x * per;
-    const int hi = lo + per < nt ? lo + per : nt;
-    long long sum = 0;
-    for (int t = lo; t < hi; ++t) sum += r.tile_cnt[t];
-    __shared__ long long part[1024];
-    part[threadIdx.x] = sum;
+    const long long nk = (long long)r.ntiles * r.nsub;
+    const long long k0 = (long long)(blockIdx.x - seg.start[ri]) * kScanChunk + (long long)threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int tot = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        v[q] = k0 + q < nk ? r.tile_cnt[k0 + q] : 0;
+        tot += v[q];
+    }
+    // block exclusive scan of the per-thread totals
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
     __syncthreads();
-    // Hillis-Steele inclusive scan over the per-thread partial sums
-    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-        long long v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
+    int before = 0, all = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) {
+        before += w < wid ? warp_tot[w] : 0;
+        all += warp_tot[w];
     }
-    long long run = part[threadIdx.x] - sum;
-    for (int t = lo; t < hi; ++t) {
-        int c = r.tile_cnt[t];
-        r.tile_off[t] = (int32_t)run;
-        r.tile_cnt[t] = (int32_t)run;
-        run += c;
+    int run = before + inc - tot;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        if (k0 + q < nk) r.tile_cnt[k0 + q] = run;
+        run += v[q];
     }
-    if (threadIdx.x == blockDim.x - 1) r.tile_off[nt] = (int32_t)part[blockDim.x - 1];
+    if (threadIdx.x == 0) sums[blockIdx.x] = all;
+}
+
+// Pass 2: block b adds the totals of the run's blocks before it; the
+// counters become the scatter cursors, tile_off[t] = cursor of key (t, 0),
+// and the last block sets tile_off[ntiles] = the run's total.
+__global__ void __launch_bounds__(kScanThreads) sort_scan_add_kernel(const Run *__restrict__ runs, Seg seg,
+                                                                     const int *__restrict__ sums)
+{
+    __shared__ int warp_tot[kScanThreads / 32];
+    const int ri = seg_run(seg, blockIdx.x);
+    const Run &r = runs[ri];
+    const int b0 = seg.start[ri], b = blockIdx.x;
+    int part = 0;
+    for (int q = b0 + threadIdx.x; q < b; q += blockDim.x) part += sums[q];
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) warp_tot[threadIdx.x >> 5] = part;
+    __syncthreads();
+    int prefix = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) prefix += warp_tot[w];
+    const long long nk = (long long)r.ntiles * r.nsub;
+    const long long k0 = (long long)(b - b0) * kScanChunk;
+    for (int q = threadIdx.x; q < kScanChunk; q += blockDim.x) {
+        const long long k = k0 + q;
+        if (k >= nk) break;
+        const int c = r.tile_cnt[k] + prefix;
+        r.tile_cnt[k] = c;
+        if ((k & (r.nsub - 1)) == 0) r.tile_off[k / r.nsub] = c;
+    }
+    if (b == seg.start[ri + 1] - 1 && threadIdx.x == 0) r.tile_off[r.ntiles] = prefix + sums[b];
 }
 
 // Scatter: each CTA ranks its chunk's particles per key in shared memory,
@@ -222,7 +276,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(const Run *_
     int slot[kSortItems], rank[kSortItems];
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
-        const int key = key_of_cell(kc, cell[j]);
+        const int key = sub_key(kc, key_of_cell(kc, cell[j]), i0 + j * kSortThreads + threadIdx.x);
         const unsigned peers = key_peers(key);
         const int leader = __ffs(peers) - 1;
         int e = -2, off = 0;
@@ -291,12 +345,12 @@ __global__ void sort_finish_kernel(const Run *__restrict__ runs, int nruns)
 
 }  // namespace
 
-cudaError_t launch_sort(const Run *runs, int nruns, Seg parts, int max_tiles, cudaStream_t st)
+cudaError_t launch_sort(const Run *runs, int nruns, Seg parts, Seg keys, int *scan_sums, cudaStream_t st)
 {
-    dim3 zg((max_tiles + kBlock - 1) / kBlock < 4096 ? (max_tiles + kBlock - 1) / kBlock : 4096, nruns);
-    sort_zero_kernel<<<zg, kBlock, 0, st>>>(runs, nruns, max_tiles);
+    sort_zero_kernel<<<dim3(1024, nruns), kBlock, 0, st>>>(runs, nruns);
     sort_count_kernel<<<parts.nblocks, kSortThreads, 0, st>>>(runs, parts);
-    sort_scan_kernel<<<nruns, 1024, 0, st>>>(runs, nruns);
+    sort_scan_local_kernel<<<keys.nblocks, kScanThreads, 0, st>>>(runs, keys, scan_sums);
+    sort_scan_add_kernel<<<keys.nblocks, kScanThreads, 0, st>>>(runs, keys, scan_sums);
     sort_scatter_kernel<<<parts.nblocks, kSortThreads, 0, st>>>(runs, parts);
     sort_finish_kernel<<<(nruns + 127) / 128, 128, 0, st>>>(runs, nruns);
     return cudaGetLastError();

@@ -120,3 +120,30 @@ def test_torch_autograd_function():
     assert knots.grad is not None and a0.grad is not None
     assert torch.all(torch.isfinite(knots.grad)) and math.isfinite(float(a0.grad))
     assert float(a0.grad) > 0  # a stronger driver heats the window's electrons
+
+
+def test_profiling_keeps_adjoint_state():
+    """Phase profiling of an adjoint-armed forward run leaves the checkpoints
+    and records intact: the gradient is the one of an unprofiled run."""
+    w, obj = _adjoint_case()
+    parts = inputs.background(w)
+
+    def grad(profile):
+        sim = Simulation(w, track_ids=True, per_particle_weight=True)
+        sim.load(parts)
+        sim.adjoint_begin(w.steps, 16)
+        if profile:
+            sim.profile_begin(w.steps)
+        sim.step(w.steps)
+        if profile:
+            phases, launches = sim.profile_end()
+            assert sum(phases.values()) > 0 and launches > 0
+        res = sim.adjoint_backward(obj["z_lo"], obj["z_hi"], obj["width"], n_knots=len(w.knots))
+        sim.close()
+        return res
+
+    a, b = grad(False), grad(True)
+    assert abs(a["L"] - b["L"]) <= 1e-6 * abs(a["L"])
+    ga, gb = np.asarray(a["dL_dknots"]), np.asarray(b["dL_dknots"])
+    assert np.max(np.abs(ga - gb)) <= 1e-4 * np.max(np.abs(ga))
+    assert abs(a["dL_da0"] - b["dL_da0"]) <= 1e-4 * abs(a["dL_da0"])
