@@ -145,7 +145,8 @@ typedef void (*pic_free_fn)(void *ptr, void *ctx);
 /* Tuning: tile[a] cells per tile per axis (powers of two, 0 = default);
  * sort_interval steps between tile sorts (0 = default); drift: cells a
  * particle may stray outside its tile between sorts and still use the
- * staged fast path (-1 = default); block: threads per tile CTA (0 = default);
+ * staged fast path (-1 = default); block: threads per tile CTA, 128, 256, 384
+ * or 512 (0 = default);
  * persistent: 0 = default (persistent for batches, one CTA per tile
  * otherwise), 1 = one persistent grid whose CTAs take tiles from a device
  * work queue, largest runs first, 2 = one CTA per tile.
@@ -156,7 +157,10 @@ typedef void (*pic_free_fn)(void *ptr, void *ctx);
  * sort_sub: sub-buckets per tile in the sort, 0 = default (1 = none),
  * else a power of two <= 32: slot i of a tile's particles goes to sub-bucket
  * i mod sort_sub, so that the particles one warp pushes together come from
- * different cells (fewer shared-memory bank conflicts in the deposit). */
+ * different cells (fewer shared-memory bank conflicts in the deposit).
+ * tma: 1 = stage the 3D field tile with the tensor-memory accelerator (the
+ * entry 8x8x8 with drift 1, whose tile rows are then 16-byte aligned TMA
+ * box rows), 0 = default (plain loads into the bank-padded tile). */
 typedef struct {
     int32_t tile[3];
     int32_t sort_interval;
@@ -165,6 +169,7 @@ typedef struct {
     int32_t use_graph;
     int32_t persistent;
     int32_t sort_sub;
+    int32_t tma;
 } pic_tuning;
 
 typedef struct {

@@ -68,6 +68,7 @@ struct Run {
     double *rho0;      // initial electron charge density (neutralising background), FP64 diagnostic
     float *mur;        // saved tangential E planes for Mur: [2][4][plane]
     ParticleBuf P[2];
+    const void *tmap;  // 3D: six TMA tensor maps (E0..2, B0..2, 128 bytes each) for the field tile, or null
     int32_t *tile_off; // [ntiles + 1] particle offsets per tile
     int32_t *tile_cnt; // [ntiles * nsub] sort counters / cursors per (tile, sub-bucket)
     int nsub;          // sort sub-buckets per tile (power of two): slot i goes to sub-bucket i % nsub

@@ -33,10 +33,14 @@ constexpr int kScanThreads = 256, kScanItems = 16, kScanChunk = kScanThreads * k
 // Particle kernel (push.cuh) over the compiled tile menu (push_menu.h).
 // push_smem_bytes returns 0 for a (tile, drift) pair that is not compiled.
 int push_default_drift(int dim, const int *tile);
-size_t push_smem_bytes(int dim, int order, const int *tile, int drift);
+// tma: the entry compiled with TMA staging of the field tile (3D only)
+size_t push_smem_bytes(int dim, int order, const int *tile, int drift, bool tma);
+// 3D: extents of the TMA box that loads one component of the field tile
+// (returns 0 for 2D or an entry not compiled with TMA staging)
+int push_tma_box(int dim, int order, const int *tile, int drift, int *box);
 // queue != nullptr: persistent grid of persistent_ctas x (CTAs per SM) taking
 // items from the device counter *queue (reset by the launch).
-cudaError_t launch_push(int dim, int order, const int *tile, int drift, const Run *runs, const Item *items,
+cudaError_t launch_push(int dim, int order, const int *tile, int drift, bool tma, const Run *runs, const Item *items,
                         int nitems, int block, int tail_block, int *queue, int persistent_ctas, cudaStream_t st);
 
 // fields.cu

@@ -11,6 +11,8 @@
 #include <new>
 #include <vector>
 
+#include <cuda.h>  // CUtensorMap and its enums; the encoder is resolved at run time
+
 #include "pic.h"
 #include "common.cuh"
 #include "internal.h"
@@ -75,6 +77,7 @@ struct pic_s {
     int *d_scan = nullptr; // per-block sums of the sort's key scan
     Seg seg_cells{}, seg_planes{}, seg_parts{}, seg_inject{}, seg_keys{};
     int sort_sub = 1;
+    bool use_tma = false;
     size_t push_smem = 0;
     int block = 256, sort_interval = 4, drift = 1, tile[3] = {16, 16, 1};
     bool use_graph = true;
@@ -180,7 +183,7 @@ int validate(const pic_config *c)
     for (int a = 0; a < g.dim; ++a)
         if (t.tile[a] != 0 && !pow2(t.tile[a])) return PIC_EINVAL;
     if (t.drift < -1 || t.drift > 8) return PIC_EINVAL;
-    if (t.block != 0 && t.block != 128 && t.block != 256 && t.block != 512) return PIC_EINVAL;
+    if (t.block != 0 && t.block != 128 && t.block != 256 && t.block != 384 && t.block != 512) return PIC_EINVAL;
     if (t.sort_interval < 0) return PIC_EINVAL;
     if (t.persistent < 0 || t.persistent > 2) return PIC_EINVAL;
     return PIC_OK;
@@ -350,7 +353,7 @@ int enqueue_step(pic_s *h, bool sort)
     if (e == cudaSuccess) e = launch_zero_j(R, h->seg_cells, st);
     mark(PIC_PH_PUSH);
     if (e == cudaSuccess)
-        e = launch_push(h->dim, h->order, h->tile, h->drift, R, h->d_items, h->n_items, h->block, kTail,
+        e = launch_push(h->dim, h->order, h->tile, h->drift, h->use_tma, R, h->d_items, h->n_items, h->block, kTail,
                         h->persistent ? h->d_queue : nullptr, h->num_sms, st);
     mark(PIC_PH_YEE_B1);
     if (e == cudaSuccess) e = launch_yee_b(h->dim, R, h->seg_cells, 0, st);
@@ -407,10 +410,64 @@ int first_step_setup(pic_s *h)
     }
     // sets the push kernel's shared-memory limit outside any graph capture
     cudaError_t e =
-        launch_push(h->dim, h->order, h->tile, h->drift, h->d_runs, h->d_items, 0, h->block, kTail, nullptr, 1,
+        launch_push(h->dim, h->order, h->tile, h->drift, h->use_tma, h->d_runs, h->d_items, 0, h->block, kTail, nullptr, 1,
                     h->stream);
     if (e != cudaSuccess) return PIC_ECUDA;
     h->started = true;
+    return PIC_OK;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn tensor_map_encoder()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+// TMA tensor maps of the six field components for the push kernel's 3D
+// field tile (one box per component and tile), when TMA staging is on.
+// Left null (the kernel then stages with plain loads) when a field base or
+// row is not on a 16-byte boundary.
+int build_tensor_maps(pic_s *h, HostRun &hr)
+{
+    Run &r = hr.r;
+    r.tmap = nullptr;
+    int box[3] = {0, 0, 0};
+    if (r.dim != 3 || !h->use_tma || !push_tma_box(3, h->order, h->tile, h->drift, box)) return PIC_OK;
+    if ((r.n[0] * sizeof(float)) % 16 != 0) return PIC_OK;
+    EncodeTiledFn enc = tensor_map_encoder();
+    if (!enc) return PIC_OK;
+    CUtensorMap maps[6];
+    const cuuint64_t dims[3] = {(cuuint64_t)r.n[0], (cuuint64_t)r.n[1], (cuuint64_t)r.n[2]};
+    const cuuint64_t strides[2] = {(cuuint64_t)r.n[0] * sizeof(float), (cuuint64_t)r.n[0] * r.n[1] * sizeof(float)};
+    const cuuint32_t bx[3] = {(cuuint32_t)box[0], (cuuint32_t)box[1], (cuuint32_t)box[2]}, es[3] = {1, 1, 1};
+    for (int c = 0; c < 6; ++c) {
+        void *base = c < 3 ? (void *)r.E[c] : (void *)r.B[c - 3];
+        if ((uintptr_t)base % 16 != 0) return PIC_OK;
+        if (enc(&maps[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return PIC_OK;
+    }
+    void *d = dev_alloc(h, sizeof(maps));
+    if (!d) return PIC_ENOMEM;
+    cudaError_t e = cudaMemcpyAsync(d, maps, sizeof(maps), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return PIC_ECUDA;
+    r.tmap = d;
     return PIC_OK;
 }
 
@@ -505,7 +562,7 @@ int init_run(pic_s *h, HostRun &hr, int idx)
         hr.inject_per_shift = (long long)plane * ppc_t;
     }
     r.state = h->d_states + idx;
-    return PIC_OK;
+    return build_tensor_maps(h, hr);
 }
 
 int create_common(const pic_config *cfgs, int n, pic_t **out)
@@ -538,11 +595,12 @@ int create_common(const pic_config *cfgs, int n, pic_t **out)
     h->use_graph = t.use_graph != 0 && h->stream != nullptr;
     h->persistent = t.persistent == 1 || (t.persistent == 0 && n > 1);
     h->sort_sub = t.sort_sub ? t.sort_sub : 1;
+    h->use_tma = t.tma > 0;
     if (h->sort_sub < 1 || h->sort_sub > 32 || (h->sort_sub & (h->sort_sub - 1))) {
         delete h;
         return PIC_EINVAL;
     }
-    h->push_smem = push_smem_bytes(h->dim, h->order, h->tile, h->drift);
+    h->push_smem = push_smem_bytes(h->dim, h->order, h->tile, h->drift, h->use_tma);
     if (h->push_smem == 0) {  // (tile, drift) not among the compiled configurations
         delete h;
         return PIC_EINVAL;
@@ -554,7 +612,7 @@ int create_common(const pic_config *cfgs, int n, pic_t **out)
         delete h;
         return PIC_ECUDA;
     }
-    if (h->push_smem + sizeof(Run) + 64 > (size_t)max_smem) {
+    if (h->push_smem + sizeof(Run) + 512 > (size_t)max_smem) {  // + the kernels' static shared memory
         delete h;
         return PIC_EINVAL;  // tile + halo does not fit in shared memory
     }

@@ -42,16 +42,65 @@ constexpr float kLoScale = 4096.f;  // 12 bits for the lo word
 constexpr float kRound = 12582912.f;  // 1.5 * 2^23: v + kRound = 2^23 + 2^22 + rint(v) for |v| < 2^22
 constexpr int kRoundBits = 0x4B400000;  // bit pattern of kRound
 constexpr float kMaxScaled = 4.0e6f;  // bound on one scaled contribution (< 2^22, with margin)
+constexpr int kTmaSpin = 1 << 20;     // bounded waits on the field-tile barrier
+constexpr size_t kSmemBudget = 230000;  // dynamic shared memory of one push CTA (of 227 KB)
 
-template <int DIM, int P, int TX, int TY, int TZ, int D>
+// ---------------------------------------------------------------- TMA staging
+// The 3D field tile is loaded by the tensor-memory accelerator: one 3D box
+// (FX x FY x FZ values) per component into its 128-byte aligned region of
+// the shared-memory tile, all six completing on one mbarrier.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_inval(uint64_t *bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void tmap_acquire(const void *tmap)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmap) : "memory");
+}
+
+// box at (x, y, z) of the field described by tmap into shared memory dst
+__device__ __forceinline__ void tma_load_box(void *dst, const void *tmap, int x, int y, int z, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_addr(dst)),
+        "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
+template <int DIM, int P, int TX, int TY, int TZ, int D, bool T>
 struct Geo {
     static constexpr int GLO = Reach<P>::GLO, GHI = Reach<P>::GHI, DLO = Reach<P>::DLO, DHI = Reach<P>::DHI;
-    static constexpr int FX = TX + 2 * D + GLO + GHI, FY = TY + 2 * D + GLO + GHI;
-    static constexpr int FZ = DIM == 3 ? TZ + 2 * D + GLO + GHI : 1;
-    static constexpr int FHX = D + GLO, FHY = D + GLO, FHZ = DIM == 3 ? D + GLO : 0;
-    static constexpr int JX = TX + 2 * D + DLO + DHI, JY = TY + 2 * D + DLO + DHI;
-    static constexpr int JZ = DIM == 3 ? TZ + 2 * D + DLO + DHI : 1;
-    static constexpr int JHX = D + DLO, JHY = D + DLO, JHZ = DIM == 3 ? D + DLO : 0;
+    static constexpr int up4(int a) { return (a + 3) / 4 * 4; }
     // 3D plane strides padded to 8 or 24 (mod 32) words, whichever needs
     // less padding: stencil rows one plane apart then fall in different
     // shared-memory banks (4 consecutive planes cover 4 distinct bank groups).
@@ -61,10 +110,56 @@ struct Geo {
                                                                                 : (24 - a % 32 + 32) % 32)
                         : a;
     }
-    static constexpr int FPL = plane(FX * FY), JPL = plane(JX * JY);
-    static constexpr int FVOL = FPL * FZ, JVOL = JPL * JZ;
+    // J tile: the deposit window of every particle within D cells of the tile
+    static constexpr int JX = TX + 2 * D + DLO + DHI, JY = TY + 2 * D + DLO + DHI;
+    static constexpr int JZ = DIM == 3 ? TZ + 2 * D + DLO + DHI : 1;
+    static constexpr int JHX = D + DLO, JHY = D + DLO, JHZ = DIM == 3 ? D + DLO : 0;
+    static constexpr int JPL = plane(JX * JY), JVOL = JPL * JZ;
+    // Field tile: rows of FX values starting FHX cells before the tile.
+    // T (the TMA layout, 3D): FHX and FX are multiples of 4 so that each row
+    // is a TMA box row that starts on a 16-byte boundary of the global field
+    // (tile origins are multiples of 8), and the box rows per plane (FY, at
+    // least the rows the stencil needs) and FX are chosen so that the dense
+    // box planes are 8 or 24 (mod 32) words apart and rows not 0 or 16: a
+    // pair whose tile would not fit next to the J tile is skipped; with none
+    // left the rows stay dense.  Otherwise: the rows the stencil needs, with
+    // 3D planes padded as for the J tile.
+    static constexpr bool TL = T && DIM == 3;
+    static constexpr int FHX = TL ? up4(D + GLO) : D + GLO, FHY = D + GLO, FHZ = DIM == 3 ? D + GLO : 0;
+    static constexpr int FZ = DIM == 3 ? TZ + 2 * D + GLO + GHI : 1;
+    static constexpr int NX = TL ? up4(FHX + TX + D + GHI) : TX + 2 * D + GLO + GHI, NY = TY + 2 * D + GLO + GHI;
+    static constexpr size_t bytes_for(int bx, int by)
+    {
+        return 128 + sizeof(float) * 6 * ((bx * by * FZ + 31) / 32 * 32) + sizeof(int) * 6 * JVOL;
+    }
+    static constexpr bool good(int bx, int by)
+    {
+        return ((bx * by) % 32 == 8 || (bx * by) % 32 == 24) && bx % 32 != 0 && bx % 32 != 16 &&
+               bytes_for(bx, by) <= kSmemBudget;
+    }
+    static constexpr int pick(int which)
+    {
+        int best_x = NX, best_y = NY, best = 1 << 30;
+        for (int bx = NX; bx <= NX + 16; bx += 4)
+            for (int by = NY; by <= NY + 4; ++by)
+                if (good(bx, by) && bx * by < best) {
+                    best = bx * by;
+                    best_x = bx;
+                    best_y = by;
+                }
+        return which == 0 ? best_x : best_y;
+    }
+    static constexpr int FX = TL ? pick(0) : NX;
+    static constexpr int FY = TL ? pick(1) : NY;
+    // (the TMA layout keeps dense planes: it is one TMA box per component)
+    static constexpr int FPL = TL ? FX * FY : plane(FX * FY);
+    // component regions of the field tile start on 128-byte boundaries
+    static constexpr int FVOL = (FPL * FZ + 31) / 32 * 32;
+    static constexpr unsigned TMA_BYTES = 6u * FZ * FY * FX * sizeof(float);  // one tile, six components
     static __host__ __device__ constexpr int tile(int a) { return a == 0 ? TX : (a == 1 ? TY : (DIM == 3 ? TZ : 1)); }
-    static constexpr size_t SMEM = sizeof(float) * 6 * FVOL + sizeof(int) * 2 * 3 * JVOL;
+    // (+128: the field tile is placed at the first 128-byte boundary of the
+    // dynamic shared memory, as TMA destinations require)
+    static constexpr size_t SMEM = 128 + sizeof(float) * 6 * FVOL + sizeof(int) * 2 * 3 * JVOL;
 };
 
 // ---------------------------------------------------------------- gather
@@ -469,14 +564,16 @@ __device__ __noinline__ SlowOut advance_global(const Run &r, const GlobalFields 
 
 // One work item: a tile of one run (staged fast path) or a block of that
 // run's unsorted tail (slow path).  Called uniformly by the whole CTA.
-template <int DIM, int P, int TX, int TY, int TZ, int D>
+template <int DIM, int P, int TX, int TY, int TZ, int D, bool T>
 __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const Item it, int tail_block)
 {
-    using G = Geo<DIM, P, TX, TY, TZ, D>;
+    using G = Geo<DIM, P, TX, TY, TZ, D, T>;
     extern __shared__ __align__(16) float smem[];
     __shared__ Run rs;
     __shared__ unsigned slow_cnt;
     __shared__ float wsum[32], wmaxs[32];
+    __shared__ __align__(8) uint64_t tma_bar;
+    if (G::TL && threadIdx.x == 0) mbar_init(&tma_bar);
     {
         const int *src = reinterpret_cast<const int *>(runs + it.run);
         int *dst = reinterpret_cast<int *>(&rs);
@@ -506,14 +603,38 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
         p0 = n_sorted + (long long)it.a * tail_block;
         p1 = p0 + tail_block < n_total ? p0 + tail_block : n_total;
     }
-    if (p0 >= p1) return;
+    if (p0 >= p1) {
+        if (G::TL && threadIdx.x == 0) mbar_inval(&tma_bar);
+        return;
+    }
 
-    float *Fs = smem;
-    int *Jhi = reinterpret_cast<int *>(smem + 6 * G::FVOL);
+    // (an offset from the shared array, so that the compiler keeps shared
+    // loads and stores for the tiles)
+    float *Fs = smem + ((128u - (smem_addr(smem) & 127u)) & 127u) / sizeof(float);
+    int *Jhi = reinterpret_cast<int *>(Fs + 6 * G::FVOL);
     int *Jlo = Jhi + 3 * G::JVOL;
     float S = 1.f;  // fixed-point scale of this tile's J
+    // TMA staging: 3D tiles whose field box lies inside the stored grid
+    // (boxes that wrap around a periodic or ring boundary are loaded below)
+    bool tma = false;
+    if (G::TL && tile_item && r.tmap) {
+        const int x0 = org[0] - G::FHX, y0 = org[1] - G::FHY, z0 = org[2] - G::FHZ;
+        tma = x0 >= 0 && x0 + G::FX <= n0 && y0 >= 0 && y0 + G::FY <= n1 && z0 >= 0 && z0 + G::FZ <= n2;
+        // the box row must start on a 16-byte boundary of the field and each
+        // destination on a 128-byte boundary of shared memory
+        tma = tma && (x0 & 3) == 0 && (smem_addr(Fs) & 127u) == 0 && ((G::FVOL * sizeof(float)) & 127u) == 0;
+        if (tma && threadIdx.x == 0) {
+            const char *maps = reinterpret_cast<const char *>(r.tmap);
+            mbar_expect(&tma_bar, G::TMA_BYTES);
+            for (int c = 0; c < 6; ++c) {
+                const void *m = maps + 128 * c;
+                tmap_acquire(m);
+                tma_load_box(Fs + c * G::FVOL, m, x0, y0, z0, &tma_bar);
+            }
+        }
+    }
     if (tile_item) {
-        for (int l = threadIdx.x; l < G::FVOL; l += blockDim.x) {
+        for (int l = tma ? G::FVOL : threadIdx.x; l < G::FVOL; l += blockDim.x) {
             const int lz = l / G::FPL, lxy = l - lz * G::FPL, ly = lxy / G::FX, lx = lxy - ly * G::FX;
             if (ly >= G::FY) continue;  // plane padding
             const int gx = modi(org[0] - G::FHX + lx, n0);
@@ -560,6 +681,14 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
         }
         const float B = 1.01f * fabsf(r.q) * wtot, M = fabsf(r.q) * wmax;
         S = B > 0.f ? fminf(1073741824.f / B, kMaxScaled / M) : 1.f;
+        if (tma) {  // bounded wait for the field tile; a timeout is latched in the status
+            bool done = false;
+            for (int it = 0; it < kTmaSpin && !done; ++it) done = mbar_try_wait(&tma_bar, 0);
+            if (!done) {
+                if (threadIdx.x == 0) atomicOr(&stp->status, kStatusTimeout);
+                for (int it = 0; it < kTmaSpin && !done; ++it) done = mbar_try_wait(&tma_bar, 0);
+            }
+        }
         __syncthreads();
     }
 
@@ -663,6 +792,7 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
     }
     if (my_slow) atomicAdd(&slow_cnt, my_slow);
     __syncthreads();
+    if (G::TL && threadIdx.x == 0) mbar_inval(&tma_bar);  // every wait on it has returned
     if (tile_item) {
         // flush the tile's current to global J (wrapping the halo)
         const float inv = 1.f / S, inv_lo = inv * (1.f / kLoScale);
@@ -689,16 +819,16 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
 
 // One CTA per item.  The persistent schedule is a kernel of its own so that
 // its loop state does not compete with the item body for registers.
-template <int DIM, int P, int TX, int TY, int TZ, int D>
+template <int DIM, int P, int TX, int TY, int TZ, int D, bool T>
 __global__ void __launch_bounds__(512) push_kernel(const Run *__restrict__ runs, const Item *__restrict__ items,
                                                    int tail_block)
 {
-    process_item<DIM, P, TX, TY, TZ, D>(runs, items[blockIdx.x], tail_block);
+    process_item<DIM, P, TX, TY, TZ, D, T>(runs, items[blockIdx.x], tail_block);
 }
 
 // Persistent grid: CTAs take items from the device work queue (items
 // ordered largest first) until it is empty.
-template <int DIM, int P, int TX, int TY, int TZ, int D>
+template <int DIM, int P, int TX, int TY, int TZ, int D, bool T>
 __global__ void __launch_bounds__(512) push_queue_kernel(const Run *__restrict__ runs,
                                                          const Item *__restrict__ items, int nitems, int tail_block,
                                                          int *queue)
@@ -710,18 +840,18 @@ __global__ void __launch_bounds__(512) push_queue_kernel(const Run *__restrict__
         const int idx = s_item;
         __syncthreads();
         if (idx >= nitems) break;
-        process_item<DIM, P, TX, TY, TZ, D>(runs, items[idx], tail_block);
+        process_item<DIM, P, TX, TY, TZ, D, T>(runs, items[idx], tail_block);
         __syncthreads();
     }
 }
 
-template <int DIM, int P, int TX, int TY, int TZ, int D>
+template <int DIM, int P, int TX, int TY, int TZ, int D, bool T>
 cudaError_t launch_t(const Run *runs, const Item *items, int nitems, int block, int tail_block, int *queue,
                      int persistent_ctas, cudaStream_t st)
 {
-    using G = Geo<DIM, P, TX, TY, TZ, D>;
-    auto k = push_kernel<DIM, P, TX, TY, TZ, D>;
-    auto kq = push_queue_kernel<DIM, P, TX, TY, TZ, D>;
+    using G = Geo<DIM, P, TX, TY, TZ, D, T>;
+    auto k = push_kernel<DIM, P, TX, TY, TZ, D, T>;
+    auto kq = push_queue_kernel<DIM, P, TX, TY, TZ, D, T>;
     static bool attr_set = false;  // raise the opt-in shared-memory limit once
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);

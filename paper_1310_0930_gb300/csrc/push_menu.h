@@ -8,3 +8,5 @@
 #define PIC_PUSH_MENU_2D(X) X(16, 16, 1, 1) X(16, 16, 1, 2) X(16, 16, 1, 3) X(8, 8, 1, 1) X(32, 32, 1, 2)
 #define PIC_PUSH_MENU_3D_A(X) X(8, 8, 8, 1)
 #define PIC_PUSH_MENU_3D_B(X) X(8, 8, 8, 2) X(8, 8, 4, 1)
+// 3D entries also compiled with TMA staging of the field tile
+#define PIC_PUSH_MENU_3D_TMA(X) X(8, 8, 8, 1)

@@ -77,6 +77,7 @@ def make_config(w: Workload, *, tuning: Optional[dict] = None, track_ids=False, 
     cfg.tuning.use_graph = int(t.get("use_graph", 1))
     cfg.tuning.persistent = int(t.get("persistent", 0))
     cfg.tuning.sort_sub = int(t.get("sort_sub", 0))
+    cfg.tuning.tma = int(t.get("tma", 0))
     if alloc is not None:
         cfg.alloc = alloc
         cfg.free = free
