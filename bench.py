@@ -85,6 +85,18 @@ def particle_chunks(w):
     return chunks
 
 
+# Per-particle figures of the push kernel from one ncu capture of a smaller
+# case of the same workload (summaries in profiles/, named below): DRAM
+# bytes (dram__bytes_read.sum + dram__bytes_write.sum) and warp instructions
+# (smsp__inst_executed.sum) per particle of one launch.  They are scaled to a
+# full launch by its particle count, and hold for the default tuning of the
+# kernel they were taken with.
+PUSH_PROFILE = {
+    ("lwfa_3d", 2): (53.3, 31.4, "push_kernel_lwfa3d_quadratic_64x64x256.md"),
+    ("warm_3d", 2): (59.7, 93.4, "push_kernel_warm3d_quadratic_128x128x128.md"),
+}
+
+
 def algorithmic_bytes(w, n_particles):
     """Bytes the method must move once per step (state read + write): per
     particle 2 * (4 packed cell + 4*dim offsets + 12 momentum [+4 weight]);
@@ -407,6 +419,16 @@ def main():
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = push_bytes / (push_ms / 1e3) / 1e9
+    prof = PUSH_PROFILE.get((w.name, w.order)) if not tuning and args.scale == 1.0 else None
+    traffic = prof[0] * n_avg if prof else None
+    issue = None
+    if prof:
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = (clk or {}).get("sm_mhz") or 2070.0
+        peak_issue = sms * 4 * mhz * 1e6  # four warp schedulers per SM, one instruction per clock each
+        ach_issue = prof[1] * n_avg / (push_ms / 1e3)
+        issue = {"achieved": ach_issue, "peak": peak_issue, "unit": "warp-instructions/s",
+                 "frac": ach_issue / peak_issue, "source": "profiles/" + prof[2]}
     status = d1["status"]
     sim.close()
     del sim
@@ -464,7 +486,9 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "timed": "device-resident state, phase events recorded on the library stream"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "push_kernel<%d,%d>" % (w.dim, w.order),
+                     "traffic": traffic, "kernel": "push_kernel<%d,%d>" % (w.dim, w.order),
+                     "traffic_source": ("ncu capture scaled by particle count, profiles/" + prof[2]) if prof else None,
+                     "issue": issue,
                      "bytes_per_launch": push_bytes, "avg_launch_ms": push_ms,
                      "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json)" if peaks else "fallback"},
         "step_roofline_frac": step_bytes / (ms / args.steps / 1e3) / 1e9 / peak,
