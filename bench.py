@@ -160,9 +160,11 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def cpu_baseline(w, budget_s, steps_hint=None):
+def cpu_baseline(w, budget_s, steps=3, warmup=0):
     """Time the FP64 oracle, as it stands, on a bounded crop of the same
-    workload (same cells, dt, density, ppc, order, laser) on all host cores."""
+    workload (same cells, dt, density, ppc, order, laser) on all host cores:
+    `warmup` untimed steps, then `steps` timed steps, the crop sized from a
+    one-step calibration so that the timed steps take about budget_s."""
     import oracle
     from paper_1310_0930_gb300 import inputs
     cores = os.cpu_count() or 1
@@ -182,29 +184,34 @@ def cpu_baseline(w, budget_s, steps_hint=None):
         return sim, parts.n
 
     # calibrate on a small crop, then size the sample to the budget
-    if w.dim == 3:
-        base = (16, 16, 64)
-    else:
-        base = (32, 32)
+    base = (16, 16, 64) if w.dim == 3 else (32, 32)
     sim, n = make(base)
     t0 = time.perf_counter()
     sim.step(1)
     t_ps = (time.perf_counter() - t0) / n
-    steps = steps_hint or 3
-    target = max(n, int(budget_s / max(t_ps, 1e-9) / steps))
+    target = max(n, int(budget_s / max(t_ps, 1e-9) / max(1, steps)))
+    grow = max(1.0, (target / n) ** 0.5)
     if w.dim == 3:
-        grow = max(1.0, (target / n) ** 0.5)
         ncrop = (min(w.n[0], int(16 * grow) // 8 * 8 or 16), min(w.n[1], int(16 * grow) // 8 * 8 or 16), 64)
     else:
-        grow = max(1.0, (target / n) ** 0.5)
         ncrop = (min(w.n[0], int(32 * grow) // 8 * 8), min(w.n[1], int(32 * grow) // 8 * 8))
     sim, n = make(ncrop)
+    if warmup:
+        sim.step(warmup)
     t0 = time.perf_counter()
     sim.step(steps)
     dt_s = time.perf_counter() - t0
     return {"value": n * steps / dt_s, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "FP64 oracle, %s crop %s cells (%d particles, same d/dt/density/ppc/order/laser), "
-                      "%d steps, %.1f s" % (w.name, "x".join(map(str, ncrop)), n, steps, dt_s)}
+                      "%d warm-up + %d timed steps, %.1f s timed" % (w.name, "x".join(map(str, ncrop)), n, warmup,
+                                                                     steps, dt_s)}
+
+
+def workload_config(w, n_particles):
+    """The workload description shared by both arms of the JSON line."""
+    return {"workload": "%s %s cells, %d ppc, order %d" % (w.name, "x".join(map(str, w.n)), w.ppc_total, w.order),
+            "grid": list(w.n), "d": list(w.d), "dt": w.dt, "particles": int(n_particles),
+            "window": w.window is not None, "laser_a0": w.laser.a0 if w.laser else None}
 
 
 def scan_bench(args):
@@ -333,19 +340,29 @@ def adjoint_bench(args):
 
 
 def reference_arm(args):
+    """The FP64 oracle timed on the host cores on the native arm's workload
+    (a bounded crop; the whole run takes about a minute).  Under torchrun
+    only rank 0 works."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     w = workload(args.workload, args.scale, args.order)
-    per_step_budget = 60.0 / max(1, args.steps + args.warmup)
-    cb = cpu_baseline(w, per_step_budget * (args.steps + args.warmup), steps_hint=args.steps + args.warmup)
+    if args.workload in ("scan_2d", "adjoint_2d"):
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the single-run workloads only"}))
+        return 0
+    cb = cpu_baseline(w, 45.0, steps=max(1, args.steps), warmup=args.warmup)
+    n_full = w.n_particles_background()
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "grid": list(w.n), "ppc": list(w.ppc), "order": w.order},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n_full / cb["value"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(workload_config(w, n_full), timed="FP64 oracle on the host cores, a crop of the "
+                                                             "workload; ms_per_step extrapolated to the full box"),
             "cpu_baseline": {"kind": cb["kind"], "cores": cb["cores"], "sample": cb["sample"], "value": cb["value"]},
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+    if args.out:
+        with open(args.out, "w") as f:
+            f.write(json.dumps(line) + "\n")
     return 0
 
 
@@ -478,13 +495,10 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "%s %s cells, %d ppc, order %d" % (w.name, "x".join(map(str, w.n)), w.ppc_total,
-                                                                 w.order),
-                   "grid": list(w.n), "d": list(w.d), "dt": w.dt, "particles": int(n_avg),
-                   "window": w.window is not None, "laser_a0": w.laser.a0 if w.laser else None,
-                   "l2": "inputs larger than L2 (%.1f GB particle state)" % (n_avg * sp / 1e9),
-                   "parallelism": "replicas" if world > 1 else "single GPU",
-                   "timed": "device-resident state, phase events recorded on the library stream"},
+        "config": dict(workload_config(w, n0), particles_timed=int(n_avg),
+                       l2="inputs larger than L2 (%.1f GB particle state)" % (n_avg * sp / 1e9),
+                       parallelism="replicas" if world > 1 else "single GPU",
+                       timed="device-resident state, phase events recorded on the library stream"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "kernel": "push_kernel<%d,%d>" % (w.dim, w.order),
                      "traffic_source": ("ncu capture scaled by particle count, profiles/" + prof[2]) if prof else None,
