@@ -713,9 +713,17 @@ __device__ __forceinline__ void adj_one(const Run &r, const AdjPtrs &A, const Tr
             }
         }
     }
-    for (int a = 0; a < DIM; ++a) A.sx[a][s] = lxo[a];
-    for (int a = 0; a < 3; ++a) A.su[a][s] = lu0[a];
-    A.sw[s] = in.lw + (double)lw;
+    // outputs: in place, or (after a sort) at the slot the particle had before it
+    if (ts.src) {
+        const long long o = ts.src[s];
+        for (int a = 0; a < DIM; ++a) A.ox[a][o] = lxo[a];
+        for (int a = 0; a < 3; ++a) A.ou[a][o] = lu0[a];
+        A.ow[o] = in.lw + (double)lw;
+    } else {
+        for (int a = 0; a < DIM; ++a) A.sx[a][s] = lxo[a];
+        for (int a = 0; a < 3; ++a) A.su[a][s] = lu0[a];
+        A.sw[s] = in.lw + (double)lw;
+    }
 }
 
 template <int DIM>
@@ -820,6 +828,8 @@ __global__ void __launch_bounds__(128, 3) adj_particles_tiled_kernel(const Run *
 #pragma unroll
             for (int a = 0; a < DIM; ++a) zero = zero && cur.lx[a] == 0.f;
             skip = zero;
+            // the accumulated weight adjoint still follows the particle
+            if (skip && ts.src) A.ow[ts.src[s]] = cur.lw;
         }
         if (!skip) {
             int rel[3] = {0, 0, 0};

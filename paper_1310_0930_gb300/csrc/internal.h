@@ -55,7 +55,10 @@ cudaError_t launch_window(const Run *runs, Seg planes, Seg inject, cudaStream_t 
 // sort.cu
 // keys: segments of kScanChunk (tile, sub-bucket) keys; scan_sums: one int
 // per key block.
-cudaError_t launch_sort(const Run *runs, int nruns, Seg parts, Seg keys, int *scan_sums, cudaStream_t st);
+// src_out (may be null): for each sorted slot, the slot the particle had
+// before the sort (single-run handles).
+cudaError_t launch_sort(const Run *runs, int nruns, Seg parts, Seg keys, int *scan_sums, int32_t *src_out,
+                        cudaStream_t st);
 
 // diag.cu
 cudaError_t launch_pack(const Run *run, long long base, long long n, int dim, const int32_t *cell,
@@ -80,6 +83,8 @@ struct AdjPtrs {
     float *wid;                                   // weight by id
     float *sx[3], *su[3];                         // particle adjoints by slot of the current record
     double *sw;
+    float *ox[3], *ou[3];                         // the same, permuted to the slots before a sort
+    double *ow;
 };
 // one recorded step: the particles and fields the push of that step read
 struct TrajStep {
@@ -89,6 +94,8 @@ struct TrajStep {
     const float *w;
     const int32_t *id;
     const int32_t *tile_off;  // tile offsets of the sort these slots follow (null: flat kernel)
+    const int32_t *src;       // slot each particle had before the sort of this step (null: no sort);
+                              // outputs then go to ox/ou/ow at that slot
     long long n;
     const float *E[3];
     const float *B[3];

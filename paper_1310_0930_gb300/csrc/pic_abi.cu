@@ -42,6 +42,7 @@ struct Ckpt {
 };
 struct Rec {
     PartCopy pc;
+    int32_t *src;       // after a sort: the slot each particle had before it
     float *E[3], *B[3];
     int32_t *tile_off;  // tile offsets of the last sort (the slots' grouping)
     double time;
@@ -327,7 +328,10 @@ int enqueue_step(pic_s *h, bool sort)
         if (ev && e == cudaSuccess) e = cudaEventRecord(ev[ph], st);
     };
     mark(PIC_PH_SORT);
-    if (sort) e = launch_sort(R, h->nruns, h->seg_parts, h->seg_keys, h->d_scan, st);
+    // a recorded step keeps, after its sort, the slot each particle had before it
+    int32_t *src_out = nullptr;
+    if (sort && h->adj && h->adj->rec_on) src_out = h->adj->rec[h->steps_done - h->adj->rec_base].src;
+    if (sort) e = launch_sort(R, h->nruns, h->seg_parts, h->seg_keys, h->d_scan, src_out, st);
     if (e == cudaSuccess && h->adj && h->adj->rec_on) {
         // the push of this step reads these particles and fields
         Rec &rc = h->adj->rec[h->steps_done - h->adj->rec_base];
@@ -1024,12 +1028,16 @@ int pic_adjoint_begin(pic_t *h, int32_t total_steps, int32_t checkpoint_every)
         a->A.lx[c] = c < dim ? F(n) : nullptr;
         a->A.su[c] = F(n);
         a->A.sx[c] = c < dim ? F(n) : nullptr;
+        a->A.ou[c] = F(n);
+        a->A.ox[c] = c < dim ? F(n) : nullptr;
         ok = ok && a->A.lE[c] && a->A.lB[c] && a->A.lJ[c] && a->A.T[c] && a->A.nE[c] && a->A.lu[c] &&
-             (c >= dim || a->A.lx[c]) && a->A.su[c] && (c >= dim || a->A.sx[c]);
+             (c >= dim || a->A.lx[c]) && a->A.su[c] && (c >= dim || a->A.sx[c]) && a->A.ou[c] &&
+             (c >= dim || a->A.ox[c]);
     }
     a->A.lw = (double *)dev_alloc(h, sizeof(double) * n);
     a->A.sw = (double *)dev_alloc(h, sizeof(double) * n);
-    ok = ok && a->A.sw;
+    a->A.ow = (double *)dev_alloc(h, sizeof(double) * n);
+    ok = ok && a->A.sw && a->A.ow;
     a->A.wid = F(n);
     a->zb = F(n);
     a->la0 = (double *)dev_alloc(h, sizeof(double) * 4);
@@ -1062,7 +1070,8 @@ int pic_adjoint_begin(pic_t *h, int32_t total_steps, int32_t checkpoint_every)
     for (Rec &rc2 : a->rec) {
         rc2.pc = part(true);
         rc2.tile_off = (int32_t *)dev_alloc(h, sizeof(int32_t) * (r.ntiles + 1));
-        ok = ok && rc2.tile_off;
+        rc2.src = (int32_t *)dev_alloc(h, sizeof(int32_t) * n);
+        ok = ok && rc2.tile_off && rc2.src;
         for (int c = 0; c < 3; ++c) {
             rc2.E[c] = F(nc);
             rc2.B[c] = F(nc);
@@ -1162,8 +1171,9 @@ int pic_adjoint_backward(pic_t *h, const pic_objective *obj, double *L, double *
         rc = pic_step(h, s1 - s0);
         a.rec_on = false;
         if (rc) return rc;
-        // particle adjoints follow the slot order of each record; they pass
-        // through id order where that order changes (sorts, segment ends)
+        // particle adjoints follow the slot order of each record: they move to
+        // the slots before a sort through the sort's record of them, and
+        // through id order at segment ends
         e = launch_adj_perm(dim, a.A, a.rec[s1 - 1 - s0].pc.id, n, 1, st);
         if (e != cudaSuccess) return PIC_ECUDA;
         for (int s = s1 - 1; s >= s0; --s) {
@@ -1181,10 +1191,25 @@ int pic_adjoint_backward(pic_t *h, const pic_objective *obj, double *L, double *
             ts.w = rc2.pc.w;
             ts.tile_off = rc2.tile_off;
             ts.n = n;
+            // after a sort inside the segment the kernel writes the adjoints at
+            // the slots of the previous record (zero for particles the sort dropped)
+            const bool moved = s > s0 && rc2.sorted;
+            ts.src = moved ? rc2.src : nullptr;
+            for (int c = 0; c < 3 && moved && e == cudaSuccess; ++c) {
+                e = cudaMemsetAsync(a.A.ou[c], 0, sizeof(float) * n, st);
+                if (e == cudaSuccess && c < dim) e = cudaMemsetAsync(a.A.ox[c], 0, sizeof(float) * n, st);
+            }
+            if (e == cudaSuccess && moved) e = cudaMemsetAsync(a.A.ow, 0, sizeof(double) * n, st);
             if (e == cudaSuccess) e = launch_adj_particles(dim, r.order, h->d_runs, r, a.A, ts, 0, st);
-            if (e == cudaSuccess && (s == s0 || rc2.sorted)) e = launch_adj_perm(dim, a.A, rc2.pc.id, n, 0, st);
-            if (e == cudaSuccess && s > s0 && rc2.sorted)
-                e = launch_adj_perm(dim, a.A, a.rec[s - 1 - s0].pc.id, n, 1, st);
+            if (moved) {
+                for (int c = 0; c < 3; ++c) {
+                    std::swap(a.A.sx[c], a.A.ox[c]);
+                    std::swap(a.A.su[c], a.A.ou[c]);
+                }
+                std::swap(a.A.sw, a.A.ow);
+            }
+            // the segment's first record: back to id order for the previous segment
+            if (e == cudaSuccess && s == s0) e = launch_adj_perm(dim, a.A, rc2.pc.id, n, 0, st);
             if (e != cudaSuccess) return PIC_ECUDA;
         }
     }

@@ -252,7 +252,8 @@ __global__ void __launch_bounds__(kScanThreads) sort_scan_add_kernel(const Run *
 // range start + rank.  Warps whose keys agree write 32 consecutive slots.
 // Cells, table slots and ranks stay in registers; the copy loads a group of
 // kSortGroup particles per thread before storing them.
-__global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(const Run *__restrict__ runs, Seg seg)
+__global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(const Run *__restrict__ runs, Seg seg,
+                                                                    int32_t *__restrict__ src_out)
 {
     __shared__ KeyTable t;
     const int ri = seg_run(seg, blockIdx.x);
@@ -328,6 +329,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(const Run *_
             dst.u[2][o] = v[q][5];
             if (src.w) dst.w[o] = wv[q];
             if (src.id) dst.id[o] = idv[q];
+            if (src_out) src_out[o] = (int32_t)(i0 + j * kSortThreads + threadIdx.x);
         }
     }
 }
@@ -345,13 +347,14 @@ __global__ void sort_finish_kernel(const Run *__restrict__ runs, int nruns)
 
 }  // namespace
 
-cudaError_t launch_sort(const Run *runs, int nruns, Seg parts, Seg keys, int *scan_sums, cudaStream_t st)
+cudaError_t launch_sort(const Run *runs, int nruns, Seg parts, Seg keys, int *scan_sums, int32_t *src_out,
+                        cudaStream_t st)
 {
     sort_zero_kernel<<<dim3(1024, nruns), kBlock, 0, st>>>(runs, nruns);
     sort_count_kernel<<<parts.nblocks, kSortThreads, 0, st>>>(runs, parts);
     sort_scan_local_kernel<<<keys.nblocks, kScanThreads, 0, st>>>(runs, keys, scan_sums);
     sort_scan_add_kernel<<<keys.nblocks, kScanThreads, 0, st>>>(runs, keys, scan_sums);
-    sort_scatter_kernel<<<parts.nblocks, kSortThreads, 0, st>>>(runs, parts);
+    sort_scatter_kernel<<<parts.nblocks, kSortThreads, 0, st>>>(runs, parts, src_out);
     sort_finish_kernel<<<(nruns + 127) / 128, 128, 0, st>>>(runs, nruns);
     return cudaGetLastError();
 }
