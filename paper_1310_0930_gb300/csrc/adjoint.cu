@@ -18,6 +18,7 @@
 // leaves frozen beyond an open end.  Particle adjoints live in arrays indexed
 // by particle id, so the tile sort between steps does not matter.
 #include <cstdint>
+#include <utility>
 
 #include "common.cuh"
 #include "internal.h"
@@ -72,9 +73,11 @@ __device__ __forceinline__ bool b_frozen(const Run &r, int comp, int il)
 }
 
 // (i)/(iii): lamE -= h curl_b(m_B lamB); antenna: lam_a0 += <lamB, dB/da0>.
+// With mask (the (i) half, followed by (ii)): also T = newE = lamE on the
+// entries the E update writes, 0 elsewhere (part 1 of (ii)).
 template <int DIM>
 __global__ void adj_b_kernel(const Run *__restrict__ run, AdjPtrs A, int origin, double t_b, int laser_on,
-                             double *la0)
+                             double *la0, int mask)
 {
     const Run &r = *run;
     __shared__ double sh[32];
@@ -102,9 +105,22 @@ __global__ void adj_b_kernel(const Run *__restrict__ run, AdjPtrs A, int origin,
             dBy_dz = (by - mb(1, mz, il_mz)) * r.inv_d[2];
             dBx_dz = (bx - mb(0, mz, il_mz)) * r.inv_d[2];
         }
-        A.lE[0][idx] -= h * (dBz_dy - dBy_dz);
-        A.lE[1][idx] -= h * (dBx_dz - dBz_dx);
-        A.lE[2][idx] -= h * (dBy_dx - dBx_dy);
+        const float e[3] = {A.lE[0][idx] - h * (dBz_dy - dBy_dz), A.lE[1][idx] - h * (dBx_dz - dBz_dx),
+                            A.lE[2][idx] - h * (dBy_dx - dBx_dy)};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            A.lE[c][idx] = e[c];
+            if (mask) {
+                bool upd = true;
+                if (r.open_last) {
+                    const int t1 = DIM == 3 ? 1 : 2, nrm = DIM == 3 ? 2 : 1;
+                    if ((c == 0 || c == t1) && (il == 0 || il == nl - 1)) upd = false;  // Mur-set tangential
+                    if (c == nrm && il == nl - 1) upd = false;                          // zeroed normal
+                }
+                A.T[c][idx] = upd ? e[c] : 0.f;
+                A.nE[c][idx] = upd ? e[c] : 0.f;
+            }
+        }
         if (laser_on && il == r.laser_plane - 1) {
             int bcomp;
             double sgn;
@@ -121,30 +137,6 @@ __global__ void adj_b_kernel(const Run *__restrict__ run, AdjPtrs A, int origin,
     }
     double t = block_reduce(acc, sh);
     if (threadIdx.x == 0 && t != 0.0) atomicAdd(la0, t);
-}
-
-// (ii) part 1: T = lamE on entries the E update writes; newE = identity part.
-template <int DIM>
-__global__ void adj_e_mask_kernel(const Run *__restrict__ run, AdjPtrs A, int origin)
-{
-    const Run &r = *run;
-    const int n0 = r.n[0], n1 = r.n[1], nl = r.n[DIM - 1];
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < r.ncell; idx += gridDim.x * blockDim.x) {
-        const int j = (idx / n0) % n1, k = DIM == 3 ? idx / (n0 * n1) : 0;
-        int il = (DIM == 3 ? k : j) - origin;
-        il = il < 0 ? il + nl : il;
-        for (int c = 0; c < 3; ++c) {
-            bool upd = true;
-            if (r.open_last) {
-                const int t1 = DIM == 3 ? 1 : 2, nrm = DIM == 3 ? 2 : 1;
-                if ((c == 0 || c == t1) && (il == 0 || il == nl - 1)) upd = false;  // Mur-set tangential
-                if (c == nrm && il == nl - 1) upd = false;                          // zeroed normal
-            }
-            const float v = upd ? A.lE[c][idx] : 0.f;
-            A.T[c][idx] = v;
-            A.nE[c][idx] = v;
-        }
-    }
 }
 
 // (ii) part 2: the Mur transposes (one thread per transverse position).
@@ -1075,28 +1067,23 @@ unsigned blocks_for(long long n)
 
 }  // namespace
 
-cudaError_t launch_adj_fields(int dim, const Run *run, const AdjPtrs &A, int ncell, int plane, int origin, double t_n,
+cudaError_t launch_adj_fields(int dim, const Run *run, AdjPtrs &A, int ncell, int plane, int origin, double t_n,
                               double dt, int laser_on, double *la0, cudaStream_t st)
 {
     const unsigned g = blocks_for(ncell), gp = blocks_for(plane);
     if (dim == 2) {
-        adj_b_kernel<2><<<g, kBlock, 0, st>>>(run, A, origin, t_n + dt, laser_on, la0);
-        adj_e_mask_kernel<2><<<g, kBlock, 0, st>>>(run, A, origin);
+        adj_b_kernel<2><<<g, kBlock, 0, st>>>(run, A, origin, t_n + dt, laser_on, la0, 1);
         adj_mur_kernel<2><<<gp, kBlock, 0, st>>>(run, A, origin);
         adj_e_curl_kernel<2><<<g, kBlock, 0, st>>>(run, A, origin, t_n, laser_on, la0);
     } else {
-        adj_b_kernel<3><<<g, kBlock, 0, st>>>(run, A, origin, t_n + dt, laser_on, la0);
-        adj_e_mask_kernel<3><<<g, kBlock, 0, st>>>(run, A, origin);
+        adj_b_kernel<3><<<g, kBlock, 0, st>>>(run, A, origin, t_n + dt, laser_on, la0, 1);
         adj_mur_kernel<3><<<gp, kBlock, 0, st>>>(run, A, origin);
         adj_e_curl_kernel<3><<<g, kBlock, 0, st>>>(run, A, origin, t_n, laser_on, la0);
     }
-    // lamE <- newE, then (iii)
-    cudaError_t e = cudaMemcpyAsync(A.lE[0], A.nE[0], sizeof(float) * ncell, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(A.lE[1], A.nE[1], sizeof(float) * ncell, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(A.lE[2], A.nE[2], sizeof(float) * ncell, cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) return e;
-    if (dim == 2) adj_b_kernel<2><<<g, kBlock, 0, st>>>(run, A, origin, t_n, laser_on, la0);
-    else adj_b_kernel<3><<<g, kBlock, 0, st>>>(run, A, origin, t_n, laser_on, la0);
+    // lamE <- newE (the buffers trade places), then (iii)
+    for (int c = 0; c < 3; ++c) std::swap(A.lE[c], A.nE[c]);
+    if (dim == 2) adj_b_kernel<2><<<g, kBlock, 0, st>>>(run, A, origin, t_n, laser_on, la0, 0);
+    else adj_b_kernel<3><<<g, kBlock, 0, st>>>(run, A, origin, t_n, laser_on, la0, 0);
     return cudaGetLastError();
 }
 

@@ -103,7 +103,8 @@ struct TrajStep {
 struct ObjArgs {
     float z_lo, z_hi, width;
 };
-cudaError_t launch_adj_fields(int dim, const Run *run, const AdjPtrs &A, int ncell, int plane, int origin, double t_n,
+// (the lamE and newE scratch buffers of A trade places)
+cudaError_t launch_adj_fields(int dim, const Run *run, AdjPtrs &A, int ncell, int plane, int origin, double t_n,
                               double dt, int laser_on, double *la0, cudaStream_t st);
 cudaError_t launch_adj_particles(int dim, int order, const Run *run, const Run &host_run, const AdjPtrs &A,
                                  const TrajStep &ts, int origin, cudaStream_t st);
