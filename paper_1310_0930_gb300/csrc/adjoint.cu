@@ -372,6 +372,17 @@ struct GlobalRead {
         return __ldg(p[comp] + wrapi(i, n0) + n0 * (wrapi(j, n1) + n1 * (n2 > 1 ? wrapi(k, n2) : 0)));
     }
 };
+// The same with the tile geometry fixed at compile time (immediate offsets).
+template <int FV, int FS0, int FS01, int FH0, int FH1, int FH2, int JV, int JS0, int JS01, int JH0, int JH1, int JH2>
+struct SmemReadC {
+    const float *f;
+    const float *l;
+    __device__ __forceinline__ float operator()(int comp, int i, int j, int k) const
+    {
+        return comp < 6 ? f[comp * FV + (i + FH0) + FS0 * (j + FH1) + FS01 * (k + FH2)]
+                        : l[(comp - 6) * JV + (i + JH0) + JS0 * (j + JH1) + JS01 * (k + JH2)];
+    }
+};
 struct SmemRead {
     const float *f;  // 6 field components, region fvol each
     const float *l;  // 3 current-adjoint components, region jvol each
@@ -754,7 +765,9 @@ __global__ void __launch_bounds__(128, 3) adj_particles_kernel(const Run *__rest
 // takes every nsplit-th group of blockDim particles); the tile's recorded
 // fields and current adjoint (plus halos wide enough for particles within
 // `drift` cells of the tile) are staged in shared memory.
-template <int DIM, int P>
+// TX > 0: tile TX x TY (x TZ) with drift DR fixed at compile time (constant
+// shared-memory strides); TX = 0: the run's tile geometry at run time.
+template <int DIM, int P, int TX, int TY, int TZ, int DR>
 __global__ void __launch_bounds__(128, 3) adj_particles_tiled_kernel(const Run *__restrict__ run, AdjPtrs A,
                                                                      TrajStep ts, int origin, int nsplit)
 {
@@ -763,7 +776,8 @@ __global__ void __launch_bounds__(128, 3) adj_particles_tiled_kernel(const Run *
     const int t = blockIdx.x / nsplit, part = blockIdx.x - t * nsplit;
     const long long p0 = ts.tile_off[t], p1 = ts.tile_off[t + 1];
     if (p0 >= p1) return;
-    const int D = r.drift;
+    constexpr bool CT = TX > 0;
+    const int D = CT ? DR : r.drift;
     const int n0 = r.n[0], n1 = r.n[1], n2 = DIM == 3 ? r.n[2] : 1;
     int org[3] = {0, 0, 0}, T[3] = {1, 1, 1}, fh[3] = {0, 0, 0}, fs[3] = {1, 1, 1}, jh[3] = {0, 0, 0},
         js[3] = {1, 1, 1};
@@ -771,7 +785,7 @@ __global__ void __launch_bounds__(128, 3) adj_particles_tiled_kernel(const Run *
     org[1] = ((t / r.nt[0]) % r.nt[1]) << r.tlog[1];
     if (DIM == 3) org[2] = (t / (r.nt[0] * r.nt[1])) << r.tlog[2];
     for (int a = 0; a < DIM; ++a) {
-        T[a] = 1 << r.tlog[a];
+        T[a] = CT ? (a == 0 ? TX : (a == 1 ? TY : TZ)) : 1 << r.tlog[a];
         fh[a] = D + Reach<P>::GLO;
         fs[a] = T[a] + 2 * D + Reach<P>::GLO + Reach<P>::GHI;
         jh[a] = D + Reach<P>::DLO;
@@ -802,6 +816,13 @@ __global__ void __launch_bounds__(128, 3) adj_particles_tiled_kernel(const Run *
     lj_any = __syncthreads_or(lj_any);
     const SmemRead sr{F, L, fvol, fh[0], fh[1], fh[2], fs[0], fs[0] * fs[1],
                       jvol, jh[0], jh[1], jh[2], js[0], js[0] * js[1]};
+    constexpr int CTX = TX > 0 ? TX : 1, CTY = TX > 0 ? TY : 1, CTZ = DIM == 3 && TX > 0 ? TZ : 1;
+    constexpr int GL = Reach<P>::GLO, GH = Reach<P>::GHI, DL = Reach<P>::DLO, DH = Reach<P>::DHI;
+    constexpr int FS0 = CTX + 2 * DR + GL + GH, FS1 = CTY + 2 * DR + GL + GH, FS2 = DIM == 3 ? CTZ + 2 * DR + GL + GH : 1;
+    constexpr int JS0 = CTX + 2 * DR + DL + DH, JS1 = CTY + 2 * DR + DL + DH, JS2 = DIM == 3 ? CTZ + 2 * DR + DL + DH : 1;
+    const SmemReadC<FS0 * FS1 * FS2, FS0, FS0 * FS1, DR + GL, DR + GL, DIM == 3 ? DR + GL : 0, JS0 * JS1 * JS2, JS0,
+                    JS0 * JS1, DR + DL, DR + DL, DIM == 3 ? DR + DL : 0>
+        src_c{F, L};
     const GlobalRead g{{ts.E[0], ts.E[1], ts.E[2], ts.B[0], ts.B[1], ts.B[2], A.lJ[0], A.lJ[1], A.lJ[2]},
                        n0, n1, n2};
     const int zero[3] = {0, 0, 0};
@@ -833,8 +854,12 @@ __global__ void __launch_bounds__(128, 3) adj_particles_tiled_kernel(const Run *
                 rel[a] = v;
                 fast = fast && v >= -D && v < T[a] + D;
             }
-            if (fast) adj_one<DIM, P>(r, A, ts, s, cur, origin, rel, org, sr);
-            else adj_one<DIM, P>(r, A, ts, s, cur, origin, c, zero, g);
+            if (fast) {
+                if constexpr (CT) adj_one<DIM, P>(r, A, ts, s, cur, origin, rel, org, src_c);
+                else adj_one<DIM, P>(r, A, ts, s, cur, origin, rel, org, sr);
+            } else {
+                adj_one<DIM, P>(r, A, ts, s, cur, origin, c, zero, g);
+            }
         }
         cur = nxt;
     }
@@ -1104,12 +1129,14 @@ cudaError_t launch_adj_t(const Run *run, const Run &hr, const AdjPtrs &A, const 
         jv *= (size_t)(T + 2 * hr.drift + Reach<P>::DLO + Reach<P>::DHI);
     }
     const size_t smem = sizeof(float) * (6 * fv + 3 * jv);
-    auto k = adj_particles_tiled_kernel<DIM, P>;
-    static size_t attr = 0;
-    if (smem > attr) {
+    // the default 2D tile (16 x 16, drift 2) has its geometry compiled in
+    const bool ct = DIM == 2 && hr.tlog[0] == 4 && hr.tlog[1] == 4 && hr.drift == 2;
+    auto k = ct ? adj_particles_tiled_kernel<DIM, P, 16, 16, 1, 2> : adj_particles_tiled_kernel<DIM, P, 0, 0, 0, 0>;
+    static size_t attr[2] = {0, 0};
+    if (smem > attr[ct]) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr = smem;
+        attr[ct] = smem;
     }
     // enough CTAs for about four waves of three CTAs per SM
     static int sms = 0;
