@@ -318,7 +318,7 @@ def adjoint_bench(args):
     plain.close()
     sim = Simulation(w, track_ids=True, per_particle_weight=True, tuning=tuning, memory=TorchMemory())
     sim.load(parts)
-    sim.adjoint_begin(S, 100)
+    kept = sim.adjoint_begin(S, 100)
     t_fwd_ck, _ = wall(lambda: (sim.step(S), sim.sync()))
     t_bwd, res = wall(lambda: sim.adjoint_backward(*obj, n_knots=len(w.knots)))
     sim.close()
@@ -331,6 +331,7 @@ def adjoint_bench(args):
                        "particles": n},
             "tuning": tuning, "forward_s": t_fwd, "forward_with_checkpoints_s": t_fwd_ck, "reverse_s": t_bwd,
             "gradient_over_forward": (t_fwd_ck + t_bwd) / t_fwd,
+            "segments": {"checkpoints": -(-S // 100), "recorded_by_forward": kept},
             "L": res["L"], "dL_da0": res["dL_da0"], "dL_dknots_norm": float(np.linalg.norm(res["dL_dknots"]))}
     print(json.dumps(line), flush=True)
     if args.out:

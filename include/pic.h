@@ -160,7 +160,11 @@ typedef void (*pic_free_fn)(void *ptr, void *ctx);
  * different cells (fewer shared-memory bank conflicts in the deposit).
  * tma: 1 = stage the 3D field tile with the tensor-memory accelerator (the
  * entry 8x8x8 with drift 1, whose tile rows are then 16-byte aligned TMA
- * box rows), 0 = default (plain loads into the bank-padded tile). */
+ * box rows), 0 = default (plain loads into the bank-padded tile).
+ * adjoint_keep: checkpoint segments whose per-step records the forward run
+ * keeps, so that the reverse sweep recomputes only the others: 0 = default
+ * (as many as 60 % of the free device memory holds), -1 = none (every
+ * segment recomputed), n = at most n. */
 typedef struct {
     int32_t tile[3];
     int32_t sort_interval;
@@ -170,6 +174,7 @@ typedef struct {
     int32_t persistent;
     int32_t sort_sub;
     int32_t tma;
+    int32_t adjoint_keep;
 } pic_tuning;
 
 typedef struct {
@@ -293,6 +298,10 @@ typedef struct {
  * replays; the recomputation inside pic_adjoint_backward runs without graphs
  * because it records each step). */
 PIC_API int pic_adjoint_begin(pic_t *h, int32_t total_steps, int32_t checkpoint_every);
+
+/* Checkpoint segments whose records the forward run keeps (see
+ * pic_tuning.adjoint_keep), after pic_adjoint_begin; negative on error. */
+PIC_API int pic_adjoint_kept(pic_t *h);
 
 /* L of the current state (no adjoint). */
 PIC_API int pic_objective_value(pic_t *h, const pic_objective *obj, double *L);

@@ -43,7 +43,7 @@ class pic_window(ctypes.Structure):
 class pic_tuning(ctypes.Structure):
     _fields_ = [("tile", c_int32 * 3), ("sort_interval", c_int32), ("drift", c_int32), ("block", c_int32),
                 ("use_graph", c_int32), ("persistent", c_int32), ("sort_sub", c_int32),
-                ("tma", c_int32)]
+                ("tma", c_int32), ("adjoint_keep", c_int32)]
 
 
 pic_alloc_fn = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p)
@@ -89,6 +89,7 @@ SIGNATURES = {
     "pic_profile_begin": (c_int32, [_handle, c_int32]),
     "pic_profile_end": (c_int32, [_handle, _P(c_double), c_int32, _P(c_int64)]),
     "pic_adjoint_begin": (c_int32, [_handle, c_int32, c_int32]),
+    "pic_adjoint_kept": (c_int32, [_handle]),
     "pic_objective_value": (c_int32, [_handle, _P(pic_objective), _P(c_double)]),
     "pic_adjoint_backward": (c_int32, [_handle, _P(pic_objective), _P(c_double), _P(c_double), c_void_p, c_int32,
                                        c_void_p]),

@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <cstring>
 #include <algorithm>
+#include <utility>
 #include <new>
 #include <vector>
 
@@ -58,6 +59,8 @@ struct Adj {
     std::vector<Rec> rec;
     bool rec_on = false, save_ckpt = true, spent = false;
     int rec_base = 0;
+    int keep = 0;       // the last `keep` segments are recorded by the forward run, not recomputed
+    int keep_base = 0;  // first step of those segments
 };
 
 }  // namespace
@@ -79,6 +82,7 @@ struct pic_s {
     Seg seg_cells{}, seg_planes{}, seg_parts{}, seg_inject{}, seg_keys{};
     int sort_sub = 1;
     bool use_tma = false;
+    int adjoint_keep = 0;
     size_t push_smem = 0;
     int block = 256, sort_interval = 4, drift = 1, tile[3] = {16, 16, 1};
     bool use_graph = true;
@@ -600,6 +604,7 @@ int create_common(const pic_config *cfgs, int n, pic_t **out)
     h->persistent = t.persistent == 1 || (t.persistent == 0 && n > 1);
     h->sort_sub = t.sort_sub ? t.sort_sub : 1;
     h->use_tma = t.tma > 0;
+    h->adjoint_keep = t.adjoint_keep;
     if (h->sort_sub < 1 || h->sort_sub > 32 || (h->sort_sub & (h->sort_sub - 1))) {
         delete h;
         return PIC_EINVAL;
@@ -739,6 +744,11 @@ int pic_step(pic_t *h, int32_t nsteps)
     }
     if (h->adj && h->adj->spent) return PIC_ESTATE;
     for (int s = 0; s < nsteps; ++s) {
+        if (h->adj && h->adj->save_ckpt) {  // forward run: record the kept segments
+            Adj &a = *h->adj;
+            a.rec_on = a.keep > 0 && h->steps_done >= a.keep_base && h->steps_done < a.total;
+            a.rec_base = a.keep_base;
+        }
         if (h->adj && h->adj->save_ckpt && h->steps_done % h->adj->K == 0 &&
             h->steps_done / h->adj->K < h->adj->nck) {
             Ckpt &ck = h->adj->ck[h->steps_done / h->adj->K];
@@ -1066,19 +1076,48 @@ int pic_adjoint_begin(pic_t *h, int32_t total_steps, int32_t checkpoint_every)
         ck.st = (RunState *)dev_alloc(h, sizeof(RunState));
         ok = ok && ck.st;
     }
-    a->rec.resize(a->K);
-    for (Rec &rc2 : a->rec) {
+    auto record = [&]() {
+        Rec rc2{};
         rc2.pc = part(true);
         rc2.tile_off = (int32_t *)dev_alloc(h, sizeof(int32_t) * (r.ntiles + 1));
         rc2.src = (int32_t *)dev_alloc(h, sizeof(int32_t) * n);
-        ok = ok && rc2.tile_off && rc2.src;
+        bool good = rc2.tile_off && rc2.src && rc2.pc.cell && rc2.pc.id && rc2.pc.u[2];
         for (int c = 0; c < 3; ++c) {
             rc2.E[c] = F(nc);
             rc2.B[c] = F(nc);
-            ok = ok && rc2.E[c] && rc2.B[c];
+            good = good && rc2.E[c] && rc2.B[c];
         }
+        return std::make_pair(rc2, good);
+    };
+    for (int q = 0; q < a->K && ok; ++q) {
+        auto rg = record();
+        a->rec.push_back(rg.first);
+        ok = ok && rg.second;
     }
     if (!ok) return PIC_ENOMEM;
+    // Segments kept from the forward run (their records are taken while it
+    // runs, so the reverse sweep does not recompute them): as many as the
+    // request allows and 60 % of the free device memory holds.
+    const int req = h->adjoint_keep;
+    int keep = req < 0 ? 0 : (req == 0 ? a->nck : (req < a->nck ? req : a->nck));
+    if (keep > 1) {
+        size_t fr = 0, tot = 0;
+        const size_t rec_bytes = sizeof(int32_t) * (size_t)n * 3 + sizeof(float) * (size_t)n * (dim + 4) +
+                                 sizeof(float) * 6 * (size_t)nc + sizeof(int32_t) * (r.ntiles + 1) + 6 * 256;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = 0;
+        const long long fit = (long long)(0.6 * (double)fr / ((double)rec_bytes * a->K));
+        keep = (int)(keep - 1 < fit ? keep : fit + 1);
+    }
+    for (int q = a->K; q < keep * a->K; ++q) {
+        auto rg = record();
+        if (!rg.second) {  // keep what fitted (whole segments)
+            keep = q / a->K;
+            break;
+        }
+        a->rec.push_back(rg.first);
+    }
+    a->keep = keep;
+    a->keep_base = (a->nck - keep) * a->K;
     rc = upload_runs(h);
     if (rc) return rc;
     cudaError_t e = launch_adj_init(h->d_runs, a->A.wid, a->zb, n, h->stream);
@@ -1119,6 +1158,12 @@ int pic_objective_value(pic_t *h, const pic_objective *obj, double *L)
     return objective_reduce(h, obj, L);
 }
 
+int pic_adjoint_kept(pic_t *h)
+{
+    if (!h || !h->adj) return PIC_ESTATE;
+    return h->adj->keep;
+}
+
 int pic_adjoint_backward(pic_t *h, const pic_objective *obj, double *L, double *dL_da0, double *dL_dknots,
                          int32_t n_knots, double *dL_dw)
 {
@@ -1151,9 +1196,13 @@ int pic_adjoint_backward(pic_t *h, const pic_objective *obj, double *L, double *
     if (e == cudaSuccess) e = launch_objective(h->d_runs, cur.origin, o, a.red, r.capacity, 1, a.A, st);
     if (e != cudaSuccess) return PIC_ECUDA;
     const int plane = r.ncell / r.n[dim - 1];
+    a.rec_on = false;
     for (int seg = a.nck - 1; seg >= 0; --seg) {
         const int s0 = seg * a.K, s1 = s0 + a.K < a.total ? s0 + a.K : a.total;
+        const bool kept = seg >= a.nck - a.keep;  // recorded by the forward run
+        const int rb = kept ? a.keep_base : s0;   // step of record 0
         Ckpt &ck = a.ck[seg];
+        if (!kept) {
         // restore the segment's start state and recompute it, recording each step
         e = cudaMemcpyAsync(h->d_states, ck.st, sizeof(RunState), cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess) e = launch_part_copy(h->dim, h->d_runs, ck.pc, n, 1, st);
@@ -1171,13 +1220,14 @@ int pic_adjoint_backward(pic_t *h, const pic_objective *obj, double *L, double *
         rc = pic_step(h, s1 - s0);
         a.rec_on = false;
         if (rc) return rc;
+        }
         // particle adjoints follow the slot order of each record: they move to
         // the slots before a sort through the sort's record of them, and
         // through id order at segment ends
-        e = launch_adj_perm(dim, a.A, a.rec[s1 - 1 - s0].pc.id, n, 1, st);
+        e = launch_adj_perm(dim, a.A, a.rec[s1 - 1 - rb].pc.id, n, 1, st);
         if (e != cudaSuccess) return PIC_ECUDA;
         for (int s = s1 - 1; s >= s0; --s) {
-            const Rec &rc2 = a.rec[s - s0];
+            const Rec &rc2 = a.rec[s - rb];
             e = launch_adj_fields(dim, h->d_runs, a.A, (int)nc, plane, 0, rc2.time, r.dt_d, r.laser_on, a.la0, st);
             TrajStep ts{};
             ts.cell = rc2.pc.cell;

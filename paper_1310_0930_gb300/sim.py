@@ -78,6 +78,7 @@ def make_config(w: Workload, *, tuning: Optional[dict] = None, track_ids=False, 
     cfg.tuning.persistent = int(t.get("persistent", 0))
     cfg.tuning.sort_sub = int(t.get("sort_sub", 0))
     cfg.tuning.tma = int(t.get("tma", 0))
+    cfg.tuning.adjoint_keep = int(t.get("adjoint_keep", 0))
     if alloc is not None:
         cfg.alloc = alloc
         cfg.free = free
@@ -166,8 +167,13 @@ class Simulation:
         abi.pic_sync(self.h)
 
     # -- adjoint ------------------------------------------------------------
-    def adjoint_begin(self, total_steps: int, checkpoint_every: int):
+    def adjoint_begin(self, total_steps: int, checkpoint_every: int) -> int:
+        """Arm the reverse mode; returns the number of checkpoint segments the
+        forward run records instead of the reverse sweep recomputing them."""
         abi.check(abi.lib().pic_adjoint_begin(self.h, int(total_steps), int(checkpoint_every)), "pic_adjoint_begin")
+        kept = abi.lib().pic_adjoint_kept(self.h)
+        abi.check(min(kept, 0), "pic_adjoint_kept")
+        return kept
 
     def objective(self, z_lo: float, z_hi: float, width: float) -> float:
         o = abi.pic_objective(z_lo, z_hi, width)

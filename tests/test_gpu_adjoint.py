@@ -79,10 +79,13 @@ def _oracle_L(w, knots, a0, obj):
     return float(np.sum(ww * K * sig) / np.sum(ww * sig))
 
 
-def test_gradient_matches_fp64_oracle_finite_differences():
+@pytest.mark.parametrize("keep", [0, -1, 1])
+def test_gradient_matches_fp64_oracle_finite_differences(keep):
+    """keep: checkpoint segments recorded by the forward run (0 = all that fit,
+    here all three; -1 = every segment recomputed; 1 = the last one kept)."""
     w, obj = _adjoint_case()
     parts = inputs.background(w)
-    sim = Simulation(w, track_ids=True, per_particle_weight=True)
+    sim = Simulation(w, track_ids=True, per_particle_weight=True, tuning={"adjoint_keep": keep})
     sim.load(parts)
     sim.adjoint_begin(w.steps, 16)
     sim.step(w.steps)
