@@ -73,7 +73,9 @@ __global__ void charge_kernel(const Run *__restrict__ run, double *__restrict__ 
     float w[3][P + 1] = {};
 #pragma unroll
     for (int a = 0; a < DIM; ++a) Shape<P>::node(c[a], pb.off[a][i], base[a], w[a]);
-    const double qw = (double)r.q * (double)(pb.w ? pb.w[i] : r.w_const);
+    // node values in FP32 (one rounding per value), sums in FP64: FP64
+    // arithmetic runs at a small fraction of the FP32 rate on this GPU
+    const float qw = r.q * (pb.w ? pb.w[i] : r.w_const);
     const int n0 = r.n[0], n1 = r.n[1], n2 = DIM == 3 ? r.n[2] : 1;
 #pragma unroll
     for (int qz = 0; qz < (DIM == 3 ? P + 1 : 1); ++qz)
@@ -81,7 +83,7 @@ __global__ void charge_kernel(const Run *__restrict__ run, double *__restrict__ 
         for (int qy = 0; qy <= P; ++qy)
 #pragma unroll
             for (int qx = 0; qx <= P; ++qx) {
-                double v = qw * (double)w[0][qx] * (double)w[1][qy] * (DIM == 3 ? (double)w[2][qz] : 1.0);
+                const double v = (double)(qw * w[0][qx] * w[1][qy] * (DIM == 3 ? w[2][qz] : 1.f));
                 int x = wrapi(base[0] + qx, n0), y = wrapi(base[1] + qy, n1);
                 int z = DIM == 3 ? wrapi(base[2] + qz, n2) : 0;
                 atomicAdd(rho + x + n0 * (y + n1 * z), v);
@@ -170,9 +172,11 @@ __global__ void kinetic_kernel(const Run *__restrict__ run, double *out)
          i += (long long)gridDim.x * blockDim.x) {
         int c[3];
         if (!live(r, s, pb.cell[i], c[0], c[1], c[2])) continue;
-        double ux = pb.u[0][i], uy = pb.u[1][i], uz = pb.u[2][i];
-        double w = pb.w ? pb.w[i] : r.w_const;
-        k += w * (double)r.m * (sqrt(1.0 + ux * ux + uy * uy + uz * uz) - 1.0);
+        // gamma - 1 = u^2 / (gamma + 1): no cancellation in FP32; sums in FP64
+        const float ux = pb.u[0][i], uy = pb.u[1][i], uz = pb.u[2][i];
+        const float u2 = ux * ux + uy * uy + uz * uz;
+        const float gm1 = u2 / (sqrtf(1.f + u2) + 1.f);
+        k += (double)((pb.w ? pb.w[i] : r.w_const) * r.m * gm1);
         cnt += 1.0;
     }
     double tk = block_sum(k, sh);
@@ -188,15 +192,16 @@ __global__ void gauss_kernel(const Run *__restrict__ run, const double *__restri
 {
     const Run &r = *run;
     const int n0 = r.n[0], n1 = r.n[1], n2 = DIM == 3 ? r.n[2] : 1;
+    const double id0 = 1.0 / r.dd[0], id1 = 1.0 / r.dd[1], id2 = DIM == 3 ? 1.0 / r.dd[2] : 0.0;
     float mr = 0.f, m0 = 0.f;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < r.ncell; idx += gridDim.x * blockDim.x) {
         int i = idx % n0, j = (idx / n0) % n1, k = DIM == 3 ? idx / (n0 * n1) : 0;
         int mx = (i == 0 ? n0 - 1 : i - 1) + n0 * (j + n1 * k);
         int my = i + n0 * ((j == 0 ? n1 - 1 : j - 1) + n1 * k);
-        double dv = ((double)r.E[0][idx] - r.E[0][mx]) / r.d[0] + ((double)r.E[1][idx] - r.E[1][my]) / r.d[1];
+        double dv = ((double)r.E[0][idx] - r.E[0][mx]) * id0 + ((double)r.E[1][idx] - r.E[1][my]) * id1;
         if (DIM == 3) {
             int mz = i + n0 * (j + n1 * (k == 0 ? n2 - 1 : k - 1));
-            dv += ((double)r.E[2][idx] - r.E[2][mz]) / r.d[2];
+            dv += ((double)r.E[2][idx] - r.E[2][mz]) * id2;
         }
         double res = dv - (rho[idx] - r.rho0[idx]);
         mr = fmaxf(mr, (float)fabs(res));
