@@ -160,6 +160,185 @@ __global__ void yee_e_kernel(const Run *__restrict__ runs, Seg seg)
     Ez[idx] = nv[2];
 }
 
+// ---------------------------------------------------------------------------
+// The same updates with four consecutive x cells per thread: rows of n0 % 4 ==
+// 0 cells, 16-byte vector loads and stores of the own cells and of the +-y,
+// +-z neighbour rows, one scalar load for the x neighbour across the quad.
+// Launched on the cell segments with kQuadThreads threads per block (each
+// block then covers the kBlock cells of one cell-segment block).
+// ---------------------------------------------------------------------------
+constexpr int kQuadThreads = kBlock / 4;
+
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void st4(float *p, const float (&v)[4]) { *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]); }
+__device__ __forceinline__ void unpack4(const float4 q, float (&v)[4])
+{
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+}
+
+template <int DIM>
+__global__ void yee_b_quad_kernel(const Run *__restrict__ runs, Seg seg, int second)
+{
+    const int ri = seg_run(seg, blockIdx.x);
+    const Run &r = runs[ri];
+    const int idx0 = (blockIdx.x - seg.start[ri]) * kBlock + 4 * threadIdx.x;
+    if (idx0 >= r.ncell) return;
+    const RunState &s = *r.state;
+    const int n0 = r.n[0], n1 = r.n[1];
+    const int i0 = idx0 % n0, row = idx0 / n0, j = row % n1, k = DIM == 3 ? row / n1 : 0;
+    const int xn = i0 + 4 == n0 ? idx0 + 4 - n0 : idx0 + 4;  // x neighbour of the last cell
+    const int cy = i0 + n0 * ((j + 1 == n1 ? 0 : j + 1) + n1 * k);
+    const float h = 0.5f * r.dt;
+    float ex[5], ey[5], ez[5], exy[4], ezy[4], exz[4] = {0, 0, 0, 0}, eyz[4] = {0, 0, 0, 0};
+    float bx[4], by[4], bz[4];
+    {
+        float t[4];
+        unpack4(ld4(r.E[0] + idx0), t);
+        for (int e = 0; e < 4; ++e) ex[e] = t[e];
+        unpack4(ld4(r.E[1] + idx0), t);
+        for (int e = 0; e < 4; ++e) ey[e] = t[e];
+        unpack4(ld4(r.E[2] + idx0), t);
+        for (int e = 0; e < 4; ++e) ez[e] = t[e];
+    }
+    ey[4] = r.E[1][xn];
+    ez[4] = r.E[2][xn];
+    unpack4(ld4(r.E[0] + cy), exy);
+    unpack4(ld4(r.E[2] + cy), ezy);
+    if (DIM == 3) {
+        const int n2 = r.n[2];
+        const int cz = i0 + n0 * (j + n1 * (k + 1 == n2 ? 0 : k + 1));
+        unpack4(ld4(r.E[0] + cz), exz);
+        unpack4(ld4(r.E[1] + cz), eyz);
+    }
+    unpack4(ld4(r.B[0] + idx0), bx);
+    unpack4(ld4(r.B[1] + idx0), by);
+    unpack4(ld4(r.B[2] + idx0), bz);
+    const int nl = r.n[DIM - 1];
+    const int il = phys_last(r, s, DIM == 3 ? k : j);
+    const bool outside = r.open_last && il == nl - 1;  // half-integer positions beyond the end
+    const bool laser = laser_active(r, s) && il == r.laser_plane - 1;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const float dEz_dy = (ezy[e] - ez[e]) * r.inv_d[1], dEz_dx = (ez[e + 1] - ez[e]) * r.inv_d[0];
+        const float dEy_dx = (ey[e + 1] - ey[e]) * r.inv_d[0], dEx_dy = (exy[e] - ex[e]) * r.inv_d[1];
+        float dEy_dz = 0.f, dEx_dz = 0.f;
+        if (DIM == 3) {
+            dEy_dz = (eyz[e] - ey[e]) * r.inv_d[2];
+            dEx_dz = (exz[e] - ex[e]) * r.inv_d[2];
+        }
+        if (DIM == 3) {
+            if (!outside) {
+                bx[e] -= h * (dEz_dy - dEy_dz);
+                by[e] -= h * (dEx_dz - dEz_dx);
+            }
+            bz[e] -= h * (dEy_dx - dEx_dy);
+        } else {
+            if (!outside) {
+                bx[e] -= h * dEz_dy;
+                bz[e] -= h * (dEy_dx - dEx_dy);
+            }
+            by[e] -= h * (-dEz_dx);
+        }
+        if (laser) {  // B_b one plane behind saw the total E_pol: remove the incident part
+            const double t = s.time + (second ? r.dt_d : 0.0);
+            const double f = laser_field(r, laser_r2(r, i0 + e, j), t);
+            const float add = (float)((DIM == 3 ? (r.laser_pol == 0 ? 1.0 : -1.0) : -1.0) * (double)h *
+                                      (double)r.inv_d[DIM - 1] * f);
+            if (DIM == 3) {
+                if (r.laser_pol == 0) by[e] += add;
+                else bx[e] += add;
+            } else {
+                bz[e] += add;
+            }
+        }
+    }
+    st4(r.B[0] + idx0, bx);
+    st4(r.B[1] + idx0, by);
+    st4(r.B[2] + idx0, bz);
+}
+
+template <int DIM>
+__global__ void yee_e_quad_kernel(const Run *__restrict__ runs, Seg seg)
+{
+    const int ri = seg_run(seg, blockIdx.x);
+    const Run &r = runs[ri];
+    const int idx0 = (blockIdx.x - seg.start[ri]) * kBlock + 4 * threadIdx.x;
+    if (idx0 >= r.ncell) return;
+    const RunState &s = *r.state;
+    const int n0 = r.n[0], n1 = r.n[1];
+    const int i0 = idx0 % n0, row = idx0 / n0, j = row % n1, k = DIM == 3 ? row / n1 : 0;
+    const int xm = i0 == 0 ? idx0 + n0 - 1 : idx0 - 1;  // x neighbour of the first cell
+    const int my = i0 + n0 * ((j == 0 ? n1 - 1 : j - 1) + n1 * k);
+    const float dt = r.dt;
+    // b?[0] is the -x neighbour of cell 0, b?[1 + e] cell e
+    float bx[4], by[5], bz[5], bxy[4], bzy[4], bxz[4] = {0, 0, 0, 0}, byz[4] = {0, 0, 0, 0};
+    float ex[4], ey[4], ez[4], jx[4], jy[4], jz[4];
+    {
+        float t[4];
+        unpack4(ld4(r.B[0] + idx0), bx);
+        unpack4(ld4(r.B[1] + idx0), t);
+        for (int e = 0; e < 4; ++e) by[e + 1] = t[e];
+        unpack4(ld4(r.B[2] + idx0), t);
+        for (int e = 0; e < 4; ++e) bz[e + 1] = t[e];
+    }
+    by[0] = r.B[1][xm];
+    bz[0] = r.B[2][xm];
+    unpack4(ld4(r.B[0] + my), bxy);
+    unpack4(ld4(r.B[2] + my), bzy);
+    if (DIM == 3) {
+        const int n2 = r.n[2];
+        const int mz = i0 + n0 * (j + n1 * (k == 0 ? n2 - 1 : k - 1));
+        unpack4(ld4(r.B[0] + mz), bxz);
+        unpack4(ld4(r.B[1] + mz), byz);
+    }
+    unpack4(ld4(r.E[0] + idx0), ex);
+    unpack4(ld4(r.E[1] + idx0), ey);
+    unpack4(ld4(r.E[2] + idx0), ez);
+    unpack4(ld4(r.J[0] + idx0), jx);
+    unpack4(ld4(r.J[1] + idx0), jy);
+    unpack4(ld4(r.J[2] + idx0), jz);
+    const int nl = r.n[DIM - 1];
+    const int il = phys_last(r, s, DIM == 3 ? k : j);
+    const bool tang = r.open_last && (il == 0 || il == nl - 1);  // tangential: set by the Mur update
+    const bool norm0 = r.open_last && il == nl - 1;
+    const bool laser = laser_active(r, s) && il == r.laser_plane;
+    float nx[4], ny[4], nz[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const float dBz_dy = (bz[e + 1] - bzy[e]) * r.inv_d[1], dBz_dx = (bz[e + 1] - bz[e]) * r.inv_d[0];
+        const float dBy_dx = (by[e + 1] - by[e]) * r.inv_d[0], dBx_dy = (bx[e] - bxy[e]) * r.inv_d[1];
+        float dBy_dz = 0.f, dBx_dz = 0.f;
+        if (DIM == 3) {
+            dBy_dz = (by[e + 1] - byz[e]) * r.inv_d[2];
+            dBx_dz = (bx[e] - bxz[e]) * r.inv_d[2];
+        }
+        float nv[3];
+        nv[0] = ex[e] + dt * (dBz_dy - dBy_dz - jx[e]);
+        nv[1] = ey[e] + dt * (dBx_dz - dBz_dx - jy[e]);
+        nv[2] = ez[e] + dt * (dBy_dx - dBx_dy - jz[e]);
+        if (tang) {
+            nv[0] = ex[e];
+            if (DIM == 3) nv[1] = ey[e];
+            else nv[2] = ez[e];
+        }
+        if (norm0) nv[DIM == 3 ? 2 : 1] = 0.f;
+        if (laser) {  // E_pol on the plane saw the scattered B_b one plane behind: add the incident B
+            const double th = s.time + 0.5 * r.dt_d;
+            const double f = laser_field(r, laser_r2(r, i0 + e, j), th + 0.5 * r.d_last_d);
+            nv[r.laser_pol] += (float)((double)dt * (double)r.inv_d[DIM - 1] * f);
+        }
+        nx[e] = nv[0];
+        ny[e] = nv[1];
+        nz[e] = nv[2];
+    }
+    st4(r.E[0] + idx0, nx);
+    st4(r.E[1] + idx0, ny);
+    st4(r.E[2] + idx0, nz);
+}
+
 __global__ void zero_j_kernel(const Run *__restrict__ runs, Seg seg)
 {
     const int ri = seg_run(seg, blockIdx.x);
@@ -348,17 +527,27 @@ cudaError_t launch_zero_j(const Run *runs, Seg cells, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_yee_b(int dim, const Run *runs, Seg cells, int second_half, cudaStream_t st)
+cudaError_t launch_yee_b(int dim, const Run *runs, Seg cells, int second_half, bool quad, cudaStream_t st)
 {
-    if (dim == 3) yee_b_kernel<3><<<cells.nblocks, kBlock, 0, st>>>(runs, cells, second_half);
-    else yee_b_kernel<2><<<cells.nblocks, kBlock, 0, st>>>(runs, cells, second_half);
+    if (quad) {
+        if (dim == 3) yee_b_quad_kernel<3><<<cells.nblocks, kQuadThreads, 0, st>>>(runs, cells, second_half);
+        else yee_b_quad_kernel<2><<<cells.nblocks, kQuadThreads, 0, st>>>(runs, cells, second_half);
+    } else {
+        if (dim == 3) yee_b_kernel<3><<<cells.nblocks, kBlock, 0, st>>>(runs, cells, second_half);
+        else yee_b_kernel<2><<<cells.nblocks, kBlock, 0, st>>>(runs, cells, second_half);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_yee_e(int dim, const Run *runs, Seg cells, cudaStream_t st)
+cudaError_t launch_yee_e(int dim, const Run *runs, Seg cells, bool quad, cudaStream_t st)
 {
-    if (dim == 3) yee_e_kernel<3><<<cells.nblocks, kBlock, 0, st>>>(runs, cells);
-    else yee_e_kernel<2><<<cells.nblocks, kBlock, 0, st>>>(runs, cells);
+    if (quad) {
+        if (dim == 3) yee_e_quad_kernel<3><<<cells.nblocks, kQuadThreads, 0, st>>>(runs, cells);
+        else yee_e_quad_kernel<2><<<cells.nblocks, kQuadThreads, 0, st>>>(runs, cells);
+    } else {
+        if (dim == 3) yee_e_kernel<3><<<cells.nblocks, kBlock, 0, st>>>(runs, cells);
+        else yee_e_kernel<2><<<cells.nblocks, kBlock, 0, st>>>(runs, cells);
+    }
     return cudaGetLastError();
 }
 

@@ -24,7 +24,7 @@ constexpr int kBlock = 256;
 // Tile sort (sort.cu): one CTA of kSortThreads threads ranks a chunk of
 // kSortChunk particle slots in a shared-memory key table of kSortHash
 // entries; the particle segments of the sort are in units of chunks.
-constexpr int kSortThreads = 256, kSortItems = 8, kSortGroup = 4, kSortChunk = kSortThreads * kSortItems;
+constexpr int kSortThreads = 256, kSortItems = 8, kSortGroup = 2, kSortChunk = kSortThreads * kSortItems;
 constexpr int kSortHashLog = 9, kSortHash = 1 << kSortHashLog, kSortProbe = 32;
 // The exclusive scan of the (tile, sub-bucket) counters runs in blocks of
 // kScanChunk keys (kScanThreads threads x kScanItems consecutive keys).
@@ -45,8 +45,10 @@ cudaError_t launch_push(int dim, int order, const int *tile, int drift, bool tma
 
 // fields.cu
 cudaError_t launch_zero_j(const Run *runs, Seg cells, cudaStream_t st);
-cudaError_t launch_yee_b(int dim, const Run *runs, Seg cells, int second_half, cudaStream_t st);
-cudaError_t launch_yee_e(int dim, const Run *runs, Seg cells, cudaStream_t st);
+// quad: four x cells per thread with 16-byte accesses (every run's n0 a
+// multiple of 4 and its field arrays 16-byte aligned)
+cudaError_t launch_yee_b(int dim, const Run *runs, Seg cells, int second_half, bool quad, cudaStream_t st);
+cudaError_t launch_yee_e(int dim, const Run *runs, Seg cells, bool quad, cudaStream_t st);
 cudaError_t launch_mur_save(const Run *runs, Seg planes, cudaStream_t st);
 cudaError_t launch_mur_apply(const Run *runs, Seg planes, cudaStream_t st);
 cudaError_t launch_end_step(const Run *runs, int nruns, cudaStream_t st);

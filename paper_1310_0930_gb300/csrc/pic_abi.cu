@@ -83,6 +83,7 @@ struct pic_s {
     int sort_sub = 1;
     bool use_tma = false;
     int adjoint_keep = 0;
+    bool yee_quad = true;  // every run: rows of a multiple of 4 cells, 16-byte aligned field arrays
     size_t push_smem = 0;
     int block = 256, sort_interval = 4, drift = 1, tile[3] = {16, 16, 1};
     bool use_graph = true;
@@ -364,13 +365,13 @@ int enqueue_step(pic_s *h, bool sort)
         e = launch_push(h->dim, h->order, h->tile, h->drift, h->use_tma, R, h->d_items, h->n_items, h->block, kTail,
                         h->persistent ? h->d_queue : nullptr, h->num_sms, st);
     mark(PIC_PH_YEE_B1);
-    if (e == cudaSuccess) e = launch_yee_b(h->dim, R, h->seg_cells, 0, st);
+    if (e == cudaSuccess) e = launch_yee_b(h->dim, R, h->seg_cells, 0, h->yee_quad, st);
     mark(PIC_PH_YEE_E);
     if (e == cudaSuccess && h->any_open) e = launch_mur_save(R, h->seg_planes, st);
-    if (e == cudaSuccess) e = launch_yee_e(h->dim, R, h->seg_cells, st);
+    if (e == cudaSuccess) e = launch_yee_e(h->dim, R, h->seg_cells, h->yee_quad, st);
     if (e == cudaSuccess && h->any_open) e = launch_mur_apply(R, h->seg_planes, st);
     mark(PIC_PH_YEE_B2);
-    if (e == cudaSuccess) e = launch_yee_b(h->dim, R, h->seg_cells, 1, st);
+    if (e == cudaSuccess) e = launch_yee_b(h->dim, R, h->seg_cells, 1, h->yee_quad, st);
     mark(PIC_PH_WINDOW);
     if (e == cudaSuccess) e = launch_end_step(R, h->nruns, st);
     if (e == cudaSuccess && h->any_window) e = launch_window(R, h->seg_planes, h->seg_inject, st);
@@ -657,6 +658,11 @@ int create_common(const pic_config *cfgs, int n, pic_t **out)
         h->any_open = h->any_open || hr.r.open_last;
         h->any_window = h->any_window || hr.r.window_on;
         h->max_tiles = hr.r.ntiles > h->max_tiles ? hr.r.ntiles : h->max_tiles;
+        bool aligned = hr.r.n[0] % 4 == 0;
+        for (int c = 0; c < 3; ++c)
+            aligned = aligned && (uintptr_t)hr.r.E[c] % 16 == 0 && (uintptr_t)hr.r.B[c] % 16 == 0 &&
+                      (uintptr_t)hr.r.J[c] % 16 == 0;
+        h->yee_quad = h->yee_quad && aligned;
     }
     int rc = upload_runs(h);
     if (!rc) rc = set_seg(h, 0, h->seg_cells, cells);

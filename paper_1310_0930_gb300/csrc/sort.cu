@@ -251,8 +251,8 @@ __global__ void __launch_bounds__(kScanThreads) sort_scan_add_kernel(const Run *
 // atomic on the tile cursor, then copies every live particle to
 // range start + rank.  Warps whose keys agree write 32 consecutive slots.
 // Cells, table slots and ranks stay in registers; the copy loads a group of
-// kSortGroup particles per thread before storing them.
-__global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(const Run *__restrict__ runs, Seg seg,
+// 2 particles per thread before storing them.
+__global__ void __launch_bounds__(kSortThreads, 3) sort_scatter_kernel(const Run *__restrict__ runs, Seg seg,
                                                                     int32_t *__restrict__ src_out)
 {
     __shared__ KeyTable t;
