@@ -327,24 +327,29 @@ __device__ __forceinline__ void esirkepov(const Axis<P> *ax, float qwvz, const E
 }
 
 // One particle's weights, gather, push and move.  cr: cell coordinates in
-// the accessor's frame.  Returns false for a non-finite or over-long move.
+// the accessor's frame.  live = false (uniform over the CTA) says that every
+// field value the gather could read is +0, so the interpolated E and B are +0
+// exactly and the weights and the gather are skipped.  Returns false for a
+// non-finite or over-long move.
 template <int DIM, int P, class GatherFn>
 __device__ __forceinline__ bool push_move(const Run &r, const GatherFn &gather, const int *cr, const float *d,
-                                          float *u, float *d1, int *k, float &ig)
+                                          float *u, float *d1, int *k, float &ig, bool live = true)
 {
-    int bn[3] = {0, 0, 0}, bh[3] = {0, 0, 0};
-    float wn[3][P + 1], wh[3][P + 1];
+    float e[3] = {0.f, 0.f, 0.f}, b[3] = {0.f, 0.f, 0.f};
+    if (live) {
+        int bn[3] = {0, 0, 0}, bh[3] = {0, 0, 0};
+        float wn[3][P + 1], wh[3][P + 1];
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-        Shape<P>::node(cr[a], d[a], bn[a], wn[a]);
-        Shape<P>::half(cr[a], d[a], bh[a], wh[a]);
-    }
-    if (DIM == 2) {
+        for (int a = 0; a < DIM; ++a) {
+            Shape<P>::node(cr[a], d[a], bn[a], wn[a]);
+            Shape<P>::half(cr[a], d[a], bh[a], wh[a]);
+        }
+        if (DIM == 2) {
 #pragma unroll
-        for (int q = 0; q <= P; ++q) wn[2][q] = wh[2][q] = 0.f;
+            for (int q = 0; q <= P; ++q) wn[2][q] = wh[2][q] = 0.f;
+        }
+        gather(bn, bh, wn, wh, e, b);
     }
-    float e[3], b[3];
-    gather(bn, bh, wn, wh, e, b);
     boris(r.qm_half_dt, e, b, u);
     ig = rsqrtf(1.f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     bool ok = true;
@@ -617,6 +622,7 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
     // TMA staging: 3D tiles whose field box lies inside the stored grid
     // (boxes that wrap around a periodic or ring boundary are loaded below)
     bool tma = false;
+    bool live = true;  // some staged field value is not +0
     if (G::TL && tile_item && r.tmap) {
         const int x0 = org[0] - G::FHX, y0 = org[1] - G::FHY, z0 = org[2] - G::FHZ;
         tma = x0 >= 0 && x0 + G::FX <= n0 && y0 >= 0 && y0 + G::FY <= n1 && z0 >= 0 && z0 + G::FZ <= n2;
@@ -634,6 +640,7 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
         }
     }
     if (tile_item) {
+        unsigned nzbits = tma ? 1u : 0u;  // (TMA-staged tiles are taken as live)
         for (int l = tma ? G::FVOL : threadIdx.x; l < G::FVOL; l += blockDim.x) {
             const int lz = l / G::FPL, lxy = l - lz * G::FPL, ly = lxy / G::FX, lx = lxy - ly * G::FX;
             if (ly >= G::FY) continue;  // plane padding
@@ -648,7 +655,10 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
                 v[3 + c] = __ldg(r.B[c] + g);
             }
 #pragma unroll
-            for (int c = 0; c < 6; ++c) Fs[c * G::FVOL + l] = v[c];
+            for (int c = 0; c < 6; ++c) {
+                Fs[c * G::FVOL + l] = v[c];
+                nzbits |= __float_as_uint(v[c]);
+            }
         }
         for (int q = threadIdx.x; q < 6 * G::JVOL; q += blockDim.x) Jhi[q] = 0;
         // scale bounds: sum and maximum of |q w| over the tile's particles
@@ -689,7 +699,7 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
                 for (int it = 0; it < kTmaSpin && !done; ++it) done = mbar_try_wait(&tma_bar, 0);
             }
         }
-        __syncthreads();
+        live = __syncthreads_or(nzbits != 0u) != 0;
     }
 
     const GlobalFields gf{{r.E[0], r.E[1], r.E[2], r.B[0], r.B[1], r.B[2]}, n0, n1, n2};
@@ -734,7 +744,7 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
                 bool ok;
                 if (fast) {
                     float d1[3] = {0.f, 0.f, 0.f}, ig;
-                    ok = push_move<DIM, P>(r, sgather, rel, d, u, d1, k, ig);
+                    ok = push_move<DIM, P>(r, sgather, rel, d, u, d1, k, ig, live);
                     if (ok) {
                         // A particle that did not move (and, in 2D, has v_z = 0)
                         // deposits exactly zero; a warp of such particles skips

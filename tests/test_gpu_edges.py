@@ -1,8 +1,10 @@
 """Edge cases of the CUDA path: particles on cell faces and just below the
 next face with relativistic momenta in smooth random fields (against the
-oracle, particle by particle), a run whose tiles are mostly empty (a single
-particle per tile at most), and a load beyond the configured capacity
-(refused with PIC_EOVERFLOW, nothing written)."""
+oracle, particle by particle), fields confined to part of the grid (tiles
+whose staged fields are all zero take the zero-force path), cold plasma in
+zero fields (bit-identical after stepping), a run whose tiles are mostly
+empty (a single particle per tile at most), and a load beyond the configured
+capacity (refused with PIC_EOVERFLOW, nothing written)."""
 import numpy as np
 import pytest
 
@@ -85,4 +87,53 @@ def test_load_beyond_capacity_is_refused():
     sim.step(w.steps)
     d = sim.diagnostics()
     assert d["status"] == 0 and d["n_particles"] == half
+    sim.close()
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_fields_in_part_of_the_grid_3d(order):
+    """Smooth fields in the lower half of z only, exact zeros elsewhere; moving
+    particles everywhere.  Tiles whose staged fields are all zero take the
+    zero-force path (no gather), the others the full gather; both against the
+    oracle, particle by particle, over 3 steps."""
+    w = inputs.thermal_3d(n=(16, 16, 48), steps=3, order=order)
+    rng = np.random.default_rng(11)
+    n = 6000
+    cell = np.stack([rng.integers(0, m, n) for m in w.n]).astype(np.int32)
+    off = rng.uniform(0, 1, size=(3, n)).astype(np.float32)
+    u = rng.normal(0, 0.2, size=(3, n)).astype(np.float32)
+    parts = inputs.Particles(cell, off, u, np.full(n, 0.05, np.float32))
+    fields = smooth_fields(w, amp=0.2)
+    for name in FIELD_NAMES:  # (arrays are [z][y][x])
+        fields[name][w.n[2] // 2:] = 0.0
+    gpu, orc = pair(w, parts, fields=fields, per_particle_weight=True)
+    gpu.step(w.steps)
+    orc.step(w.steps)
+    _compare_particles(gpu, orc, n, w.n)
+    for name in FIELD_NAMES:
+        assert rel_l2(gpu.field(name), orc.field(name)) < 1e-5, name
+    gpu.close()
+
+
+def test_cold_plasma_in_zero_fields_is_unchanged():
+    """Particles at rest with E = B = 0 everywhere: after 5 steps every cell,
+    offset and momentum is bit-identical to the load and J and the fields are
+    exactly zero (the zero-force path must not change anything)."""
+    w = inputs.thermal_3d(n=(16, 16, 32), steps=5, order=2)
+    rng = np.random.default_rng(12)
+    n = 5000
+    cell = np.stack([rng.integers(0, m, n) for m in w.n]).astype(np.int32)
+    off = rng.uniform(0, 1, size=(3, n)).astype(np.float32)
+    u = np.zeros((3, n), np.float32)
+    parts = inputs.Particles(cell, off, u, np.full(n, 0.05, np.float32))
+    sim = Simulation(w, track_ids=True, per_particle_weight=True)
+    sim.load(parts)
+    sim.step(w.steps)
+    g = sim.particles()
+    order = np.argsort(g["id"])
+    assert np.array_equal(g["cell"][:, order], cell)
+    assert np.array_equal(g["off"][:, order], off)
+    assert np.array_equal(g["u"][:, order], u)
+    for name in FIELD_NAMES + ["Jx", "Jy", "Jz"]:
+        assert not np.any(sim.field(name)), name
     sim.close()
