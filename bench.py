@@ -85,15 +85,14 @@ def particle_chunks(w):
     return chunks
 
 
-# Per-particle figures of the push kernel from one ncu capture of a smaller
-# case of the same workload (summaries in profiles/, named below): DRAM
-# bytes (dram__bytes_read.sum + dram__bytes_write.sum) and warp instructions
-# (smsp__inst_executed.sum) per particle of one launch.  They are scaled to a
-# full launch by its particle count, and hold for the default tuning of the
-# kernel they were taken with.
+# Per-particle figures of the push kernel from one single-pass ncu capture of
+# one launch of the bench workload at its full size (summaries in profiles/,
+# named below): DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) and
+# warp instructions (smsp__inst_executed.sum) per particle of that launch.
+# They are scaled to the timed launches by their particle count, and hold for
+# the default tuning of the kernel they were taken with.
 PUSH_PROFILE = {
-    ("lwfa_3d", 2): (53.3, 31.4, "push_kernel_lwfa3d_quadratic_64x64x256.md"),
-    ("warm_3d", 2): (59.7, 93.4, "push_kernel_warm3d_quadratic_128x128x128.md"),
+    ("lwfa_3d", 2): (61.08, 16.69, "push_kernel_lwfa3d_quadratic_256x256x1024.md"),
 }
 
 
@@ -502,7 +501,7 @@ def main():
                        timed="device-resident state, phase events recorded on the library stream"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "kernel": "push_kernel<%d,%d>" % (w.dim, w.order),
-                     "traffic_source": ("ncu capture scaled by particle count, profiles/" + prof[2]) if prof else None,
+                     "traffic_source": ("ncu capture of one launch, per particle, profiles/" + prof[2]) if prof else None,
                      "issue": issue,
                      "bytes_per_launch": push_bytes, "avg_launch_ms": push_ms,
                      "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json)" if peaks else "fallback"},

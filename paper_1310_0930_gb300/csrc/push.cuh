@@ -567,6 +567,8 @@ __device__ __noinline__ SlowOut advance_global(const Run &r, const GlobalFields 
     return o;
 }
 
+constexpr int kStage = 4;  // field-tile rows loaded at once per thread
+
 // One work item: a tile of one run (staged fast path) or a block of that
 // run's unsorted tail (slow path).  Called uniformly by the whole CTA.
 template <int DIM, int P, int TX, int TY, int TZ, int D, bool T>
@@ -641,24 +643,39 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
     }
     if (tile_item) {
         unsigned nzbits = tma ? 1u : 0u;  // (TMA-staged tiles are taken as live)
-        for (int l = tma ? G::FVOL : threadIdx.x; l < G::FVOL; l += blockDim.x) {
-            const int lz = l / G::FPL, lxy = l - lz * G::FPL, ly = lxy / G::FX, lx = lxy - ly * G::FX;
-            if (ly >= G::FY) continue;  // plane padding
-            const int gx = modi(org[0] - G::FHX + lx, n0);
-            const int gy = modi(org[1] - G::FHY + ly, n1);
-            const int gz = DIM == 3 ? modi(org[2] - G::FHZ + lz, n2) : 0;
-            const int g = gx + n0 * (gy + n1 * gz);
-            float v[6];
+        // (kStage rows of loads in flight per thread before their stores)
+        for (int l0 = tma ? G::FVOL : threadIdx.x; l0 < G::FVOL; l0 += kStage * blockDim.x) {
+            float v[kStage][6];
+            int ls[kStage];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                v[c] = __ldg(r.E[c] + g);
-                v[3 + c] = __ldg(r.B[c] + g);
+            for (int s = 0; s < kStage; ++s) {
+                const int l = l0 + s * blockDim.x;
+                ls[s] = -1;
+                if (l < G::FVOL) {
+                    const int lz = l / G::FPL, lxy = l - lz * G::FPL, ly = lxy / G::FX, lx = lxy - ly * G::FX;
+                    if (ly < G::FY) {  // (else plane padding)
+                        const int gx = modi(org[0] - G::FHX + lx, n0);
+                        const int gy = modi(org[1] - G::FHY + ly, n1);
+                        const int gz = DIM == 3 ? modi(org[2] - G::FHZ + lz, n2) : 0;
+                        const int g = gx + n0 * (gy + n1 * gz);
+                        ls[s] = l;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            v[s][c] = __ldg(r.E[c] + g);
+                            v[s][3 + c] = __ldg(r.B[c] + g);
+                        }
+                    }
+                }
             }
 #pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                Fs[c * G::FVOL + l] = v[c];
-                nzbits |= __float_as_uint(v[c]);
-            }
+            for (int s = 0; s < kStage; ++s)
+                if (ls[s] >= 0) {
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) {
+                        Fs[c * G::FVOL + ls[s]] = v[s][c];
+                        nzbits |= __float_as_uint(v[s][c]);
+                    }
+                }
         }
         for (int q = threadIdx.x; q < 6 * G::JVOL; q += blockDim.x) Jhi[q] = 0;
         // scale bounds: sum and maximum of |q w| over the tile's particles
