@@ -567,7 +567,7 @@ __device__ __noinline__ SlowOut advance_global(const Run &r, const GlobalFields 
     return o;
 }
 
-constexpr int kStage = 4;  // field-tile rows loaded at once per thread
+constexpr int kStage = 6;  // field-tile rows loaded at once per thread
 
 // One work item: a tile of one run (staged fast path) or a block of that
 // run's unsorted tail (slow path).  Called uniformly by the whole CTA.
