@@ -92,7 +92,7 @@ def particle_chunks(w):
 # They are scaled to the timed launches by their particle count, and hold for
 # the default tuning of the kernel they were taken with.
 PUSH_PROFILE = {
-    ("lwfa_3d", 2): (61.08, 16.69, "push_kernel_lwfa3d_quadratic_256x256x1024.md"),
+    ("lwfa_3d", 2): (61.09, 16.65, "push_kernel_lwfa3d_quadratic_256x256x1024.md"),
 }
 
 
@@ -496,6 +496,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(workload_config(w, n0), particles_timed=int(n_avg),
+                       sort_policy="fixed" if (tuning or {}).get("sort_policy") == 1 else "adaptive",
+                       sorts_timed=int(d1["sorts"] - d0["sorts"]),
                        l2="inputs larger than L2 (%.1f GB particle state)" % (n_avg * sp / 1e9),
                        parallelism="replicas" if world > 1 else "single GPU",
                        timed="device-resident state, phase events recorded on the library stream"),

@@ -143,7 +143,16 @@ typedef void *(*pic_alloc_fn)(size_t bytes, void *ctx);
 typedef void (*pic_free_fn)(void *ptr, void *ctx);
 
 /* Tuning: tile[a] cells per tile per axis (powers of two, 0 = default);
- * sort_interval steps between tile sorts (0 = default); drift: cells a
+ * sort_interval: steps between tile sorts under the fixed policy (0 =
+ * default, 4), the longest interval under the adaptive one (0 = default,
+ * 16); sort_policy: 0 = adaptive (default): each step the device sorts a
+ * run when sort_interval steps have passed since its last sort or when its
+ * push has sent, summed over the steps since that sort, at least 1/65536 of
+ * its particles down the slow path (particles outside their tile's staged
+ * region, each of which stalls its warp); 1 = fixed: every sort_interval
+ * steps.  The adjoint form always
+ * uses the fixed schedule (a recomputed segment repeats the forward run's
+ * sorts).  drift: cells a
  * particle may stray outside its tile between sorts and still use the
  * staged fast path (-1 = default); block: threads per tile CTA, 128, 256, 384
  * or 512 (0 = default);
@@ -175,6 +184,7 @@ typedef struct {
     int32_t sort_sub;
     int32_t tma;
     int32_t adjoint_keep;
+    int32_t sort_policy;
 } pic_tuning;
 
 typedef struct {
@@ -206,7 +216,7 @@ typedef struct {
     double imbalance;      /* max / mean particles per occupied tile (Sec. 3) */
     int64_t slow_path;     /* particles outside their tile's staged region, last step */
     int32_t status;        /* latched device status (PIC_OK or a PIC_E* code) */
-    int32_t reserved;
+    int32_t sorts;         /* tile sorts so far */
 } pic_diag;
 
 typedef struct pic_s pic_t;

@@ -43,7 +43,7 @@ class pic_window(ctypes.Structure):
 class pic_tuning(ctypes.Structure):
     _fields_ = [("tile", c_int32 * 3), ("sort_interval", c_int32), ("drift", c_int32), ("block", c_int32),
                 ("use_graph", c_int32), ("persistent", c_int32), ("sort_sub", c_int32),
-                ("tma", c_int32), ("adjoint_keep", c_int32)]
+                ("tma", c_int32), ("adjoint_keep", c_int32), ("sort_policy", c_int32)]
 
 
 pic_alloc_fn = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p)
@@ -65,7 +65,7 @@ class pic_objective(ctypes.Structure):
 class pic_diag(ctypes.Structure):
     _fields_ = [("step", c_int64), ("time", c_double), ("shifts", c_int64), ("W_E", c_double), ("W_B", c_double),
                 ("W_kin", c_double), ("gauss_resid", c_double), ("n_particles", c_int64),
-                ("imbalance", c_double), ("slow_path", c_int64), ("status", c_int32), ("reserved", c_int32)]
+                ("imbalance", c_double), ("slow_path", c_int64), ("status", c_int32), ("sorts", c_int32)]
 
 
 # name -> (restype, argtypes); the order and types follow include/pic.h

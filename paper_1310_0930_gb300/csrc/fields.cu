@@ -413,6 +413,8 @@ __global__ void end_step_kernel(const Run *__restrict__ runs, int nruns)
     s.time += r.dt_d;
     s.step += 1;
     s.slow_last = s.slow;
+    s.slow_acc += s.slow;
+    s.since_sort += 1;
     s.slow = 0;
     s.shift_pending = 0;
     if (r.window_on && s.time >= r.window_t0) {

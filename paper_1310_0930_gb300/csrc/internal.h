@@ -26,6 +26,9 @@ constexpr int kBlock = 256;
 // entries; the particle segments of the sort are in units of chunks.
 constexpr int kSortThreads = 256, kSortItems = 8, kSortGroup = 2, kSortChunk = kSortThreads * kSortItems;
 constexpr int kSortHashLog = 9, kSortHash = 1 << kSortHashLog, kSortProbe = 32;
+// adaptive sort: sort once the slow path has taken n_total / kSortSlowDiv
+// particle-steps since the last sort
+constexpr unsigned long long kSortSlowDiv = 65536;
 // The exclusive scan of the (tile, sub-bucket) counters runs in blocks of
 // kScanChunk keys (kScanThreads threads x kScanItems consecutive keys).
 constexpr int kScanThreads = 256, kScanItems = 16, kScanChunk = kScanThreads * kScanItems;
@@ -59,8 +62,10 @@ cudaError_t launch_window(const Run *runs, Seg planes, Seg inject, cudaStream_t 
 // per key block.
 // src_out (may be null): for each sorted slot, the slot the particle had
 // before the sort (single-run handles).
+// force: every run sorts; adaptive: a run also sorts when max_interval
+// steps have passed or its slow path has grown (sort_decide_kernel).
 cudaError_t launch_sort(const Run *runs, int nruns, Seg parts, Seg keys, int *scan_sums, int32_t *src_out,
-                        cudaStream_t st);
+                        int force, int max_interval, int adaptive, cudaStream_t st);
 
 // diag.cu
 cudaError_t launch_pack(const Run *run, long long base, long long n, int dim, const int32_t *cell,

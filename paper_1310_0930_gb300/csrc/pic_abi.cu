@@ -22,7 +22,8 @@ using namespace pic;
 
 namespace {
 
-constexpr int kTail = 256;  // particles per tail work item
+constexpr int kTail = 256;              // particles per tail work item (at least)
+constexpr int kSortMaxAdaptive = 16;    // default longest interval between sorts, adaptive policy
 
 struct HostRun {
     pic_config cfg;
@@ -82,6 +83,7 @@ struct pic_s {
     Seg seg_cells{}, seg_planes{}, seg_parts{}, seg_inject{}, seg_keys{};
     int sort_sub = 1;
     bool use_tma = false;
+    bool sort_adaptive = true;  // the device decides when to sort (sort_decide_kernel)
     int adjoint_keep = 0;
     bool yee_quad = true;  // every run: rows of a multiple of 4 cells, 16-byte aligned field arrays
     size_t push_smem = 0;
@@ -95,7 +97,8 @@ struct pic_s {
     int *d_queue = nullptr;  // work-queue counter of the persistent push kernel
     bool persistent = false;
     int num_sms = 1;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int tail_block = 256;  // particles per tail work item (build_items)
+    cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};  // [sort forced + 2 * adaptive]
     // phase profiling: events[step][PIC_NUM_PHASES + 1]
     std::vector<cudaEvent_t> prof_events;
     int prof_max = 0, prof_steps = 0;
@@ -293,11 +296,22 @@ int read_state(pic_s *h, int run, RunState *out)
 int build_items(pic_s *h)
 {
     std::vector<Item> items;
+    // tail items of kTail particles, or larger ones when more than four per
+    // SM would be needed (an item past the current tail returns at once, but
+    // each still costs a CTA launch)
+    long long tail_items = 0;
+    for (int i = 0; i < h->nruns; ++i) {
+        const HostRun &hr = h->runs[i];
+        const long long max_tail = (long long)(h->sort_interval + 1) * hr.inject_per_shift;
+        tail_items += (max_tail + kTail - 1) / kTail;
+    }
+    const long long cap = 4ll * (h->num_sms > 0 ? h->num_sms : 1);
+    h->tail_block = tail_items > cap ? (int)(kTail * ((tail_items + cap - 1) / cap)) : kTail;
     for (int i = 0; i < h->nruns; ++i) {
         const HostRun &hr = h->runs[i];
         if (hr.inject_per_shift > 0) {
-            long long max_tail = (long long)(h->sort_interval + 1) * hr.inject_per_shift;
-            int tail_blocks = (int)((max_tail + kTail - 1) / kTail);
+            const long long max_tail = (long long)(h->sort_interval + 1) * hr.inject_per_shift;
+            const int tail_blocks = (int)((max_tail + h->tail_block - 1) / h->tail_block);
             for (int b = 0; b < tail_blocks; ++b) items.push_back(Item{i, 1, b, 0});
         }
     }
@@ -322,7 +336,7 @@ int build_items(pic_s *h)
     return cuda_fail(e);
 }
 
-int enqueue_step(pic_s *h, bool sort)
+int enqueue_step(pic_s *h, bool sort, bool adaptive)
 {
     cudaError_t e = cudaSuccess;
     const Run *R = h->d_runs;
@@ -336,7 +350,9 @@ int enqueue_step(pic_s *h, bool sort)
     // a recorded step keeps, after its sort, the slot each particle had before it
     int32_t *src_out = nullptr;
     if (sort && h->adj && h->adj->rec_on) src_out = h->adj->rec[h->steps_done - h->adj->rec_base].src;
-    if (sort) e = launch_sort(R, h->nruns, h->seg_parts, h->seg_keys, h->d_scan, src_out, st);
+    if (sort || adaptive)
+        e = launch_sort(R, h->nruns, h->seg_parts, h->seg_keys, h->d_scan, src_out, sort ? 1 : 0, h->sort_interval,
+                        adaptive ? 1 : 0, st);
     if (e == cudaSuccess && h->adj && h->adj->rec_on) {
         // the push of this step reads these particles and fields
         Rec &rc = h->adj->rec[h->steps_done - h->adj->rec_base];
@@ -362,7 +378,7 @@ int enqueue_step(pic_s *h, bool sort)
     if (e == cudaSuccess) e = launch_zero_j(R, h->seg_cells, st);
     mark(PIC_PH_PUSH);
     if (e == cudaSuccess)
-        e = launch_push(h->dim, h->order, h->tile, h->drift, h->use_tma, R, h->d_items, h->n_items, h->block, kTail,
+        e = launch_push(h->dim, h->order, h->tile, h->drift, h->use_tma, R, h->d_items, h->n_items, h->block, h->tail_block,
                         h->persistent ? h->d_queue : nullptr, h->num_sms, st);
     mark(PIC_PH_YEE_B1);
     if (e == cudaSuccess) e = launch_yee_b(h->dim, R, h->seg_cells, 0, h->yee_quad, st);
@@ -600,7 +616,12 @@ int create_common(const pic_config *cfgs, int n, pic_t **out)
     }
     h->drift = t.drift >= 0 ? t.drift : push_default_drift(h->dim, h->tile);
     h->block = t.block ? t.block : (h->dim == 3 ? 512 : 256);
-    h->sort_interval = t.sort_interval ? t.sort_interval : 4;
+    if (t.sort_policy < 0 || t.sort_policy > 1) {
+        delete h;
+        return PIC_EINVAL;
+    }
+    h->sort_adaptive = t.sort_policy == 0;
+    h->sort_interval = t.sort_interval ? t.sort_interval : (h->sort_adaptive ? kSortMaxAdaptive : 4);
     h->use_graph = t.use_graph != 0 && h->stream != nullptr;
     h->persistent = t.persistent == 1 || (t.persistent == 0 && n > 1);
     h->sort_sub = t.sort_sub ? t.sort_sub : 1;
@@ -771,13 +792,18 @@ int pic_step(pic_t *h, int32_t nsteps)
             if (e != cudaSuccess) return PIC_ECUDA;
             ck.time = h->time_host;
         }
-        bool sort = h->need_sort || h->since_sort >= h->sort_interval;
-        int kind = sort ? 1 : 0;
+        // adaptive policy: the device decides each step (sort_decide_kernel);
+        // the host forces a sort only where it must (after loads, at the start
+        // of a recomputed segment).  The adjoint keeps the fixed schedule, so
+        // that a recomputed segment repeats the forward run's sorts.
+        const bool adaptive = h->sort_adaptive && !h->adj;
+        bool sort = h->need_sort || (!adaptive && h->since_sort >= h->sort_interval);
+        int kind = (sort ? 1 : 0) + (adaptive ? 2 : 0);
         if (h->use_graph && !h->prof_on && !(h->adj && h->adj->rec_on)) {
             if (!h->graph[kind]) {
                 cudaGraph_t g = nullptr;
                 if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PIC_ECUDA;
-                int rc = enqueue_step(h, sort);
+                int rc = enqueue_step(h, sort, adaptive);
                 cudaError_t e = cudaStreamEndCapture(h->stream, &g);
                 if (rc || e != cudaSuccess) {
                     if (g) cudaGraphDestroy(g);
@@ -789,7 +815,7 @@ int pic_step(pic_t *h, int32_t nsteps)
             }
             if (cudaGraphLaunch(h->graph[kind], h->stream) != cudaSuccess) return PIC_ECUDA;
         } else {
-            int rc = enqueue_step(h, sort);
+            int rc = enqueue_step(h, sort, adaptive);
             if (rc) return rc;
         }
         if (sort) {
@@ -975,6 +1001,7 @@ int pic_diagnostics(pic_t *h, pic_diag *out)
     out->gauss_resid = mrho > 0.f ? (double)mres / (double)mrho : (double)mres;
     out->imbalance = (um[3] > 0 && dd[3] > 0) ? (double)um[2] / (dd[3] / (double)um[3]) : 0.0;
     out->slow_path = (int64_t)st.slow_last;
+    out->sorts = (int32_t)st.sorts;
     out->status = status_code(st.status);
     return out->status;
 }
@@ -1346,7 +1373,7 @@ void pic_destroy(pic_t *h)
     if (!h) return;
     cudaStreamSynchronize(h->stream);
     for (cudaEvent_t ev : h->prof_events) cudaEventDestroy(ev);
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < 4; ++k)
         if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
     std::vector<void *> all = h->allocs;
     for (void *p : all) {

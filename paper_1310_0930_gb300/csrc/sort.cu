@@ -41,6 +41,15 @@ __device__ __forceinline__ int seg_run(const Seg &s, int b)
     return lo;
 }
 
+// Grid-stride walk over the chunks of a particle segment: the next chunk of
+// this CTA at or after chunk `from` (chunks b with b = blockIdx.x mod
+// gridDim.x), used to step over a run that does not sort this step.
+__device__ __forceinline__ int next_own_chunk(int from)
+{
+    const int g = (int)gridDim.x, r = (from - (int)blockIdx.x) % g;
+    return r == 0 ? from : from + (g - r);
+}
+
 // What the tile key of a packed cell depends on, held in registers.
 struct KeyCtx {
     int b0, b1, m0, m1, t0, t1, t2, nt0, nt1, dim, open_last, origin, nl, lo, hi, nsub;
@@ -90,11 +99,39 @@ __device__ __forceinline__ int key_of_cell(const KeyCtx &k, int32_t c)
     return (cx >> k.t0) + k.nt0 * ((cy >> k.t1) + k.nt1 * (k.dim == 3 ? (cz >> k.t2) : 0));
 }
 
+// Whether each run sorts this step: when the host asks (force), or, under
+// the adaptive policy, when max_interval steps have passed since the last
+// sort or the slow path has taken at least n_total / kSortSlowDiv
+// particle-steps since then.  A particle that strays beyond its tile's
+// staged region takes the slow path (global gather and global atomics) and
+// stalls the other lanes of its warp meanwhile: a fraction of a percent of
+// such particles costs the push more than a sort, so the threshold is low.
+// The kernels of the sort below skip the runs that do not sort.
+__global__ void sort_decide_kernel(const Run *__restrict__ runs, int nruns, int force, int max_interval,
+                                   int adaptive)
+{
+    const int ri = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ri >= nruns) return;
+    RunState &s = *runs[ri].state;
+    bool go = force != 0;
+    if (adaptive) {
+        const unsigned long long n = s.n_total > 0 ? (unsigned long long)s.n_total : 0ull;
+        go = go || s.since_sort >= max_interval || (s.slow_acc > 0 && s.slow_acc * kSortSlowDiv >= n);
+    }
+    s.do_sort = go ? 1 : 0;
+    if (go) {
+        s.since_sort = 0;
+        s.slow_acc = 0;
+        s.sorts += 1;
+    }
+}
+
 __global__ void sort_zero_kernel(const Run *__restrict__ runs, int nruns)
 {
     const int ri = blockIdx.y;
     if (ri >= nruns) return;
     const Run &r = runs[ri];
+    if (!r.state->do_sort) return;
     const long long nk = (long long)r.ntiles * r.nsub;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nk; t += (long long)gridDim.x * blockDim.x)
         r.tile_cnt[t] = 0;
@@ -145,34 +182,41 @@ __device__ __forceinline__ int table_slot(KeyTable &t, int key)
 __global__ void __launch_bounds__(kSortThreads) sort_count_kernel(const Run *__restrict__ runs, Seg seg)
 {
     __shared__ KeyTable t;
-    const int ri = seg_run(seg, blockIdx.x);
-    const Run &r = runs[ri];
-    const KeyCtx kc = key_ctx(r, *r.state);
-    const long long i0 = (long long)(blockIdx.x - seg.start[ri]) * kSortChunk;
-    if (i0 >= kc.n_total) return;  // CTA-uniform
-    const int32_t *cells = r.P[r.state->buf].cell;
-    int32_t cell[kSortItems];
-#pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
-        const long long i = i0 + j * kSortThreads + threadIdx.x;
-        cell[j] = i < kc.n_total ? cells[i] : -1;
-    }
-    table_init(t);
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
-        const int key = sub_key(kc, key_of_cell(kc, cell[j]), i0 + j * kSortThreads + threadIdx.x);
-        const unsigned peers = key_peers(key);
-        if (key >= 0 && lane == __ffs(peers) - 1) {
-            const int e = table_slot(t, key);
-            if (e >= 0) atomicAdd(&t.cnt[e], __popc(peers));
-            else atomicAdd(&r.tile_cnt[key], __popc(peers));
+    for (int b = blockIdx.x; b < seg.nblocks; b += gridDim.x) {  // (CTA-uniform control flow)
+        const int ri = seg_run(seg, b);
+        const Run &r = runs[ri];
+        if (!r.state->do_sort) {  // the run does not sort this step: skip its chunks
+            b = next_own_chunk(seg.start[ri + 1]) - (int)gridDim.x;
+            continue;
         }
+        const KeyCtx kc = key_ctx(r, *r.state);
+        const long long i0 = (long long)(b - seg.start[ri]) * kSortChunk;
+        if (i0 >= kc.n_total) continue;
+        const int32_t *cells = r.P[r.state->buf].cell;
+        int32_t cell[kSortItems];
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            const long long i = i0 + j * kSortThreads + threadIdx.x;
+            cell[j] = i < kc.n_total ? cells[i] : -1;
+        }
+        table_init(t);
+        __syncthreads();
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            const int key = sub_key(kc, key_of_cell(kc, cell[j]), i0 + j * kSortThreads + threadIdx.x);
+            const unsigned peers = key_peers(key);
+            if (key >= 0 && lane == __ffs(peers) - 1) {
+                const int e = table_slot(t, key);
+                if (e >= 0) atomicAdd(&t.cnt[e], __popc(peers));
+                else atomicAdd(&r.tile_cnt[key], __popc(peers));
+            }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < kSortHash; e += blockDim.x)
+            if (t.key[e] >= 0 && t.cnt[e] > 0) atomicAdd(&r.tile_cnt[t.key[e]], t.cnt[e]);
+        __syncthreads();  // (the next chunk re-initialises the table)
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < kSortHash; e += blockDim.x)
-        if (t.key[e] >= 0 && t.cnt[e] > 0) atomicAdd(&r.tile_cnt[t.key[e]], t.cnt[e]);
 }
 
 // Exclusive scan of the key counters, pass 1: block b of a run scans its
@@ -184,6 +228,7 @@ __global__ void __launch_bounds__(kScanThreads) sort_scan_local_kernel(const Run
     __shared__ int warp_tot[kScanThreads / 32];
     const int ri = seg_run(seg, blockIdx.x);
     const Run &r = runs[ri];
+    if (!r.state->do_sort) return;  // CTA-uniform
     const long long nk = (long long)r.ntiles * r.nsub;
     const long long k0 = (long long)(blockIdx.x - seg.start[ri]) * kScanChunk + (long long)threadIdx.x * kScanItems;
     int v[kScanItems];
@@ -226,6 +271,7 @@ __global__ void __launch_bounds__(kScanThreads) sort_scan_add_kernel(const Run *
     __shared__ int warp_tot[kScanThreads / 32];
     const int ri = seg_run(seg, blockIdx.x);
     const Run &r = runs[ri];
+    if (!r.state->do_sort) return;  // CTA-uniform
     const int b0 = seg.start[ri], b = blockIdx.x;
     int part = 0;
     for (int q = b0 + threadIdx.x; q < b; q += blockDim.x) part += sums[q];
@@ -256,81 +302,88 @@ __global__ void __launch_bounds__(kSortThreads, 3) sort_scatter_kernel(const Run
                                                                     int32_t *__restrict__ src_out)
 {
     __shared__ KeyTable t;
-    const int ri = seg_run(seg, blockIdx.x);
-    const Run &r = runs[ri];
-    const KeyCtx kc = key_ctx(r, *r.state);
-    const long long i0 = (long long)(blockIdx.x - seg.start[ri]) * kSortChunk;
-    if (i0 >= kc.n_total) return;  // CTA-uniform
-    const int buf = r.state->buf;
-    const ParticleBuf src = r.P[buf];
-    const ParticleBuf dst = r.P[buf ^ 1];
-    int32_t cell[kSortItems];
-#pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
-        const long long i = i0 + j * kSortThreads + threadIdx.x;
-        cell[j] = i < kc.n_total ? src.cell[i] : -1;
-    }
-    table_init(t);
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const unsigned below = (1u << lane) - 1u;
-    int slot[kSortItems], rank[kSortItems];
-#pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
-        const int key = sub_key(kc, key_of_cell(kc, cell[j]), i0 + j * kSortThreads + threadIdx.x);
-        const unsigned peers = key_peers(key);
-        const int leader = __ffs(peers) - 1;
-        int e = -2, off = 0;
-        if (key >= 0 && lane == leader) {
-            e = table_slot(t, key);
-            off = e >= 0 ? atomicAdd(&t.cnt[e], __popc(peers)) : atomicAdd(&r.tile_cnt[key], __popc(peers));
+    for (int b = blockIdx.x; b < seg.nblocks; b += gridDim.x) {  // (CTA-uniform control flow)
+        const int ri = seg_run(seg, b);
+        const Run &r = runs[ri];
+        if (!r.state->do_sort) {  // the run does not sort this step: skip its chunks
+            b = next_own_chunk(seg.start[ri + 1]) - (int)gridDim.x;
+            continue;
         }
-        e = __shfl_sync(0xffffffffu, e, leader);
-        off = __shfl_sync(0xffffffffu, off, leader);
-        slot[j] = key >= 0 ? e : -2;  // -2: dead or outside the window, -1: rank is absolute
-        rank[j] = off + __popc(peers & below);
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < kSortHash; e += blockDim.x)
-        if (t.key[e] >= 0 && t.cnt[e] > 0) t.base[e] = atomicAdd(&r.tile_cnt[t.key[e]], t.cnt[e]);
-    __syncthreads();
-    const bool d3 = kc.dim == 3;
+        const KeyCtx kc = key_ctx(r, *r.state);
+        const long long i0 = (long long)(b - seg.start[ri]) * kSortChunk;
+        if (i0 >= kc.n_total) continue;
+        const int buf = r.state->buf;
+        const ParticleBuf src = r.P[buf];
+        const ParticleBuf dst = r.P[buf ^ 1];
+        int32_t cell[kSortItems];
 #pragma unroll
-    for (int g = 0; g < kSortItems; g += kSortGroup) {
-        float v[kSortGroup][6];
-        float wv[kSortGroup];
-        int32_t idv[kSortGroup];
-#pragma unroll
-        for (int q = 0; q < kSortGroup; ++q) {
-            const int j = g + q;
+        for (int j = 0; j < kSortItems; ++j) {
             const long long i = i0 + j * kSortThreads + threadIdx.x;
-            if (slot[j] != -2) {
-                v[q][0] = src.off[0][i];
-                v[q][1] = src.off[1][i];
-                v[q][2] = d3 ? src.off[2][i] : 0.f;
-                v[q][3] = src.u[0][i];
-                v[q][4] = src.u[1][i];
-                v[q][5] = src.u[2][i];
-                wv[q] = src.w ? src.w[i] : 0.f;
-                idv[q] = src.id ? src.id[i] : 0;
+            cell[j] = i < kc.n_total ? src.cell[i] : -1;
+        }
+        table_init(t);
+        __syncthreads();
+        const int lane = threadIdx.x & 31;
+        const unsigned below = (1u << lane) - 1u;
+        int slot[kSortItems], rank[kSortItems];
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            const int key = sub_key(kc, key_of_cell(kc, cell[j]), i0 + j * kSortThreads + threadIdx.x);
+            const unsigned peers = key_peers(key);
+            const int leader = __ffs(peers) - 1;
+            int e = -2, off = 0;
+            if (key >= 0 && lane == leader) {
+                e = table_slot(t, key);
+                off = e >= 0 ? atomicAdd(&t.cnt[e], __popc(peers)) : atomicAdd(&r.tile_cnt[key], __popc(peers));
+            }
+            e = __shfl_sync(0xffffffffu, e, leader);
+            off = __shfl_sync(0xffffffffu, off, leader);
+            slot[j] = key >= 0 ? e : -2;  // -2: dead or outside the window, -1: rank is absolute
+            rank[j] = off + __popc(peers & below);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < kSortHash; e += blockDim.x)
+            if (t.key[e] >= 0 && t.cnt[e] > 0) t.base[e] = atomicAdd(&r.tile_cnt[t.key[e]], t.cnt[e]);
+        __syncthreads();
+        const bool d3 = kc.dim == 3;
+#pragma unroll
+        for (int g = 0; g < kSortItems; g += kSortGroup) {
+            float v[kSortGroup][6];
+            float wv[kSortGroup];
+            int32_t idv[kSortGroup];
+#pragma unroll
+            for (int q = 0; q < kSortGroup; ++q) {
+                const int j = g + q;
+                const long long i = i0 + j * kSortThreads + threadIdx.x;
+                if (slot[j] != -2) {
+                    v[q][0] = src.off[0][i];
+                    v[q][1] = src.off[1][i];
+                    v[q][2] = d3 ? src.off[2][i] : 0.f;
+                    v[q][3] = src.u[0][i];
+                    v[q][4] = src.u[1][i];
+                    v[q][5] = src.u[2][i];
+                    wv[q] = src.w ? src.w[i] : 0.f;
+                    idv[q] = src.id ? src.id[i] : 0;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kSortGroup; ++q) {
+                const int j = g + q;
+                if (slot[j] == -2) continue;
+                const long long o = slot[j] >= 0 ? (long long)t.base[slot[j]] + rank[j] : (long long)rank[j];
+                dst.cell[o] = cell[j];
+                dst.off[0][o] = v[q][0];
+                dst.off[1][o] = v[q][1];
+                if (d3) dst.off[2][o] = v[q][2];
+                dst.u[0][o] = v[q][3];
+                dst.u[1][o] = v[q][4];
+                dst.u[2][o] = v[q][5];
+                if (src.w) dst.w[o] = wv[q];
+                if (src.id) dst.id[o] = idv[q];
+                if (src_out) src_out[o] = (int32_t)(i0 + j * kSortThreads + threadIdx.x);
             }
         }
-#pragma unroll
-        for (int q = 0; q < kSortGroup; ++q) {
-            const int j = g + q;
-            if (slot[j] == -2) continue;
-            const long long o = slot[j] >= 0 ? (long long)t.base[slot[j]] + rank[j] : (long long)rank[j];
-            dst.cell[o] = cell[j];
-            dst.off[0][o] = v[q][0];
-            dst.off[1][o] = v[q][1];
-            if (d3) dst.off[2][o] = v[q][2];
-            dst.u[0][o] = v[q][3];
-            dst.u[1][o] = v[q][4];
-            dst.u[2][o] = v[q][5];
-            if (src.w) dst.w[o] = wv[q];
-            if (src.id) dst.id[o] = idv[q];
-            if (src_out) src_out[o] = (int32_t)(i0 + j * kSortThreads + threadIdx.x);
-        }
+        __syncthreads();  // (the next chunk re-initialises the table)
     }
 }
 
@@ -340,6 +393,7 @@ __global__ void sort_finish_kernel(const Run *__restrict__ runs, int nruns)
     if (ri >= nruns) return;
     const Run &r = runs[ri];
     RunState &s = *r.state;
+    if (!s.do_sort) return;
     s.buf ^= 1;
     s.n_sorted = r.tile_off[r.ntiles];
     s.n_total = s.n_sorted;
@@ -348,13 +402,25 @@ __global__ void sort_finish_kernel(const Run *__restrict__ runs, int nruns)
 }  // namespace
 
 cudaError_t launch_sort(const Run *runs, int nruns, Seg parts, Seg keys, int *scan_sums, int32_t *src_out,
-                        cudaStream_t st)
+                        int force, int max_interval, int adaptive, cudaStream_t st)
 {
+    sort_decide_kernel<<<(nruns + 127) / 128, 128, 0, st>>>(runs, nruns, force, max_interval, adaptive);
     sort_zero_kernel<<<dim3(1024, nruns), kBlock, 0, st>>>(runs, nruns);
-    sort_count_kernel<<<parts.nblocks, kSortThreads, 0, st>>>(runs, parts);
+    // count and scatter: a grid of a few CTAs per SM walks the chunks (a
+    // run that does not sort costs each CTA one check, not one CTA per chunk)
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    const int g_count = parts.nblocks < 16 * sms ? parts.nblocks : 16 * sms;
+    const int g_scatter = parts.nblocks < 12 * sms ? parts.nblocks : 12 * sms;
+    sort_count_kernel<<<g_count > 0 ? g_count : 1, kSortThreads, 0, st>>>(runs, parts);
     sort_scan_local_kernel<<<keys.nblocks, kScanThreads, 0, st>>>(runs, keys, scan_sums);
     sort_scan_add_kernel<<<keys.nblocks, kScanThreads, 0, st>>>(runs, keys, scan_sums);
-    sort_scatter_kernel<<<parts.nblocks, kSortThreads, 0, st>>>(runs, parts, src_out);
+    sort_scatter_kernel<<<g_scatter > 0 ? g_scatter : 1, kSortThreads, 0, st>>>(runs, parts, src_out);
     sort_finish_kernel<<<(nruns + 127) / 128, 128, 0, st>>>(runs, nruns);
     return cudaGetLastError();
 }

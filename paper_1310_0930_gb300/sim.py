@@ -79,6 +79,7 @@ def make_config(w: Workload, *, tuning: Optional[dict] = None, track_ids=False, 
     cfg.tuning.sort_sub = int(t.get("sort_sub", 0))
     cfg.tuning.tma = int(t.get("tma", 0))
     cfg.tuning.adjoint_keep = int(t.get("adjoint_keep", 0))
+    cfg.tuning.sort_policy = int(t.get("sort_policy", 0))
     if alloc is not None:
         cfg.alloc = alloc
         cfg.free = free

@@ -79,7 +79,8 @@ def test_load_beyond_capacity_is_refused():
     parts = inputs.background(w)
     half = parts.n // 2
     first, second = parts.subset(np.arange(half)), parts.subset(np.arange(half, parts.n))
-    sim = Simulation(w, capacity=half + 12 * 32 * 4 + 4096)
+    # (fixed sort interval 4: the injection room is (4 + 2) shifts of particles)
+    sim = Simulation(w, capacity=half + 12 * 32 * 4 + 4096, tuning={"sort_interval": 4, "sort_policy": 1})
     sim.load(first)
     with pytest.raises(abi.PicError) as err:
         sim.load(second)

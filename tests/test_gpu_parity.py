@@ -129,7 +129,7 @@ def test_sort_interval_and_drift_do_not_change_results():
     runs = []
     for tuning in ({"sort_interval": 1, "drift": 1}, {"sort_interval": 7, "drift": 3},
                    {"sort_interval": 5, "tile": (8, 8)}, {"sort_interval": 3, "tile": (32, 32)},
-                   {"use_graph": 0}):
+                   {"use_graph": 0}, {"sort_policy": 1}, {"sort_policy": 1, "sort_interval": 9, "use_graph": 0}):
         gpu, _ = pair(w, parts, tuning=tuning)
         gpu.step(w.steps)
         runs.append({n: gpu.field(n) for n in FIELD_NAMES})
@@ -137,6 +137,30 @@ def test_sort_interval_and_drift_do_not_change_results():
     for other in runs[1:]:
         for n in FIELD_NAMES:
             assert rel_l2(other[n], runs[0][n]) < 2e-5, n
+
+
+def test_adaptive_sort_follows_the_slow_path():
+    """Adaptive sort policy: a slow thermal plasma sorts only at the longest
+    interval, a fast stream (|u| = 5, 0.69 cells per step) sorts as soon as
+    particles stray beyond the drift region; both step like the fixed policy."""
+    steps = 40
+    for uth, lo, hi in ((0.01, 2, 4), (5.0, 8, 41)):
+        w = inputs.thermal_2d(n=(64, 64), steps=steps)
+        w.uth = uth
+        parts = inputs.background(w)
+        out = {}
+        for name, tuning in (("adaptive", {}), ("fixed", {"sort_policy": 1, "sort_interval": 2})):
+            gpu, _ = pair(w, parts, tuning=tuning)
+            gpu.step(steps)
+            d = gpu.diagnostics()
+            assert d["status"] == 0
+            out[name] = (d["sorts"], {n: gpu.field(n) for n in FIELD_NAMES})
+            gpu.close()
+        sorts = out["adaptive"][0]
+        assert lo <= sorts <= hi, (uth, sorts)
+        assert out["fixed"][0] == steps // 2, out["fixed"][0]
+        for n in FIELD_NAMES:
+            assert rel_l2(out["adaptive"][1][n], out["fixed"][1][n]) < 1e-4, (uth, n)
 
 
 def test_lwfa_2d_laser_open_boundary_moving_window():
