@@ -150,9 +150,9 @@ typedef void (*pic_free_fn)(void *ptr, void *ctx);
  * push has sent, summed over the steps since that sort, at least 1/65536 of
  * its particles down the slow path (particles outside their tile's staged
  * region, each of which stalls its warp); 1 = fixed: every sort_interval
- * steps.  The adjoint form always
- * uses the fixed schedule (a recomputed segment repeats the forward run's
- * sorts).  drift: cells a
+ * steps.  The adjoint form always uses the fixed schedule (every
+ * sort_interval steps, default 4), so that a recomputed segment repeats the
+ * forward run's sorts.  drift: cells a
  * particle may stray outside its tile between sorts and still use the
  * staged fast path (-1 = default); block: threads per tile CTA, 128, 256, 384
  * or 512 (0 = default);

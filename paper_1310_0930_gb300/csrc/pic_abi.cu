@@ -87,7 +87,7 @@ struct pic_s {
     int adjoint_keep = 0;
     bool yee_quad = true;  // every run: rows of a multiple of 4 cells, 16-byte aligned field arrays
     size_t push_smem = 0;
-    int block = 256, sort_interval = 4, drift = 1, tile[3] = {16, 16, 1};
+    int block = 256, sort_interval = 4, fixed_interval = 4, drift = 1, tile[3] = {16, 16, 1};
     bool use_graph = true;
     bool started = false, need_sort = true, any_open = false, any_window = false;
     int since_sort = 0;
@@ -621,6 +621,10 @@ int create_common(const pic_config *cfgs, int n, pic_t **out)
         return PIC_EINVAL;
     }
     h->sort_adaptive = t.sort_policy == 0;
+    // sort_interval: the longest interval of the adaptive policy (also what
+    // the injection room and tail items are sized for); fixed_interval: the
+    // interval of the fixed schedule, which the adjoint form uses as well
+    h->fixed_interval = t.sort_interval ? t.sort_interval : 4;
     h->sort_interval = t.sort_interval ? t.sort_interval : (h->sort_adaptive ? kSortMaxAdaptive : 4);
     h->use_graph = t.use_graph != 0 && h->stream != nullptr;
     h->persistent = t.persistent == 1 || (t.persistent == 0 && n > 1);
@@ -797,7 +801,7 @@ int pic_step(pic_t *h, int32_t nsteps)
         // of a recomputed segment).  The adjoint keeps the fixed schedule, so
         // that a recomputed segment repeats the forward run's sorts.
         const bool adaptive = h->sort_adaptive && !h->adj;
-        bool sort = h->need_sort || (!adaptive && h->since_sort >= h->sort_interval);
+        bool sort = h->need_sort || (!adaptive && h->since_sort >= h->fixed_interval);
         int kind = (sort ? 1 : 0) + (adaptive ? 2 : 0);
         if (h->use_graph && !h->prof_on && !(h->adj && h->adj->rec_on)) {
             if (!h->graph[kind]) {
