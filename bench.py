@@ -93,6 +93,8 @@ def particle_chunks(w):
 # the default tuning of the kernel they were taken with.
 PUSH_PROFILE = {
     ("lwfa_3d", 2): (61.09, 16.65, "push_kernel_lwfa3d_quadratic_256x256x1024.md"),
+    ("warm_3d", 2): (65.32, 93.19, "push_kernel_warm3d_quadratic_256x256x256.md"),
+    ("bunch_3d", 3): (68.12, 22.37, "push_kernel_bunch3d_cubic_256x256x512.md"),
 }
 
 
