@@ -98,6 +98,24 @@ PUSH_PROFILE = {
 }
 
 
+def aggregate_replicas(elapsed, units):
+    """Whole-job figures of independent replicas, one per rank: the slowest
+    rank's elapsed time and the units all ranks processed (max and sum over
+    the ranks of the initialised process group; the local figures alone
+    without one).  Tensors live where the backend wants them (CUDA for nccl,
+    host memory for gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(elapsed), float(units)
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=dev)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def algorithmic_bytes(w, n_particles):
     """Bytes the method must move once per step (state read + write): per
     particle 2 * (4 packed cell + 4*dim offsets + 12 momentum [+4 weight]);
@@ -423,12 +441,9 @@ def main():
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     d1 = sim.diagnostics()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     n_avg = 0.5 * (d0["n_particles"] + d1["n_particles"])
-    value = world * n_avg * args.steps / (ms / 1e3)
+    ms, units = aggregate_replicas(ms, n_avg * args.steps)
+    value = units / (ms / 1e3)
     step_bytes, push_bytes, sp = algorithmic_bytes(w, n_avg)
     push_ms = phases["push"] / args.steps
     peaks = {}
@@ -477,12 +492,8 @@ def main():
         dd = sim2.diagnostics()  # energies and particle count back to the host
         t1 = time.perf_counter()
         barrier()
-        sec = t1 - t0
-        if world > 1:
-            t = torch.tensor([sec], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            sec = float(t.item())
-        e2e = {"value": world * n0 * args.steps / sec, "unit": UNIT,
+        sec, units_e2e = aggregate_replicas(t1 - t0, n0 * args.steps)
+        e2e = {"value": units_e2e / sec, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(96 + 96 / args.steps),
                "includes": "pic_load_particles from pinned host memory, %d x (pic_step + pic_sync), "
                            "pic_diagnostics" % args.steps}
