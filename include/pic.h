@@ -148,8 +148,9 @@ typedef void (*pic_free_fn)(void *ptr, void *ctx);
  * 16); sort_policy: 0 = adaptive (default): each step the device sorts a
  * run when sort_interval steps have passed since its last sort or when its
  * push has sent, summed over the steps since that sort, at least 1/65536 of
- * its particles down the slow path (particles outside their tile's staged
- * region, each of which stalls its warp); 1 = fixed: every sort_interval
+ * its particles down the slow path from their tiles (particles outside their
+ * tile's staged region, each of which stalls its warp; the unsorted tail that
+ * the moving window injects is not counted); 1 = fixed: every sort_interval
  * steps.  The adjoint form always uses the fixed schedule (every
  * sort_interval steps, default 4), so that a recomputed segment repeats the
  * forward run's sorts.  drift: cells a

@@ -46,7 +46,8 @@ struct RunState {
     long long n_total;   // slots [n_sorted, n_total) are an unsorted tail
     unsigned long long slow;       // slow-path particles of the push in progress
     unsigned long long slow_last;  // slow-path particles of the last completed step
-    unsigned long long slow_acc;   // slow-path particle-steps since the last sort
+    unsigned long long stray;      // of those, particles of tiles outside the drift region
+    unsigned long long slow_acc;   // stray particle-steps since the last sort
     int since_sort;                // completed steps since the last sort
     int do_sort;                   // this step sorts (set by the sort decision)
     long long sorts;               // sorts so far

@@ -413,7 +413,8 @@ __global__ void end_step_kernel(const Run *__restrict__ runs, int nruns)
     s.time += r.dt_d;
     s.step += 1;
     s.slow_last = s.slow;
-    s.slow_acc += s.slow;
+    s.slow_acc += s.stray;  // (the unsorted tail is bounded by the longest interval)
+    s.stray = 0;
     s.since_sort += 1;
     s.slow = 0;
     s.shift_pending = 0;

@@ -26,8 +26,8 @@ constexpr int kBlock = 256;
 // entries; the particle segments of the sort are in units of chunks.
 constexpr int kSortThreads = 256, kSortItems = 8, kSortGroup = 2, kSortChunk = kSortThreads * kSortItems;
 constexpr int kSortHashLog = 9, kSortHash = 1 << kSortHashLog, kSortProbe = 32;
-// adaptive sort: sort once the slow path has taken n_total / kSortSlowDiv
-// particle-steps since the last sort
+// adaptive sort: sort once strays (particles outside their tile's drift
+// region) add up to n_total / kSortSlowDiv particle-steps since the last sort
 constexpr unsigned long long kSortSlowDiv = 65536;
 // The exclusive scan of the (tile, sub-bucket) counters runs in blocks of
 // kScanChunk keys (kScanThreads threads x kScanItems consecutive keys).

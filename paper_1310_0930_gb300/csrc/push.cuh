@@ -841,7 +841,10 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
                 if (hi[c] | lo[c]) atomicAdd(r.J[c] + g, fmaf((float)lo[c], inv_lo, (float)hi[c] * inv));
         }
     }
-    if (threadIdx.x == 0 && slow_cnt) atomicAdd(&stp->slow, (unsigned long long)slow_cnt);
+    if (threadIdx.x == 0 && slow_cnt) {
+        atomicAdd(&stp->slow, (unsigned long long)slow_cnt);
+        if (tile_item) atomicAdd(&stp->stray, (unsigned long long)slow_cnt);  // (not the unsorted tail)
+    }
 }
 
 // One CTA per item.  The persistent schedule is a kernel of its own so that

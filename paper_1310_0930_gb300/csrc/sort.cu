@@ -101,11 +101,13 @@ __device__ __forceinline__ int key_of_cell(const KeyCtx &k, int32_t c)
 
 // Whether each run sorts this step: when the host asks (force), or, under
 // the adaptive policy, when max_interval steps have passed since the last
-// sort or the slow path has taken at least n_total / kSortSlowDiv
-// particle-steps since then.  A particle that strays beyond its tile's
-// staged region takes the slow path (global gather and global atomics) and
-// stalls the other lanes of its warp meanwhile: a fraction of a percent of
-// such particles costs the push more than a sort, so the threshold is low.
+// sort or particles that strayed beyond their tiles' staged regions add up
+// to n_total / kSortSlowDiv particle-steps since then.  A stray takes the
+// slow path (global gather and global atomics) and stalls the other lanes of
+// its warp meanwhile: a fraction of a percent of strays costs the push more
+// than a sort, so the threshold is low.  The unsorted tail of particles
+// injected by the moving window is not counted (it is pushed by CTAs of its
+// own, and the longest interval bounds it).
 // The kernels of the sort below skip the runs that do not sort.
 __global__ void sort_decide_kernel(const Run *__restrict__ runs, int nruns, int force, int max_interval,
                                    int adaptive)
