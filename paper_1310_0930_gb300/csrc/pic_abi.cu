@@ -194,6 +194,7 @@ int validate(const pic_config *c)
     if (t.drift < -1 || t.drift > 8) return PIC_EINVAL;
     if (t.block != 0 && t.block != 128 && t.block != 256 && t.block != 384 && t.block != 512) return PIC_EINVAL;
     if (t.sort_interval < 0) return PIC_EINVAL;
+    if (t.sort_policy < 0 || t.sort_policy > 1) return PIC_EINVAL;
     if (t.persistent < 0 || t.persistent > 2) return PIC_EINVAL;
     return PIC_OK;
 }
@@ -616,10 +617,6 @@ int create_common(const pic_config *cfgs, int n, pic_t **out)
     }
     h->drift = t.drift >= 0 ? t.drift : push_default_drift(h->dim, h->tile);
     h->block = t.block ? t.block : (h->dim == 3 ? 512 : 256);
-    if (t.sort_policy < 0 || t.sort_policy > 1) {
-        delete h;
-        return PIC_EINVAL;
-    }
     h->sort_adaptive = t.sort_policy == 0;
     // sort_interval: the longest interval of the adaptive policy (also what
     // the injection room and tail items are sized for); fixed_interval: the

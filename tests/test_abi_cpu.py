@@ -89,6 +89,11 @@ def test_validation_rejects_bad_configs_before_touching_the_device():
     # non power-of-two tile
     cfg, keep = make_config(w, tuning={"tile": (12, 16)})
     assert _create(cfg)[0] == abi.PIC_EINVAL
+    # unknown sort policy, negative sort interval
+    cfg, keep = make_config(w, tuning={"sort_policy": 2})
+    assert _create(cfg)[0] == abi.PIC_EINVAL
+    cfg, keep = make_config(w, tuning={"sort_interval": -1})
+    assert _create(cfg)[0] == abi.PIC_EINVAL
     # window on a periodic axis
     cfg, keep = make_config(w)
     cfg.window.enabled = 1
