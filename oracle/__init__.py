@@ -25,7 +25,10 @@ force, never against itself:
                             below a bound.
 * moving window          -- equals a fixed larger box in the window frame
                             until boundary effects arrive.
-LWFA physics beyond these (wake amplitude, injection): parity unpinned.
+* laser-plasma coupling  -- the linear wake of a weak Gaussian pulse: peak
+                            field, wavelength at the group velocity, a0^2
+                            scaling against the 1D closed form.
+LWFA physics beyond these (nonlinear wakes, self-injection): parity unpinned.
 """
 from __future__ import annotations
 
