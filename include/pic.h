@@ -174,7 +174,12 @@ typedef void (*pic_free_fn)(void *ptr, void *ctx);
  * adjoint_keep: checkpoint segments whose per-step records the forward run
  * keeps, so that the reverse sweep recomputes only the others: 0 = default
  * (as many as 60 % of the free device memory holds), -1 = none (every
- * segment recomputed), n = at most n. */
+ * segment recomputed), n = at most n.
+ * stream_zero_tiles: 0 = default (1), 1 = each step, classify the tiles on
+ * the device: a tile whose staged field region is all +0 (E = B = 0 at every
+ * particle, as ahead of a laser front) is advanced by a streaming kernel
+ * without shared-memory tiles, the others by the staged kernel; 2 = every
+ * tile through the staged kernel. */
 typedef struct {
     int32_t tile[3];
     int32_t sort_interval;
@@ -186,6 +191,7 @@ typedef struct {
     int32_t tma;
     int32_t adjoint_keep;
     int32_t sort_policy;
+    int32_t stream_zero_tiles;
 } pic_tuning;
 
 typedef struct {
@@ -285,7 +291,8 @@ PIC_API int pic_diagnostics(pic_t *h, pic_diag *out);
 #define PIC_PH_YEE_E 4 /* includes the Mur save/apply */
 #define PIC_PH_YEE_B2 5
 #define PIC_PH_WINDOW 6 /* end-of-step bookkeeping, window shift and injection */
-#define PIC_NUM_PHASES 7
+#define PIC_PH_PUSH_ZERO 7 /* the zero-field tiles' streaming kernel: a part of PIC_PH_PUSH */
+#define PIC_NUM_PHASES 8
 PIC_API int pic_profile_begin(pic_t *h, int32_t max_steps);
 PIC_API int pic_profile_end(pic_t *h, double *ms, int32_t n_phases, int64_t *launches);
 
@@ -352,7 +359,9 @@ PIC_API int pic_adjoint_fields(pic_t *h, float *lam, float *lam_j, double t);
  * overlap on the GPU (different streams, threads or handles) race and must
  * be ordered by the caller.  The first call on a device looks up the
  * array's device address (with that device current), so make that first
- * call before any CUDA stream capture.  No cudaMalloc, cudaFree or other
+ * call before any CUDA stream capture; after cudaDeviceReset the next call
+ * looks it up again in the new context.  Host threads may call
+ * concurrently (the address lookup is locked).  No cudaMalloc, cudaFree or other
  * allocating routine is called.  Errors: PIC_EINVAL (arguments, grid too
  * large), PIC_ECUDA (launch failure). */
 #define PIC_STATIC_MAX_CELLS (1ll << 21)

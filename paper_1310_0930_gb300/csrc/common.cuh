@@ -77,6 +77,10 @@ struct Run {
     int32_t *tile_off; // [ntiles + 1] particle offsets per tile
     int32_t *tile_cnt; // [ntiles * nsub] sort counters / cursors per (tile, sub-bucket)
     int nsub;          // sort sub-buckets per tile (power of two): slot i goes to sub-bucket i % nsub
+    // per tile: 1 if some E or B value of the tile's own cells may be non-zero,
+    // 0 if all are +0 (cleared by the first B half step, set by the second; set
+    // for every tile whenever E or B is written from outside the timestep)
+    uint8_t *fz;
     long long capacity;
     // laser antenna
     int laser_on, laser_pol, laser_plane;

@@ -52,12 +52,23 @@ __device__ double laser_r2(const Run &r, int i, int j)
     return r2;
 }
 
+// Field flags of the tiles (Run::fz): the first B half step of a timestep
+// clears them (the push of the step has read them), the second sets the flag
+// of every tile holding a cell whose final E or B is not +0.  The push of the
+// next step streams the particles of tiles whose neighbourhood is all +0.
+__device__ __forceinline__ void clear_tile_flags(const Run &r, const Seg &seg, int ri, int t)
+{
+    const int nthreads = (seg.start[ri + 1] - seg.start[ri]) * blockDim.x;
+    for (; t < r.ntiles; t += nthreads) r.fz[t] = 0;
+}
+
 template <int DIM>
 __global__ void yee_b_kernel(const Run *__restrict__ runs, Seg seg, int second)
 {
     const int ri = seg_run(seg, blockIdx.x);
     const Run &r = runs[ri];
     const int idx = (blockIdx.x - seg.start[ri]) * blockDim.x + threadIdx.x;
+    if (!second && r.fz) clear_tile_flags(r, seg, ri, idx);
     if (idx >= r.ncell) return;
     const RunState &s = *r.state;
     const int n0 = r.n[0], n1 = r.n[1];
@@ -107,6 +118,11 @@ __global__ void yee_b_kernel(const Run *__restrict__ runs, Seg seg, int second)
         const double t = s.time + (second ? r.dt_d : 0.0);
         const double e = laser_field(r, laser_r2(r, i, j), t);
         r.B[bcomp][idx] += (float)(sgn * (double)h * (double)r.inv_d[DIM - 1] * e);
+    }
+    if (second && r.fz) {
+        const unsigned nz = __float_as_uint(ex) | __float_as_uint(ey) | __float_as_uint(ez) |
+                            __float_as_uint(Bx[idx]) | __float_as_uint(By[idx]) | __float_as_uint(Bz[idx]);
+        if (nz) r.fz[tile_of(r, i, j, k)] = 1;  // (several threads may store the same 1)
     }
 }
 
@@ -185,6 +201,7 @@ __global__ void yee_b_quad_kernel(const Run *__restrict__ runs, Seg seg, int sec
     const int ri = seg_run(seg, blockIdx.x);
     const Run &r = runs[ri];
     const int idx0 = (blockIdx.x - seg.start[ri]) * kBlock + 4 * threadIdx.x;
+    if (!second && r.fz) clear_tile_flags(r, seg, ri, (blockIdx.x - seg.start[ri]) * blockDim.x + threadIdx.x);
     if (idx0 >= r.ncell) return;
     const RunState &s = *r.state;
     const int n0 = r.n[0], n1 = r.n[1];
@@ -258,6 +275,16 @@ __global__ void yee_b_quad_kernel(const Run *__restrict__ runs, Seg seg, int sec
     st4(r.B[0] + idx0, bx);
     st4(r.B[1] + idx0, by);
     st4(r.B[2] + idx0, bz);
+    if (second && r.fz) {
+        unsigned nz = 0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            nz |= __float_as_uint(ex[e]) | __float_as_uint(ey[e]) | __float_as_uint(ez[e]) | __float_as_uint(bx[e]) |
+                  __float_as_uint(by[e]) | __float_as_uint(bz[e]);
+        // (tiles are at least 4 cells wide along x and rows start on multiples
+        // of 4, so the four cells share one tile; several threads may store the same 1)
+        if (nz) r.fz[tile_of(r, i0, j, k)] = 1;
+    }
 }
 
 template <int DIM>

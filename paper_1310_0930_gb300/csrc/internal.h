@@ -41,10 +41,33 @@ size_t push_smem_bytes(int dim, int order, const int *tile, int drift, bool tma)
 // 3D: extents of the TMA box that loads one component of the field tile
 // (returns 0 for 2D or an entry not compiled with TMA staging)
 int push_tma_box(int dim, int order, const int *tile, int drift, int *box);
-// queue != nullptr: persistent grid of persistent_ctas x (CTAs per SM) taking
-// items from the device counter *queue (reset by the launch).
-cudaError_t launch_push(int dim, int order, const int *tile, int drift, bool tma, const Run *runs, const Item *items,
-                        int nitems, int block, int tail_block, int *queue, int persistent_ctas, cudaStream_t st);
+// the field region a tile stages: lo[a] cells before the tile origin, len[a]
+// cells long, per axis (returns 0 for an entry that is not compiled)
+int push_stage_extent(int dim, int order, const int *tile, int drift, bool tma, int *lo, int *len);
+
+// One launch of the staged particle kernel.
+struct PushArgs {
+    const Run *runs;
+    const Item *items;
+    int nitems;           // items of the launch; with live_cnt, the leading fixed items
+    const int *live_cnt;  // device count of the items after the fixed ones (may be null)
+    int max_extra;        // upper bound of that count
+    int block, tail_block;
+    int *queue;           // non-null: persistent grid of persistent_ctas x (CTAs per SM)
+                          // taking items from this device counter (reset by the launch)
+    int persistent_ctas;
+};
+cudaError_t launch_push(int dim, int order, const int *tile, int drift, bool tma, const PushArgs &a, cudaStream_t st);
+
+// Per-step tile classification (push.cu): the tile items items[n_tail,
+// n_items) are split into live tiles, appended to `live` after its n_tail
+// tail items (count in cnt[0]), and zero-field tiles, written to `zero`
+// (count in cnt[1]); cnt must be cleared before.  The zero-field tiles are
+// then advanced by the streaming kernel (launch_push_zero).
+cudaError_t launch_classify(const Run *runs, const Item *items, int n_tail, int n_items, const int *stage_lo,
+                            const int *stage_len, Item *live, Item *zero, int *cnt, cudaStream_t st);
+cudaError_t launch_push_zero(int dim, int order, const Run *runs, const Item *zero, const int *count, int max_items,
+                             int num_sms, cudaStream_t st);
 
 // fields.cu
 cudaError_t launch_zero_j(const Run *runs, Seg cells, cudaStream_t st);

@@ -11,6 +11,7 @@
 // loads the library holds the array until the process exits.
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 
 #include "pic.h"
 #include "common.cuh"
@@ -25,10 +26,54 @@ static_assert(kStaticMaxCells == PIC_STATIC_MAX_CELLS, "header and implementatio
 
 __device__ __align__(256) double g_rho_scratch[kStaticMaxCells];
 
-// Device address of g_rho_scratch per device, looked up once with that
-// device current (the host-side symbol is only a stand-in for it).
+// Device address of g_rho_scratch per device.  In host code the symbol is
+// only a stand-in, so the address is looked up with cudaGetSymbolAddress
+// with that device current.  The lookup is cached together with the unique
+// id of the context it was made in: after cudaDeviceReset the module is
+// loaded again into a new context, the id changes and the address is looked
+// up again instead of reusing a stale one.  A mutex guards the cache, so
+// host threads may call concurrently (their kernels still share the array).
 constexpr int kMaxDevices = 64;
-double *g_scratch_ptr[kMaxDevices] = {};
+struct ScratchSlot {
+    unsigned long long ctx_id;  // 0: not looked up
+    double *ptr;
+};
+ScratchSlot g_scratch[kMaxDevices] = {};
+std::mutex g_scratch_mu;
+
+// Unique id of the calling thread's current context (cuCtxGetId through the
+// runtime's driver entry point, so the library does not link libcuda), or 0
+// when there is none or the driver lacks the call.
+unsigned long long current_context_id()
+{
+    using GetIdFn = int (*)(void *ctx, unsigned long long *id);
+    static GetIdFn fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<GetIdFn>(f);
+    }();
+    unsigned long long id = 0;
+    if (!fn || fn(nullptr, &id) != 0) return 0;
+    return id;
+}
+
+// Device address of the scratch array on device `dev` (current), or null.
+double *scratch_address(int dev)
+{
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    ScratchSlot &slot = g_scratch[dev];
+    const unsigned long long id = current_context_id();
+    if (slot.ptr && id != 0 && slot.ctx_id == id) return slot.ptr;
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_rho_scratch) != cudaSuccess || !p) return nullptr;
+    // (the lookup creates the context if there was none yet: take its id now)
+    slot.ctx_id = current_context_id();
+    slot.ptr = static_cast<double *>(p);
+    return slot.ptr;
+}
 
 struct GridArgs {
     int n[3];
@@ -101,20 +146,18 @@ extern "C" int pic_charge_density_static(const pic_grid *grid, int32_t shape_ord
     GridArgs g{{1, 1, 1}, 1};
     for (int a = 0; a < grid->dim; ++a) {
         if (grid->n[a] < 1) return PIC_EINVAL;
+        // the static scratch holds PIC_STATIC_MAX_CELLS cells; checked per
+        // axis before multiplying, so the product cannot overflow
+        if (grid->n[a] > kStaticMaxCells / ncell) return PIC_EINVAL;
         g.n[a] = grid->n[a];
         ncell *= grid->n[a];
     }
-    if (ncell > kStaticMaxCells) return PIC_EINVAL;  // the static scratch holds PIC_STATIC_MAX_CELLS cells
     g.ncell = (int)ncell;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PIC_ECUDA;
-    if (!g_scratch_ptr[dev]) {
-        // first call on this device: resolve the array's device address with the device current
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_rho_scratch) != cudaSuccess || !p) return PIC_ECUDA;
-        g_scratch_ptr[dev] = static_cast<double *>(p);
-    }
-    double *s = g_scratch_ptr[dev];
+    // first call on a device (or in a new context of it): look up the array's device address
+    double *s = scratch_address(dev);
+    if (!s) return PIC_ECUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const unsigned zb = (unsigned)((ncell + kBlock - 1) / kBlock < 4096 ? (ncell + kBlock - 1) / kBlock : 4096);
     zero_kernel<<<zb, kBlock, 0, st>>>(s, g.ncell);  // the array keeps the previous call's sums

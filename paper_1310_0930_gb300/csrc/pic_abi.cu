@@ -23,6 +23,10 @@ using namespace pic;
 namespace {
 
 constexpr int kTail = 256;              // particles per tail work item (at least)
+// profiling events of one step: the marks that open phases 0..PIC_PH_WINDOW in
+// order, the end mark, and the start of the zero-field kernel (the end of
+// PIC_PH_PUSH_ZERO is the mark that opens PIC_PH_YEE_B1)
+constexpr int kMarkEnd = PIC_PH_WINDOW + 1, kMarkZero = kMarkEnd + 1, kEvPerStep = kMarkZero + 1;
 constexpr int kSortMaxAdaptive = 16;    // default longest interval between sorts, adaptive policy
 
 struct HostRun {
@@ -78,6 +82,12 @@ struct pic_s {
     RunState *d_states = nullptr;
     Item *d_items = nullptr;
     int n_items = 0;
+    int n_tail = 0;               // leading tail items of d_items
+    bool classify = true;         // stream the zero-field tiles (launch_classify)
+    Item *d_live = nullptr;       // per step: tail items, then the live tiles
+    Item *d_zero = nullptr;       // per step: the zero-field tiles
+    int *d_cnt = nullptr;         // [4]: live tiles, zero tiles, work queue of the live kernel, spare
+    int stage_lo[3] = {0, 0, 0}, stage_len[3] = {1, 1, 1};  // field region a tile stages
     int *d_seg = nullptr;  // 5 segment tables of nruns+1 ints
     int *d_scan = nullptr; // per-block sums of the sort's key scan
     Seg seg_cells{}, seg_planes{}, seg_parts{}, seg_inject{}, seg_keys{};
@@ -99,7 +109,7 @@ struct pic_s {
     int num_sms = 1;
     int tail_block = 256;  // particles per tail work item (build_items)
     cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};  // [sort forced + 2 * adaptive]
-    // phase profiling: events[step][PIC_NUM_PHASES + 1]
+    // phase profiling: events[step][kEvPerStep]
     std::vector<cudaEvent_t> prof_events;
     int prof_max = 0, prof_steps = 0;
     bool prof_on = false;
@@ -196,6 +206,7 @@ int validate(const pic_config *c)
     if (t.sort_interval < 0) return PIC_EINVAL;
     if (t.sort_policy < 0 || t.sort_policy > 1) return PIC_EINVAL;
     if (t.persistent < 0 || t.persistent > 2) return PIC_EINVAL;
+    if (t.stream_zero_tiles < 0 || t.stream_zero_tiles > 2) return PIC_EINVAL;
     return PIC_OK;
 }
 
@@ -316,6 +327,7 @@ int build_items(pic_s *h)
             for (int b = 0; b < tail_blocks; ++b) items.push_back(Item{i, 1, b, 0});
         }
     }
+    const int n_tail = (int)items.size();
     std::vector<int> order(h->nruns);
     for (int i = 0; i < h->nruns; ++i) order[i] = i;
     auto load = [&](int i) {
@@ -328,13 +340,30 @@ int build_items(pic_s *h)
         for (int t = 0; t < hr.r.ntiles; ++t) items.push_back(Item{i, 0, t, 0});
     }
     if (h->d_items) dev_free(h, h->d_items);
-    h->d_items = (Item *)dev_alloc(h, sizeof(Item) * (items.size() ? items.size() : 1));
-    if (!h->d_items) return PIC_ENOMEM;
+    if (h->d_live) dev_free(h, h->d_live);
+    if (h->d_zero) dev_free(h, h->d_zero);
+    const size_t nb = sizeof(Item) * (items.size() ? items.size() : 1);
+    h->d_items = (Item *)dev_alloc(h, nb);
+    h->d_live = (Item *)dev_alloc(h, nb);
+    h->d_zero = (Item *)dev_alloc(h, nb);
+    if (!h->d_items || !h->d_live || !h->d_zero) return PIC_ENOMEM;
     h->n_items = (int)items.size();
+    h->n_tail = n_tail;
     cudaError_t e = cudaMemcpyAsync(h->d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice,
                                     h->stream);
+    // the live list starts with the tail items; the classification appends the live tiles
+    if (e == cudaSuccess && n_tail)
+        e = cudaMemcpyAsync(h->d_live, items.data(), sizeof(Item) * n_tail, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     return cuda_fail(e);
+}
+
+// Mark every tile of run `hr` as possibly holding non-zero fields (after E or
+// B was written from outside the timestep); the next second B half step
+// recomputes the flags.
+cudaError_t flag_all_tiles(pic_s *h, HostRun &hr)
+{
+    return hr.r.fz ? cudaMemsetAsync(hr.r.fz, 1, (size_t)hr.r.ntiles, h->stream) : cudaSuccess;
 }
 
 int enqueue_step(pic_s *h, bool sort, bool adaptive)
@@ -343,7 +372,7 @@ int enqueue_step(pic_s *h, bool sort, bool adaptive)
     const Run *R = h->d_runs;
     cudaStream_t st = h->stream;
     cudaEvent_t *ev = nullptr;
-    if (h->prof_on && h->prof_steps < h->prof_max) ev = &h->prof_events[(size_t)h->prof_steps * (PIC_NUM_PHASES + 1)];
+    if (h->prof_on && h->prof_steps < h->prof_max) ev = &h->prof_events[(size_t)h->prof_steps * kEvPerStep];
     auto mark = [&](int ph) {
         if (ev && e == cudaSuccess) e = cudaEventRecord(ev[ph], st);
     };
@@ -378,9 +407,25 @@ int enqueue_step(pic_s *h, bool sort, bool adaptive)
     mark(PIC_PH_ZERO_J);
     if (e == cudaSuccess) e = launch_zero_j(R, h->seg_cells, st);
     mark(PIC_PH_PUSH);
-    if (e == cudaSuccess)
-        e = launch_push(h->dim, h->order, h->tile, h->drift, h->use_tma, R, h->d_items, h->n_items, h->block, h->tail_block,
-                        h->persistent ? h->d_queue : nullptr, h->num_sms, st);
+    if (h->classify) {
+        // live tiles (and the tail) through the staged kernel, zero-field tiles streamed
+        const int n_tiles = h->n_items - h->n_tail;
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->d_cnt, 0, sizeof(int) * 4, st);
+        if (e == cudaSuccess)
+            e = launch_classify(R, h->d_items, h->n_tail, h->n_items, h->stage_lo, h->stage_len, h->d_live, h->d_zero,
+                                h->d_cnt, st);
+        const PushArgs a{R, h->d_live, h->n_tail, h->d_cnt, n_tiles, h->block, h->tail_block,
+                         h->persistent ? h->d_cnt + 2 : nullptr, h->num_sms};
+        if (e == cudaSuccess) e = launch_push(h->dim, h->order, h->tile, h->drift, h->use_tma, a, st);
+        if (ev && e == cudaSuccess) e = cudaEventRecord(ev[kMarkZero], st);
+        if (e == cudaSuccess)
+            e = launch_push_zero(h->dim, h->order, R, h->d_zero, h->d_cnt + 1, n_tiles, h->num_sms, st);
+    } else {
+        const PushArgs a{R, h->d_items, h->n_items, nullptr, 0, h->block, h->tail_block,
+                         h->persistent ? h->d_queue : nullptr, h->num_sms};
+        if (e == cudaSuccess) e = launch_push(h->dim, h->order, h->tile, h->drift, h->use_tma, a, st);
+        if (ev && e == cudaSuccess) e = cudaEventRecord(ev[kMarkZero], st);
+    }
     mark(PIC_PH_YEE_B1);
     if (e == cudaSuccess) e = launch_yee_b(h->dim, R, h->seg_cells, 0, h->yee_quad, st);
     mark(PIC_PH_YEE_E);
@@ -392,10 +437,10 @@ int enqueue_step(pic_s *h, bool sort, bool adaptive)
     mark(PIC_PH_WINDOW);
     if (e == cudaSuccess) e = launch_end_step(R, h->nruns, st);
     if (e == cudaSuccess && h->any_window) e = launch_window(R, h->seg_planes, h->seg_inject, st);
-    mark(PIC_NUM_PHASES);
+    mark(kMarkEnd);
     if (ev) {
         h->prof_steps += 1;
-        h->prof_launches += (sort ? 6 : 0) + 6 + (h->any_open ? 2 : 0) + (h->any_window ? 3 : 0);
+        h->prof_launches += (sort ? 6 : 0) + 6 + (h->classify ? 2 : 0) + (h->any_open ? 2 : 0) + (h->any_window ? 3 : 0);
     }
     return cuda_fail(e);
 }
@@ -435,9 +480,8 @@ int first_step_setup(pic_s *h)
         if (e != cudaSuccess) return PIC_ECUDA;
     }
     // sets the push kernel's shared-memory limit outside any graph capture
-    cudaError_t e =
-        launch_push(h->dim, h->order, h->tile, h->drift, h->use_tma, h->d_runs, h->d_items, 0, h->block, kTail, nullptr, 1,
-                    h->stream);
+    const PushArgs a0{h->d_runs, h->d_items, 0, nullptr, 0, h->block, kTail, nullptr, 1};
+    cudaError_t e = launch_push(h->dim, h->order, h->tile, h->drift, h->use_tma, a0, h->stream);
     if (e != cudaSuccess) return PIC_ECUDA;
     h->started = true;
     return PIC_OK;
@@ -546,7 +590,8 @@ int init_run(pic_s *h, HostRun &hr, int idx)
     r.nsub = h->sort_sub;
     if ((long long)r.ntiles * r.nsub > (1ll << 30)) return PIC_EINVAL;
     r.tile_cnt = (int32_t *)dev_alloc(h, sizeof(int32_t) * ((size_t)r.ntiles * r.nsub + 1));
-    if (!r.rho0 || !hr.rho || !hr.rho32 || !r.mur || !r.tile_off || !r.tile_cnt) return PIC_ENOMEM;
+    r.fz = (uint8_t *)dev_alloc(h, (size_t)r.ntiles);
+    if (!r.rho0 || !hr.rho || !hr.rho32 || !r.mur || !r.tile_off || !r.tile_cnt || !r.fz) return PIC_ENOMEM;
     cudaError_t e = cudaSuccess;
     for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
         e = cudaMemsetAsync(r.E[a], 0, sizeof(float) * ncell, h->stream);
@@ -556,6 +601,7 @@ int init_run(pic_s *h, HostRun &hr, int idx)
     if (e == cudaSuccess) e = cudaMemsetAsync(r.rho0, 0, sizeof(double) * ncell, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(r.mur, 0, sizeof(float) * 8 * plane, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(r.tile_off, 0, sizeof(int32_t) * (r.ntiles + 1), h->stream);
+    if (e == cudaSuccess) e = flag_all_tiles(h, hr);
     if (e != cudaSuccess) return PIC_ECUDA;
     const pic_laser &L = c.laser;
     r.laser_on = L.enabled;
@@ -628,12 +674,14 @@ int create_common(const pic_config *cfgs, int n, pic_t **out)
     h->sort_sub = t.sort_sub ? t.sort_sub : 1;
     h->use_tma = t.tma > 0;
     h->adjoint_keep = t.adjoint_keep;
+    h->classify = t.stream_zero_tiles != 2;
     if (h->sort_sub < 1 || h->sort_sub > 32 || (h->sort_sub & (h->sort_sub - 1))) {
         delete h;
         return PIC_EINVAL;
     }
     h->push_smem = push_smem_bytes(h->dim, h->order, h->tile, h->drift, h->use_tma);
-    if (h->push_smem == 0) {  // (tile, drift) not among the compiled configurations
+    if (h->push_smem == 0 ||  // (tile, drift) not among the compiled configurations
+        !push_stage_extent(h->dim, h->order, h->tile, h->drift, h->use_tma, h->stage_lo, h->stage_len)) {
         delete h;
         return PIC_EINVAL;
     }
@@ -655,8 +703,9 @@ int create_common(const pic_config *cfgs, int n, pic_t **out)
     h->d_diag = (double *)dev_alloc(h, sizeof(double) * 16);
     h->d_count = (unsigned long long *)dev_alloc(h, sizeof(unsigned long long));
     h->d_queue = (int *)dev_alloc(h, sizeof(int));
+    h->d_cnt = (int *)dev_alloc(h, sizeof(int) * 4);
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (!h->d_runs || !h->d_states || !h->d_seg || !h->d_diag || !h->d_count || !h->d_queue) {
+    if (!h->d_runs || !h->d_states || !h->d_seg || !h->d_diag || !h->d_count || !h->d_queue || !h->d_cnt) {
         pic_destroy(h);
         return PIC_ENOMEM;
     }
@@ -904,6 +953,7 @@ int pic_write_fields(pic_t *h, int32_t which, const float *src, size_t n_elems, 
     int rc = read_state(h, h->cur, &st);
     if (rc) return rc;
     float *dstp = which < 3 ? hr.r.E[which] : hr.r.B[which - 3];
+    if (flag_all_tiles(h, hr) != cudaSuccess) return PIC_ECUDA;
     return copy_field(h, hr, st, dstp, const_cast<float *>(src), false, on_device);
 }
 
@@ -1011,7 +1061,7 @@ int pic_profile_begin(pic_t *h, int32_t max_steps)
 {
     if (!h || max_steps < 1) return PIC_EINVAL;
     for (cudaEvent_t ev : h->prof_events) cudaEventDestroy(ev);
-    h->prof_events.assign((size_t)max_steps * (PIC_NUM_PHASES + 1), nullptr);
+    h->prof_events.assign((size_t)max_steps * kEvPerStep, nullptr);
     for (auto &ev : h->prof_events)
         if (cudaEventCreate(&ev) != cudaSuccess) return PIC_ECUDA;
     h->prof_max = max_steps;
@@ -1028,10 +1078,12 @@ int pic_profile_end(pic_t *h, double *ms, int32_t n_phases, int64_t *launches)
     const int np = n_phases < PIC_NUM_PHASES ? n_phases : PIC_NUM_PHASES;
     for (int p = 0; p < n_phases; ++p) ms[p] = 0.0;
     for (int s = 0; s < h->prof_steps; ++s) {
-        cudaEvent_t *ev = &h->prof_events[(size_t)s * (PIC_NUM_PHASES + 1)];
+        cudaEvent_t *ev = &h->prof_events[(size_t)s * kEvPerStep];
         for (int p = 0; p < np; ++p) {
             float t = 0.f;
-            if (cudaEventElapsedTime(&t, ev[p], ev[p + 1]) != cudaSuccess) return PIC_ECUDA;
+            cudaError_t e = p == PIC_PH_PUSH_ZERO ? cudaEventElapsedTime(&t, ev[kMarkZero], ev[PIC_PH_YEE_B1])
+                                                  : cudaEventElapsedTime(&t, ev[p], ev[p + 1]);
+            if (e != cudaSuccess) return PIC_ECUDA;
             ms[p] += t;
         }
     }
@@ -1244,6 +1296,7 @@ int pic_adjoint_backward(pic_t *h, const pic_objective *obj, double *L, double *
             e = cudaMemcpyAsync(r.E[c], ck.E[c], sizeof(float) * nc, cudaMemcpyDeviceToDevice, st);
             if (e == cudaSuccess) e = cudaMemcpyAsync(r.B[c], ck.B[c], sizeof(float) * nc, cudaMemcpyDeviceToDevice, st);
         }
+        if (e == cudaSuccess) e = flag_all_tiles(h, h->runs[0]);
         if (e != cudaSuccess) return PIC_ECUDA;
         h->steps_done = s0;
         h->time_host = ck.time;

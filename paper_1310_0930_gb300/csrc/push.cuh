@@ -847,12 +847,176 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
     }
 }
 
+// ---------------------------------------------------------------- zero-field tiles
+// A tile whose staged field region holds only +0 values (ahead of a laser
+// front, or wherever the fields have not arrived yet) interpolates E = B = +0
+// at every one of its particles.  The Boris push then returns u unchanged
+// (every term adds or multiplies exact zeros; a zero momentum comes out as
+// +0), so a particle at rest stays where it is and deposits no current: its
+// step reads its state and writes it back.  Such tiles are streamed by this
+// kernel with 16-byte accesses (four consecutive slots per thread; the ragged
+// ends of a tile's range slot by slot) and no shared-memory tiles, so that
+// many CTAs per SM keep loads in flight.  A particle of such a tile that does
+// move takes the general slow path (the gather from global memory reads the
+// same zeros; the current goes to global memory by atomics) and is counted as
+// a slow-path particle.  Particles outside their tile's drift region cost
+// nothing here (no tile is staged) and are not counted as strays: the
+// adaptive sort counts the strays that slow the staged kernel down.
+constexpr int kZeroThreads = 256;
+
+struct ZeroCtx {
+    int origin, nl;
+    int last_shift;  // bit offset of the last axis in the packed cell
+};
+
+// One slot: absorption on an open last axis, the state of a particle at rest.
+// Returns true when the particle moves (u != 0) and needs the slow path.
+template <int DIM>
+__device__ __forceinline__ bool zero_slot(const Run &r, const ZeroCtx &z, int32_t &cell, float *u)
+{
+    if (cell < 0) return false;
+    if (r.open_last) {
+        int pl = (cell >> z.last_shift) - z.origin;
+        pl = pl < 0 ? pl + z.nl : pl;
+        if (pl < r.margin || pl >= z.nl - r.margin) {  // left the window: absorbed
+            cell = -1;
+            return false;
+        }
+    }
+    const bool rest = u[0] == 0.f && u[1] == 0.f && u[2] == 0.f;
+    if (rest) u[0] = u[1] = u[2] = 0.f;  // (+0, as the push computes it)
+    return !rest;
+}
+
+// The slow path for one moving particle of a zero-field tile (reloaded from
+// its slot, so that no other state lives across the call).
+template <int DIM, int P>
+__device__ __forceinline__ void zero_mover(const Run &r, const ZeroCtx &z, const ParticleBuf &pb, long long i)
+{
+    RunState *stp = r.state;
+    const GlobalFields gf{{r.E[0], r.E[1], r.E[2], r.B[0], r.B[1], r.B[2]}, r.n[0], r.n[1], DIM == 3 ? r.n[2] : 1};
+    int c[3];
+    unpack_cell(r, pb.cell[i], c[0], c[1], c[2]);
+    const float w = pb.w ? pb.w[i] : r.w_const;
+    const SlowOut so = advance_global<DIM, P>(r, gf, c[0], c[1], c[2], pb.off[0][i], pb.off[1][i],
+                                              DIM == 3 ? pb.off[2][i] : 0.f, pb.u[0][i], pb.u[1][i], pb.u[2][i], w);
+    if (!so.ok) {  // non-finite or over-long move: drop the particle, latch the status
+        pb.cell[i] = -1;
+        atomicOr(&stp->status, kStatusBadIndex);
+        return;
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) c[a] = wrapi(c[a] + so.k[a], r.n[a]);
+    bool absorbed = false;
+    if (r.open_last) {
+        int pl = c[DIM - 1] - z.origin;
+        pl = pl < 0 ? pl + z.nl : pl;
+        absorbed = pl < r.margin || pl >= z.nl - r.margin;
+    }
+    pb.cell[i] = absorbed ? -1 : pack_cell(r, c[0], c[1], DIM == 3 ? c[2] : 0);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) pb.off[a][i] = so.d[a];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) pb.u[a][i] = so.u[a];
+}
+
+template <int DIM, int P>
+__global__ void __launch_bounds__(kZeroThreads, 3) push_zero_kernel(const Run *__restrict__ runs,
+                                                                    const Item *__restrict__ list,
+                                                                    const int *__restrict__ count)
+{
+    __shared__ Run rs;
+    __shared__ unsigned s_slow;
+    const int n = *count;
+    int cur = -1;
+    for (int w = blockIdx.x; w < n; w += gridDim.x) {
+        const Item it = list[w];
+        __syncthreads();  // (the previous item is done with rs and the counter)
+        if (it.run != cur) {
+            const int *src = reinterpret_cast<const int *>(runs + it.run);
+            int *dst = reinterpret_cast<int *>(&rs);
+            for (int q = threadIdx.x; q < (int)(sizeof(Run) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
+            cur = it.run;
+        }
+        if (threadIdx.x == 0) s_slow = 0;
+        __syncthreads();
+        const Run &r = rs;
+        const RunState *stp = r.state;
+        const ParticleBuf pb = r.P[stp->buf];
+        ZeroCtx z;
+        z.origin = stp->origin;
+        z.nl = r.n[DIM - 1];
+        z.last_shift = DIM == 3 ? r.bits[0] + r.bits[1] : r.bits[0];
+        const int t = it.a;
+        const long long p0 = r.tile_off[t], p1 = r.tile_off[t + 1];
+        unsigned slow = 0;
+        // four consecutive slots per thread with 16-byte accesses where every
+        // array is 16-byte aligned; slot by slot elsewhere
+        uintptr_t al = (uintptr_t)pb.cell | (uintptr_t)pb.u[0] | (uintptr_t)pb.u[1] | (uintptr_t)pb.u[2];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) al |= (uintptr_t)pb.off[a];
+        long long v0 = (p0 + 3) & ~3ll, v1 = p1 & ~3ll;
+        if ((al & 15u) != 0 || v0 >= v1) v0 = v1 = p1;
+        for (long long g = (v0 >> 2) + threadIdx.x; g < (v1 >> 2); g += blockDim.x) {
+            int4 c4 = reinterpret_cast<const int4 *>(pb.cell)[g];
+            float4 o4[DIM], u4[3];
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) o4[a] = reinterpret_cast<const float4 *>(pb.off[a])[g];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) u4[a] = reinterpret_cast<const float4 *>(pb.u[a])[g];
+            int32_t cl[4] = {c4.x, c4.y, c4.z, c4.w};
+            float uu[4][3] = {{u4[0].x, u4[1].x, u4[2].x}, {u4[0].y, u4[1].y, u4[2].y},
+                              {u4[0].z, u4[1].z, u4[2].z}, {u4[0].w, u4[1].w, u4[2].w}};
+            unsigned movers = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) movers |= zero_slot<DIM>(r, z, cl[q], uu[q]) ? 1u << q : 0u;
+            // (a moving slot's values are written back unchanged; the slow path
+            // below then overwrites them)
+            reinterpret_cast<int4 *>(pb.cell)[g] = make_int4(cl[0], cl[1], cl[2], cl[3]);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) reinterpret_cast<float4 *>(pb.off[a])[g] = o4[a];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                reinterpret_cast<float4 *>(pb.u[a])[g] = make_float4(uu[0][a], uu[1][a], uu[2][a], uu[3][a]);
+            while (movers) {  // rare: a moving particle deposits, so its fields are soon non-zero
+                const int q = __ffs(movers) - 1;
+                movers &= movers - 1;
+                ++slow;
+                zero_mover<DIM, P>(r, z, pb, 4 * g + q);
+            }
+        }
+        // the ragged ends (and every slot when an array is not 16-byte aligned)
+        const long long ends = (v0 - p0) + (p1 - v1);
+        for (long long e = threadIdx.x; e < ends; e += blockDim.x) {
+            const long long i = e < v0 - p0 ? p0 + e : v1 + (e - (v0 - p0));
+            int32_t cl = pb.cell[i];
+            float uu[3] = {pb.u[0][i], pb.u[1][i], pb.u[2][i]};
+            const bool moves = zero_slot<DIM>(r, z, cl, uu);
+            pb.cell[i] = cl;
+            if (cl >= 0) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) pb.u[a][i] = uu[a];
+            }
+            if (moves) {
+                ++slow;
+                zero_mover<DIM, P>(r, z, pb, i);
+            }
+        }
+        if (slow) atomicAdd(&s_slow, slow);
+        __syncthreads();
+        if (threadIdx.x == 0 && s_slow) atomicAdd(&r.state->slow, (unsigned long long)s_slow);
+    }
+}
+
 // One CTA per item.  The persistent schedule is a kernel of its own so that
 // its loop state does not compete with the item body for registers.
+// live_cnt (may be null): the items past the first n_fixed are counted on
+// the device; CTAs past the count return at once.
 template <int DIM, int P, int TX, int TY, int TZ, int D, bool T>
 __global__ void __launch_bounds__(512) push_kernel(const Run *__restrict__ runs, const Item *__restrict__ items,
-                                                   int tail_block)
+                                                   int tail_block, int n_fixed, const int *__restrict__ live_cnt)
 {
+    if (live_cnt && (int)blockIdx.x >= n_fixed + *live_cnt) return;
     process_item<DIM, P, TX, TY, TZ, D, T>(runs, items[blockIdx.x], tail_block);
 }
 
@@ -861,9 +1025,10 @@ __global__ void __launch_bounds__(512) push_kernel(const Run *__restrict__ runs,
 template <int DIM, int P, int TX, int TY, int TZ, int D, bool T>
 __global__ void __launch_bounds__(512) push_queue_kernel(const Run *__restrict__ runs,
                                                          const Item *__restrict__ items, int nitems, int tail_block,
-                                                         int *queue)
+                                                         int *queue, const int *__restrict__ live_cnt)
 {
     __shared__ int s_item;
+    if (live_cnt) nitems += *live_cnt;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
         __syncthreads();
@@ -875,9 +1040,11 @@ __global__ void __launch_bounds__(512) push_queue_kernel(const Run *__restrict__
     }
 }
 
+// nitems: items of the launch (with live_cnt: the fixed leading items; the
+// device count of the others is added on the device, up to max_extra).
 template <int DIM, int P, int TX, int TY, int TZ, int D, bool T>
 cudaError_t launch_t(const Run *runs, const Item *items, int nitems, int block, int tail_block, int *queue,
-                     int persistent_ctas, cudaStream_t st)
+                     int persistent_ctas, cudaStream_t st, const int *live_cnt = nullptr, int max_extra = 0)
 {
     using G = Geo<DIM, P, TX, TY, TZ, D, T>;
     auto k = push_kernel<DIM, P, TX, TY, TZ, D, T>;
@@ -890,19 +1057,33 @@ cudaError_t launch_t(const Run *runs, const Item *items, int nitems, int block, 
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    if (nitems == 0) return cudaSuccess;
+    if (nitems + max_extra == 0) return cudaSuccess;
     if (queue) {
         int per_sm = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kq, block, G::SMEM);
         if (e != cudaSuccess) return e;
         int grid = persistent_ctas * (per_sm > 0 ? per_sm : 1);
-        grid = grid < nitems ? grid : nitems;
+        grid = grid < nitems + max_extra ? grid : nitems + max_extra;
         e = cudaMemsetAsync(queue, 0, sizeof(int), st);
         if (e != cudaSuccess) return e;
-        kq<<<grid, block, G::SMEM, st>>>(runs, items, nitems, tail_block, queue);
+        kq<<<grid, block, G::SMEM, st>>>(runs, items, nitems, tail_block, queue, live_cnt);
     } else {
-        k<<<nitems, block, G::SMEM, st>>>(runs, items, tail_block);
+        k<<<nitems + max_extra, block, G::SMEM, st>>>(runs, items, tail_block, nitems, live_cnt);
     }
+    return cudaGetLastError();
+}
+
+template <int DIM, int P>
+cudaError_t launch_zero(const Run *runs, const Item *list, const int *count, int max_items, int num_sms,
+                        cudaStream_t st)
+{
+    if (max_items <= 0) return cudaSuccess;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, push_zero_kernel<DIM, P>, kZeroThreads, 0);
+    if (e != cudaSuccess) return e;
+    int grid = num_sms * (per_sm > 0 ? per_sm : 1);
+    grid = grid < max_items ? grid : max_items;
+    push_zero_kernel<DIM, P><<<grid, kZeroThreads, 0, st>>>(runs, list, count);
     return cudaGetLastError();
 }
 

@@ -6,8 +6,7 @@
 
 namespace pic {
 
-cudaError_t launch_push_3d_tma(int order, const int *tile, int drift, const Run *runs, const Item *items, int nitems,
-                      int block, int tail_block, int *queue, int ctas, cudaStream_t st)
+cudaError_t launch_push_3d_tma(int order, const int *tile, int drift, const PushArgs &a, cudaStream_t st)
 {
     PIC_PUSH_MENU_3D_TMA(PIC_PUSH_CASE)
     return cudaErrorInvalidValue;
@@ -16,6 +15,12 @@ cudaError_t launch_push_3d_tma(int order, const int *tile, int drift, const Run 
 size_t smem_push_3d_tma(int order, const int *tile, int drift)
 {
     PIC_PUSH_MENU_3D_TMA(PIC_PUSH_SMEM)
+    return 0;
+}
+
+int stage_push_3d_tma(int order, const int *tile, int drift, int *lo, int *len)
+{
+    PIC_PUSH_MENU_3D_TMA(PIC_PUSH_STAGE)
     return 0;
 }
 

@@ -80,6 +80,7 @@ def make_config(w: Workload, *, tuning: Optional[dict] = None, track_ids=False, 
     cfg.tuning.tma = int(t.get("tma", 0))
     cfg.tuning.adjoint_keep = int(t.get("adjoint_keep", 0))
     cfg.tuning.sort_policy = int(t.get("sort_policy", 0))
+    cfg.tuning.stream_zero_tiles = int(t.get("stream_zero_tiles", 0))
     if alloc is not None:
         cfg.alloc = alloc
         cfg.free = free

@@ -137,3 +137,12 @@ def test_static_charge_entry_point_rejects_oversized_grid_without_device_work():
     g.dim = 4
     assert L.pic_charge_density_static(ctypes.byref(g), 2, -1.0, 1.0, 10, dummy, dummy, None, dummy, None) == \
         abi.PIC_EINVAL
+    # axes whose product wraps a 64-bit count to 0 (2^21 * 2^21 * 2^22 = 2^64)
+    # must be refused too, not pass the size check after the wrap
+    g.dim = 3
+    g.n[0], g.n[1], g.n[2] = 1 << 21, 1 << 21, 1 << 22
+    assert L.pic_charge_density_static(ctypes.byref(g), 2, -1.0, 1.0, 10, dummy, dummy, None, dummy, None) == \
+        abi.PIC_EINVAL
+    g.n[0], g.n[1], g.n[2] = 1 << 30, 1 << 30, 1 << 30
+    assert L.pic_charge_density_static(ctypes.byref(g), 2, -1.0, 1.0, 10, dummy, dummy, None, dummy, None) == \
+        abi.PIC_EINVAL

@@ -1,0 +1,116 @@
+"""Zero-field tiles: each step the device classifies the tiles, and those whose
+staged field region is all +0 (E = B = 0 at every particle) are advanced by a
+streaming kernel instead of the staged tile kernel.  The results must not
+depend on that choice: against the same run with every tile staged
+(stream_zero_tiles = 2), and against the FP64 oracle.
+
+Tolerances as in the other parity tests: fields relative L2 <= 1e-5 between
+the two device runs (only the order of the FP32 atomic current sums
+differs), <= 1e-4 against the oracle; particle and window-shift counts
+exact; particles at rest in zero fields bit-identical.
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import FIELD_NAMES, pair, rel_l2, smooth_fields
+from paper_1310_0930_gb300 import inputs
+from paper_1310_0930_gb300.sim import Simulation
+
+pytestmark = pytest.mark.gpu
+
+
+def _by_id(p):
+    order = np.argsort(p["id"])
+    return {k: (v[..., order] if isinstance(v, np.ndarray) else v) for k, v in p.items()}
+
+
+def test_lwfa_3d_streamed_tiles_equal_staged_and_oracle():
+    # the laser enters through the rear plane: the box ahead of its front is
+    # field-free, so most tiles are streamed until the window moves
+    w = inputs.lwfa_3d(n=(16, 16, 128), steps=60)
+    w.laser.a0, w.laser.waist, w.laser.fwhm = 1.5, 5.0, 6.0
+    w.window.t0 = 10.0
+    parts = inputs.background(w)
+    extra = 16 * 16 * 8 * 40
+    gpu, orc = pair(w, parts, extra=extra)
+    staged = Simulation(w, tuning={"stream_zero_tiles": 2}, track_ids=True)
+    staged.load(parts)
+    gpu.profile_begin(10)
+    gpu.step(10)
+    ph, _ = gpu.profile_end()
+    assert ph["push_zero"] > 0.0  # the streaming kernel ran
+    gpu.step(w.steps - 10)
+    staged.step(w.steps)
+    orc.step(w.steps)
+    d, ds = gpu.diagnostics(), staged.diagnostics()
+    assert d["shifts"] == ds["shifts"] == orc.shifts > 5
+    assert d["n_particles"] == ds["n_particles"] == orc.np
+    assert d["status"] == 0 and ds["status"] == 0
+    for name in FIELD_NAMES:
+        a = gpu.field(name).astype(np.float64)
+        assert rel_l2(a, staged.field(name)) <= 1e-5, name
+        assert rel_l2(a, orc.field(name)) <= 1e-4, name
+    # particles of the initial load by id (the window injects particles with id -1)
+    pa, pb = _by_id(gpu.particles()), _by_id(staged.particles())
+    assert np.array_equal(pa["id"], pb["id"])
+    keep = pa["id"] >= 0
+    assert keep.sum() > 0 and (~keep).sum() > 0
+    pa = {k: pa[k][..., keep] for k in ("id", "cell", "off", "u")}
+    pb = {k: pb[k][..., keep] for k in ("id", "cell", "off", "u")}
+    assert np.array_equal(pa["cell"], pb["cell"])
+    assert np.max(np.abs(pa["off"] - pb["off"])) <= 1e-5
+    assert np.max(np.abs(pa["u"] - pb["u"])) <= 1e-5 * max(1.0, float(np.max(np.abs(pb["u"]))))
+    gpu.close()
+    staged.close()
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_fields_written_into_a_streamed_region_are_gathered(order):
+    """A cold plasma in zero fields is streamed; fields written afterwards
+    from the host into half of the box must reach the particles there at the
+    next step (writing marks every tile live again)."""
+    w = inputs.thermal_3d(n=(32, 16, 16), order=order)
+    w.uth = 0.0
+    parts = inputs.background(w)
+    gpu, orc = pair(w, parts)
+    gpu.step(3)
+    orc.step(3)
+    p0 = _by_id(gpu.particles())
+    fields = smooth_fields(w, amp=0.05, seed=5)
+    half = np.zeros(tuple(reversed(w.n)), np.float32)
+    half[..., : w.n[0] // 2] = 1.0
+    for name, arr in fields.items():
+        v = (arr * half).astype(np.float32)
+        gpu.set_field(name, v)
+        orc.field(name)[...] = v.astype(np.float64)
+    gpu.step(2)
+    orc.step(2)
+    p1 = _by_id(gpu.particles())
+    moved = np.any(p1["u"] != p0["u"], axis=0)
+    assert moved.mean() > 0.3  # the particles in the written half felt the fields
+    _, uo, _ = orc.particles()  # (periodic box: the oracle keeps the load order, the ids)
+    ou = uo[:, p1["id"]]
+    scale = max(float(np.max(np.abs(ou))), 1e-30)
+    assert np.max(np.abs(p1["u"] - ou)) <= 1e-5 * scale
+    for name in FIELD_NAMES:
+        assert rel_l2(gpu.field(name), orc.field(name)) <= 1e-4, name
+    gpu.close()
+
+
+def test_cold_plasma_in_zero_fields_stays_bit_identical_when_streamed():
+    w = inputs.lwfa_3d(n=(16, 16, 64), steps=6, with_window=False)
+    w.laser = None
+    parts = inputs.background(w)
+    gpu = Simulation(w, track_ids=True)
+    gpu.load(parts)
+    p0 = _by_id(gpu.particles())
+    gpu.profile_begin(6)
+    gpu.step(6)
+    ph, _ = gpu.profile_end()
+    assert ph["push_zero"] > 0.0
+    p1 = _by_id(gpu.particles())
+    for k in ("cell", "off", "u"):
+        assert np.array_equal(p0[k], p1[k]), k
+    for name in FIELD_NAMES + ["Jx", "Jy", "Jz"]:
+        assert not np.any(gpu.field(name)), name
+    gpu.close()
