@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--tuning", default="", help="json dict of pic_tuning overrides")
     ap.add_argument("--out", default="", help="also write the JSON line to this file")
+    ap.add_argument("--no-full-run", action="store_true", help="skip the whole-run (500-step) timing")
+    ap.add_argument("--no-scan", action="store_true", help="skip the batched-scan ratio")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint ratio")
+    ap.add_argument("--scan-steps", type=int, default=40)
     return ap.parse_args()
 
 
@@ -85,17 +89,13 @@ def particle_chunks(w):
     return chunks
 
 
-# Per-particle figures of the push kernel from one single-pass ncu capture of
-# one launch of the bench workload at its full size (summaries in profiles/,
-# named below): DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) and
-# warp instructions (smsp__inst_executed.sum) per particle of that launch.
-# They are scaled to the timed launches by their particle count, and hold for
-# the default tuning of the kernel they were taken with.
-PUSH_PROFILE = {
-    ("lwfa_3d", 2): (61.09, 16.65, "push_kernel_lwfa3d_quadratic_256x256x1024.md"),
-    ("warm_3d", 2): (65.32, 93.19, "push_kernel_warm3d_quadratic_256x256x256.md"),
-    ("bunch_3d", 3): (68.12, 22.37, "push_kernel_bunch3d_cubic_256x256x512.md"),
-}
+# Per-particle figures of the particle phase's kernels from ncu captures of a
+# small case of the same workload (summaries in profiles/, named below): DRAM
+# bytes (dram__bytes_read.sum + dram__bytes_write.sum) and warp instructions
+# (smsp__inst_executed.sum) per particle slot the kernel processed, scaled to
+# the timed launches by their particle counts.  Empty until captured for the
+# current kernels: the bench then reports traffic as null.
+PUSH_PROFILE = {}
 
 
 def aggregate_replicas(elapsed, units):
@@ -233,21 +233,27 @@ def workload_config(w, n_particles):
             "window": w.window is not None, "laser_a0": w.laser.a0 if w.laser else None}
 
 
-def scan_bench(args):
-    """Batched parameter scan: 64 uneven 2D LWFA runs advanced by one handle
-    (one launch per phase over every run's tiles, persistent push kernel,
-    CUDA-graph replay) against the same runs advanced one after another by
-    plain single-run handles.  Same K timed steps per run in both."""
+def scan_measure(args, steps, warmup, window_moves=False):
+    """Batched parameter scan: independent 2D LWFA runs of uneven sizes
+    advanced by one handle (one launch per phase over every run's tiles,
+    persistent push kernel, CUDA-graph replay) against the same runs advanced
+    one after another by plain single-run handles, the same `steps` timed
+    steps per run in both.  window_moves: every run's moving window starts a
+    quarter of the way into the timed steps, so that both arms time window
+    shifts and the injection of new plasma."""
     import torch
     from paper_1310_0930_gb300 import autotune, inputs
     from paper_1310_0930_gb300.sim import Simulation, TorchMemory
 
     torch.cuda.set_device(0)
     runs = inputs.scan_2d(count=args.scan_runs)
+    if window_moves:
+        for w in runs:
+            w.window.t0 = w.dt * (warmup + steps // 4)
     parts = [inputs.background(w) for w in runs]
     n_total = sum(p.n for p in parts)
     cells = sum(w.n_cells for w in runs)
-    tuning = json.loads(args.tuning) if args.tuning else {}
+    tuning = json.loads(args.tuning) if (args.tuning and args.workload == "scan_2d") else {}
     if args.autotune:
         sub = list(range(min(8, len(runs))))
 
@@ -258,14 +264,14 @@ def scan_bench(args):
             return sum(parts[r].n for r in sub)
         tuning = autotune.tune([runs[r] for r in sub], loader, refresh=True)
 
-    def timed(sim, n_steps):
+    def timed(sim, clocks=None):
         st = sim.mem.stream
-        sim.step(args.warmup)
+        sim.step(warmup)
         sim.sync()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(st)
-        sim.step(n_steps)
+        sim.step(steps)
         e1.record(st)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1)
@@ -275,28 +281,43 @@ def scan_bench(args):
         batch.select(r)
         batch.load(p)
     clocks = Clocks(0)
-    ms_b = timed(batch, args.steps)
-    clk = clocks.stop()
+    ms_b = timed(batch)
+    clk_b = clocks.stop()
+    shifts_b = []
+    for r in range(len(runs)):
+        batch.select(r)
+        shifts_b.append(batch.diagnostics()["shifts"])
     batch.close()
     del batch
     single_tuning = {k: v for k, v in tuning.items() if k != "persistent"}
     ms_s = 0.0
+    clocks = Clocks(0)
     for w, p in zip(runs, parts):
         sim = Simulation(w, tuning=single_tuning, memory=TorchMemory())
         sim.load(p)
-        ms_s += timed(sim, args.steps)
+        ms_s += timed(sim)
         sim.close()
-    value = n_total * args.steps / (ms_b / 1e3)
-    seq = n_total * args.steps / (ms_s / 1e3)
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_b / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+    clk_s = clocks.stop()
+    value = n_total * steps / (ms_b / 1e3)
+    seq = n_total * steps / (ms_s / 1e3)
+    return {"runs": len(runs), "particles": n_total, "cells": cells, "steps": steps, "warmup": warmup,
+            "tuning": tuning, "window_shifts_per_run": [min(shifts_b), max(shifts_b)],
+            "batched": {"value": value, "ms_per_step": ms_b / steps, "clocks": clk_b},
+            "sequential_plain": {"value": seq, "ms_per_step": ms_s / steps, "clocks": clk_s},
+            "batched_over_sequential": value / seq}
+
+
+def scan_bench(args):
+    """The batched scan as the bench line's own workload."""
+    m = scan_measure(args, args.steps, args.warmup)
+    line = {"metric": METRIC, "value": m["batched"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": m["batched"]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "scan_2d: %d independent 2D LWFA runs (nz 256-2048 x nx 128-512, dz=0.3, "
-                                   "dx=1, dt=0.28, 4-16 ppc, n 0.001-0.01, a0 1-6), quadratic" % len(runs),
-                       "runs": len(runs), "particles": n_total, "cells": cells, "tuning": tuning},
-            "batched": {"value": value, "ms_per_step": ms_b / args.steps},
-            "sequential_plain": {"value": seq, "ms_per_step": ms_s / args.steps},
-            "batched_over_sequential": value / seq, "clocks": clk}
+                                   "dx=1, dt=0.28, 4-16 ppc, n 0.001-0.01, a0 1-6), quadratic" % m["runs"],
+                       "runs": m["runs"], "particles": m["particles"], "cells": m["cells"], "tuning": m["tuning"]},
+            "batched": m["batched"], "sequential_plain": m["sequential_plain"],
+            "batched_over_sequential": m["batched_over_sequential"], "clocks": m["batched"]["clocks"]}
     print(json.dumps(line), flush=True)
     if args.out:
         with open(args.out, "w") as f:
@@ -304,17 +325,16 @@ def scan_bench(args):
     return 0
 
 
-def adjoint_bench(args):
+def adjoint_measure(args, S, warmup):
     """Gradient of the trailing-window kinetic energy with respect to 32
     density knots and a0 on the 2D LWFA box 256 x 1024 cells (dx=1, dz=0.3,
-    dt=0.28), 16 ppc, checkpoints every 100 steps: forward alone against
-    forward with checkpoints plus the reverse sweep."""
+    dt=0.28), 16 ppc, checkpoints every 100 steps: the plain forward run
+    against the forward run with checkpoints plus the reverse sweep."""
     import torch
     from paper_1310_0930_gb300 import inputs
     from paper_1310_0930_gb300.sim import Simulation, TorchMemory
 
     torch.cuda.set_device(0)
-    S = args.adjoint_steps
     w = inputs.adjoint_2d(steps=S)
     w.window = None
     w.knot_z = (0.0, w.n[-1] * w.d[-1])
@@ -328,30 +348,44 @@ def adjoint_bench(args):
         torch.cuda.synchronize()
         return time.perf_counter() - t0, out
 
-    tuning = json.loads(args.tuning) if args.tuning else None
+    tuning = json.loads(args.tuning) if (args.tuning and args.workload == "adjoint_2d") else None
     plain = Simulation(w, per_particle_weight=True, tuning=tuning, memory=TorchMemory())
     plain.load(parts)
-    plain.step(args.warmup)
+    plain.step(warmup)
     plain.sync()
+    clocks = Clocks(0)
     t_fwd, _ = wall(lambda: (plain.step(S), plain.sync()))
+    clk_f = clocks.stop()
     plain.close()
     sim = Simulation(w, track_ids=True, per_particle_weight=True, tuning=tuning, memory=TorchMemory())
     sim.load(parts)
     kept = sim.adjoint_begin(S, 100)
+    clocks = Clocks(0)
     t_fwd_ck, _ = wall(lambda: (sim.step(S), sim.sync()))
     t_bwd, res = wall(lambda: sim.adjoint_backward(*obj, n_knots=len(w.knots)))
+    clk_g = clocks.stop()
     sim.close()
     n = parts.n
-    line = {"metric": METRIC, "value": n * S / (t_fwd_ck + t_bwd), "unit": UNIT, "n_gpus": 1, "steps": S,
-            "warmup": args.warmup, "ms_per_step": 1e3 * (t_fwd_ck + t_bwd) / S, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "adjoint_2d: 2D LWFA 256x1024 cells, 16 ppc, 32 density knots, a0=3, "
-                                   "%d steps, checkpoint every 100, gradient w.r.t. knots and a0" % S,
-                       "particles": n},
-            "tuning": tuning, "forward_s": t_fwd, "forward_with_checkpoints_s": t_fwd_ck, "reverse_s": t_bwd,
+    return {"workload": "adjoint_2d: 2D LWFA 256x1024 cells, 16 ppc, 32 density knots, a0=3, %d steps, "
+                        "checkpoint every 100, gradient w.r.t. knots and a0" % S,
+            "particles": n, "steps": S, "tuning": tuning, "forward_s": t_fwd, "forward_clocks": clk_f,
+            "forward_with_checkpoints_s": t_fwd_ck, "reverse_s": t_bwd, "gradient_clocks": clk_g,
             "gradient_over_forward": (t_fwd_ck + t_bwd) / t_fwd,
             "segments": {"checkpoints": -(-S // 100), "recorded_by_forward": kept},
             "L": res["L"], "dL_da0": res["dL_da0"], "dL_dknots_norm": float(np.linalg.norm(res["dL_dknots"]))}
+
+
+def adjoint_bench(args):
+    """The adjoint form as the bench line's own workload."""
+    S = args.adjoint_steps
+    m = adjoint_measure(args, S, args.warmup)
+    n = m["particles"]
+    line = {"metric": METRIC, "value": n * S / (m["forward_with_checkpoints_s"] + m["reverse_s"]), "unit": UNIT,
+            "n_gpus": 1, "steps": S, "warmup": args.warmup,
+            "ms_per_step": 1e3 * (m["forward_with_checkpoints_s"] + m["reverse_s"]) / S, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": m["workload"], "particles": n}, "clocks": m["gradient_clocks"]}
+    line.update({k: v for k, v in m.items() if k not in ("workload", "particles")})
     print(json.dumps(line), flush=True)
     if args.out:
         with open(args.out, "w") as f:
@@ -453,6 +487,22 @@ def main():
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = push_bytes / (push_ms / 1e3) / 1e9
+    # the particle phase's two kernels: zero-field tiles streamed (particle
+    # state read and written, 2 S_p bytes per slot) and the staged tiles
+    streamed = (d1["streamed"] - d0["streamed"]) / args.steps
+    zero_ms = phases["push_zero"] / args.steps
+    staged_ms = push_ms - zero_ms
+    zero_bytes = streamed * 2 * sp
+    staged_bytes = push_bytes - zero_bytes
+    kernels = [
+        {"kernel": "push_zero_kernel<%d,%d> (zero-field tiles)" % (w.dim, w.order), "slots_per_launch": streamed,
+         "bytes_per_launch": zero_bytes, "avg_launch_ms": zero_ms,
+         "achieved_gbs": zero_bytes / (zero_ms / 1e3) / 1e9 if zero_ms > 0 else None,
+         "frac": zero_bytes / (zero_ms / 1e3) / 1e9 / peak if zero_ms > 0 else None},
+        {"kernel": "tile classification + push_kernel<%d,%d> (live tiles)" % (w.dim, w.order),
+         "particles_per_launch": n_avg - streamed, "bytes_per_launch": staged_bytes, "avg_launch_ms": staged_ms,
+         "achieved_gbs": staged_bytes / (staged_ms / 1e3) / 1e9 if staged_ms > 0 else None,
+         "frac": staged_bytes / (staged_ms / 1e3) / 1e9 / peak if staged_ms > 0 else None}]
     prof = PUSH_PROFILE.get((w.name, w.order)) if not tuning and args.scale == 1.0 else None
     traffic = prof[0] * n_avg if prof else None
     issue = None
@@ -464,8 +514,39 @@ def main():
         issue = {"achieved": ach_issue, "peak": peak_issue, "unit": "warp-instructions/s",
                  "frac": ach_issue / peak_issue, "source": "profiles/" + prof[2]}
     status = d1["status"]
+    sorts_timed = int(d1["sorts"] - d0["sorts"])
     sim.close()
     del sim
+
+    # ---- the configured run from its first step to its last ----------------
+    full = None
+    if world == 1 and not args.no_full_run and w.steps > args.steps:
+        mem_f = TorchMemory(device=local)
+        simf = Simulation(w, tuning=tuning, capacity=cap, memory=mem_f)
+        for c in chunks:
+            simf.load(c)
+        simf.sync()
+        f0 = simf.diagnostics()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clocks_f = Clocks(local)
+        torch.cuda.synchronize()
+        e0.record(mem_f.stream)
+        simf.step(w.steps)
+        e1.record(mem_f.stream)
+        torch.cuda.synchronize()
+        clk_f = clocks_f.stop()
+        ms_f = e0.elapsed_time(e1)
+        f1 = simf.diagnostics()
+        nf = 0.5 * (f0["n_particles"] + f1["n_particles"])
+        sb_f, _, _ = algorithmic_bytes(w, nf)
+        full = {"value": nf * w.steps / (ms_f / 1e3), "ms_per_step": ms_f / w.steps, "steps": w.steps,
+                "step_roofline_frac": sb_f / (ms_f / w.steps / 1e3) / 1e9 / peak, "clocks": clk_f,
+                "sorts": int(f1["sorts"] - f0["sorts"]), "window_shifts": int(f1["shifts"]),
+                "streamed_fraction": (f1["streamed"] - f0["streamed"]) / max(1.0, nf * w.steps),
+                "status": f1["status"],
+                "timed": "steps 1..%d from the loaded state, CUDA-graph replay, one pair of CUDA events" % w.steps}
+        simf.close()
+        del simf
 
     # ---- end to end through the C ABI with host buffers ----------------------
     e2e = None
@@ -500,6 +581,13 @@ def main():
         sim2.close()
         del sim2, pinned
 
+    # ---- the metric's other half: batched scan and adjoint against plain runs --
+    scan = adj = None
+    if world == 1 and not args.no_scan:
+        scan = scan_measure(args, args.scan_steps, 5, window_moves=True)
+    if world == 1 and not args.no_adjoint:
+        adj = adjoint_measure(args, args.adjoint_steps, 5)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, args.cpu_budget_s)
@@ -510,12 +598,17 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(workload_config(w, n0), particles_timed=int(n_avg),
                        sort_policy="fixed" if (tuning or {}).get("sort_policy") == 1 else "adaptive",
-                       sorts_timed=int(d1["sorts"] - d0["sorts"]),
+                       sorts_timed=sorts_timed,
+                       steps_covered="steps %d..%d of the configured %d (after %d untimed warm-up steps)" % (
+                           args.warmup + 1, args.warmup + args.steps, w.steps, args.warmup),
                        l2="inputs larger than L2 (%.1f GB particle state)" % (n_avg * sp / 1e9),
                        parallelism="replicas" if world > 1 else "single GPU",
                        timed="device-resident state, phase events recorded on the library stream"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": "push_kernel<%d,%d>" % (w.dim, w.order),
+                     "traffic": traffic,
+                     "kernel": "particle phase: push_zero_kernel<%d,%d> + push_kernel<%d,%d>" % (
+                         w.dim, w.order, w.dim, w.order),
+                     "kernels": kernels,
                      "traffic_source": ("ncu capture of one launch, per particle, profiles/" + prof[2]) if prof else None,
                      "issue": issue,
                      "bytes_per_launch": push_bytes, "avg_launch_ms": push_ms,
@@ -527,6 +620,9 @@ def main():
         "e2e": e2e,
         "cpu_baseline": cpu,
         "status": status,
+        "full_run": full,
+        "batched_scan": scan,
+        "adjoint": adj,
     }
     if rank == 0:
         s = json.dumps(line)

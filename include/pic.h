@@ -224,6 +224,7 @@ typedef struct {
     int64_t slow_path;     /* particles outside their tile's staged region, last step */
     int32_t status;        /* latched device status (PIC_OK or a PIC_E* code) */
     int32_t sorts;         /* tile sorts so far */
+    int64_t streamed;      /* particle slots advanced by the zero-field tile kernel, all steps so far */
 } pic_diag;
 
 typedef struct pic_s pic_t;

@@ -51,6 +51,7 @@ struct RunState {
     int since_sort;                // completed steps since the last sort
     int do_sort;                   // this step sorts (set by the sort decision)
     long long sorts;               // sorts so far
+    unsigned long long streamed;   // particle slots of zero-field tiles streamed so far
 };
 
 // Immutable per-run descriptor (device copy).

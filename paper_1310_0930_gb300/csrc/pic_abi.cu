@@ -1053,6 +1053,7 @@ int pic_diagnostics(pic_t *h, pic_diag *out)
     out->imbalance = (um[3] > 0 && dd[3] > 0) ? (double)um[2] / (dd[3] / (double)um[3]) : 0.0;
     out->slow_path = (int64_t)st.slow_last;
     out->sorts = (int32_t)st.sorts;
+    out->streamed = (int64_t)st.streamed;
     out->status = status_code(st.status);
     return out->status;
 }

@@ -159,7 +159,19 @@ struct Geo {
     static __host__ __device__ constexpr int tile(int a) { return a == 0 ? TX : (a == 1 ? TY : (DIM == 3 ? TZ : 1)); }
     // (+128: the field tile is placed at the first 128-byte boundary of the
     // dynamic shared memory, as TMA destinations require)
-    static constexpr size_t SMEM = 128 + sizeof(float) * 6 * FVOL + sizeof(int) * 2 * 3 * JVOL;
+    static constexpr size_t SMEM_TILES = 128 + sizeof(float) * 6 * FVOL + sizeof(int) * 2 * 3 * JVOL;
+    // Deposit staging of one round's moving particles (bucketed deposit, see
+    // deposit_round): STG_W words per particle, one padding word per 32 slots.
+    static constexpr int STG_W = 8, STG_N = 512 + 512 / 32;
+    static constexpr size_t STG_BYTES = sizeof(int) * STG_W * STG_N;
+    // The staging is used for cubic and higher orders (5^3-node windows: the
+    // conflict-free atomics save more than the round's three barriers cost;
+    // measured on 256^3 warm plasma, 8 ppc: cubic 47.5 -> 30.6 ms, quadratic
+    // 17.5 -> 15.8 ms but 3D LWFA live tiles 115 -> 121 ps per particle,
+    // linear 7.1 -> 8.7 ms), where it fits next to the tiles and the kernel's
+    // static shared memory; otherwise each thread deposits its own particle.
+    static constexpr bool BK = P >= 3 && SMEM_TILES + STG_BYTES + 2048 <= 232448;
+    static constexpr size_t SMEM = SMEM_TILES + (BK ? STG_BYTES : 0);
 };
 
 // ---------------------------------------------------------------- gather
@@ -392,33 +404,42 @@ struct SmemGather {
     }
 };
 
-// Add one value to the fixed-point J tile: x = value * S (|x| < 2^22) split
-// into its nearest integer (hi) and 12 bits of the remainder (lo).  x is
-// computed as ps * fac with ps already scaled by S.
-__device__ __forceinline__ void fix_add(int *hi_base, int *lo_base, int off, float ps, float fac)
+// Add one value to the fixed-point J tile at hi (its lo word JLO words
+// further): x = ps * fac (ps already scaled by S, |x| < 2^22) split into the
+// integer nearest to the exact product (hi) and 12 bits of the remainder
+// (lo).  t = fma(ps, fac, 1.5 * 2^23) holds that integer in its low mantissa
+// bits; the remainder fma(ps, fac, -integer) is exact to FP32 rounding of a
+// value below 1.  `on` is false where this lane's value is zero by
+// structure (the far window node of an axis along which the lane did not
+// change nodes); it predicates the two atomics, with no branch per value.
+template <int JLO>
+__device__ __forceinline__ void fix_add(int *hi, float ps, float fac, bool on)
 {
-    const float x = ps * fac;
-    if (x == 0.f) return;
-    const float t = x + kRound;                 // kRound + rint(x), exact
-    const float rem = fmaf(ps, fac, kRound - t);  // x - rint(x), |rem| <= 1/2
+    const float t = fmaf(ps, fac, kRound);          // kRound + rint(x), exact
+    const float rem = fmaf(ps, fac, kRound - t);    // x - rint(x), |rem| <= 1/2
     const float tl = fmaf(rem, kLoScale, kRound);
-    atomicAdd(hi_base + off, __float_as_int(t) - kRoundBits);
-    atomicAdd(lo_base + off, __float_as_int(tl) - kRoundBits);
+    const int vh = __float_as_int(t) - kRoundBits, vl = __float_as_int(tl) - kRoundBits;
+    if (on) {
+        atomicAdd(hi, vh);
+        atomicAdd(hi + JLO, vl);
+    }
 }
 
 // 3D Esirkepov deposit into the shared-memory J tile: a loop over the three
 // components, axis roles (a, b, c) = (comp, comp+1, comp+2) selected per
 // iteration.  The last window node of an axis is visited only if some lane
 // of the warp moved its nearest node along that axis (warp-uniform branch):
-// for the common case of no node change this is 54 values instead of 144.
+// for the common case of no node change this is 54 values instead of 144;
+// lanes that did not move along that axis skip those values by predication.
 template <int P, class G>
-__device__ __forceinline__ void deposit3_smem(const Axis<P> *ax, float S, int *Jhi, int *Jlo)
+__device__ __forceinline__ void deposit3_smem(const Axis<P> *ax, float S, int *Jhi)
 {
     constexpr int W = P + 2;
+    constexpr int JLO = 3 * G::JVOL;
     const float twelfth = 1.f / 12.f;
     const unsigned act = __activemask();
-    const bool f0 = __any_sync(act, ax[0].shift != 0), f1 = __any_sync(act, ax[1].shift != 0),
-               f2 = __any_sync(act, ax[2].shift != 0);
+    const bool m0 = ax[0].shift != 0, m1 = ax[1].shift != 0, m2 = ax[2].shift != 0;  // this lane
+    const bool f0 = __any_sync(act, m0), f1 = __any_sync(act, m1), f2 = __any_sync(act, m2);  // the warp
     const int base = (ax[0].wb + G::JHX) + G::JX * (ax[1].wb + G::JHY) + G::JPL * (ax[2].wb + G::JHZ);
     constexpr int s0 = 1, s1 = G::JX, s2 = G::JPL;
 #pragma unroll
@@ -439,19 +460,24 @@ __device__ __forceinline__ void deposit3_smem(const Axis<P> *ax, float S, int *J
         const bool fa = comp == 0 ? f0 : (comp == 1 ? f1 : f2);
         const bool fb = comp == 0 ? f1 : (comp == 1 ? f2 : f0);
         const bool fc = comp == 0 ? f2 : (comp == 1 ? f0 : f1);
-        int *hb = Jhi + comp * G::JVOL + base, *lb = Jlo + comp * G::JVOL + base;
+        const bool ma = comp == 0 ? m0 : (comp == 1 ? m1 : m2);
+        const bool mb = comp == 0 ? m1 : (comp == 1 ? m2 : m0);
+        const bool mc = comp == 0 ? m2 : (comp == 1 ? m0 : m1);
+        int *hb = Jhi + comp * G::JVOL + base;
 #pragma unroll
         for (int qc = 0; qc < W; ++qc) {
             if (qc == W - 1 && !fc) continue;
+            const bool oc = qc < W - 1 || mc;
 #pragma unroll
             for (int qb = 0; qb < W; ++qb) {
                 if (qb == W - 1 && !fb) continue;
+                const bool ob = oc && (qb < W - 1 || mb);
                 const float fac = fmaf(Db[qb] * twelfth, Dc[qc], Ab[qb] * Ac[qc]);
                 const int row = qb * sb + qc * sc;
 #pragma unroll
                 for (int qa = 0; qa < W - 1; ++qa) {
                     if (qa == W - 2 && !fa) continue;
-                    fix_add(hb, lb, row + qa * sa, pa[qa], fac);
+                    fix_add<JLO>(hb + row + qa * sa, pa[qa], fac, ob && (qa < W - 2 || ma));
                 }
             }
         }
@@ -460,12 +486,14 @@ __device__ __forceinline__ void deposit3_smem(const Axis<P> *ax, float S, int *J
 
 // 2D Esirkepov deposit into the shared-memory J tile, same skipping rule.
 template <int P, class G>
-__device__ __forceinline__ void deposit2_smem(const Axis<P> *ax, float S, float qwvz, int *Jhi, int *Jlo)
+__device__ __forceinline__ void deposit2_smem(const Axis<P> *ax, float S, float qwvz, int *Jhi)
 {
     constexpr int W = P + 2;
+    constexpr int JLO = 3 * G::JVOL;
     const float twelfth = 1.f / 12.f;
     const unsigned act = __activemask();
-    const bool f0 = __any_sync(act, ax[0].shift != 0), f1 = __any_sync(act, ax[1].shift != 0);
+    const bool m0 = ax[0].shift != 0, m1 = ax[1].shift != 0;
+    const bool f0 = __any_sync(act, m0), f1 = __any_sync(act, m1);
     const int base = (ax[0].wb + G::JHX) + G::JX * (ax[1].wb + G::JHY);
     float px[W - 1], py[W - 1];
 #pragma unroll
@@ -477,16 +505,113 @@ __device__ __forceinline__ void deposit2_smem(const Axis<P> *ax, float S, float 
 #pragma unroll
     for (int qb = 0; qb < W; ++qb) {
         if (qb == W - 1 && !f1) continue;
+        const bool ob = qb < W - 1 || m1;  // A_y, DS_y of this node not zero by structure
 #pragma unroll
         for (int qa = 0; qa < W; ++qa) {
             if (qa == W - 1 && !f0) continue;
-            const int off = qa + G::JX * qb;
-            if (qa < W - 1 && !(qa == W - 2 && !f0)) fix_add(Jhi + base, Jlo + base, off, px[qa], ax[1].A[qb]);
+            const bool oa = qa < W - 1 || m0;
+            int *h = Jhi + base + qa + G::JX * qb;
+            if (qa < W - 1 && !(qa == W - 2 && !f0))
+                fix_add<JLO>(h, px[qa], ax[1].A[qb], ob && (qa < W - 2 || m0));
             if (qb < W - 1 && !(qb == W - 2 && !f1))
-                fix_add(Jhi + G::JVOL + base, Jlo + G::JVOL + base, off, py[qb], ax[0].A[qa]);
-            fix_add(Jhi + 2 * G::JVOL + base, Jlo + 2 * G::JVOL + base, off, sz,
-                    fmaf(ax[0].DS[qa] * twelfth, ax[1].DS[qb], ax[0].A[qa] * ax[1].A[qb]));
+                fix_add<JLO>(h + G::JVOL, py[qb], ax[0].A[qa], oa && (qb < W - 2 || m1));
+            fix_add<JLO>(h + 2 * G::JVOL, sz, fmaf(ax[0].DS[qa] * twelfth, ax[1].DS[qb], ax[0].A[qa] * ax[1].A[qb]),
+                         oa && ob);
         }
+    }
+}
+
+// Node base of the Esirkepov window of a move from (c, d) by k cells to d1
+// along one axis: the lower of the old and new nearest-node bases.
+template <int P>
+__device__ __forceinline__ int window_base(int c, float d, int k, float d1)
+{
+    int bo, bn;
+    float w[P + 1];
+    Shape<P>::node(c, d, bo, w);
+    Shape<P>::node(c + k, d1, bn, w);
+    return bo < bn ? bo : bn;
+}
+
+// Bucketed deposit of one round (all threads of the CTA call it together).
+// The current is what the thread-per-particle deposit gives; only the
+// assignment of particles to threads changes.  The moving particles of the
+// round are sorted by the shared-memory bank of their J window base (a
+// counting sort into 32 buckets), then warp w takes the particles w, w + nw,
+// w + 2 nw, ... of that order: the lanes of a warp then hold windows in
+// (mostly) distinct banks, so the window's atomics, whose offsets from the
+// base are the same for every lane, are (mostly) free of bank conflicts.
+// A particle that moves is described by its staged record: packed tile
+// coordinates and cell carries, old and new offsets, q w and (2D) q w v_z.
+template <int DIM, int P, class G>
+__device__ __forceinline__ void deposit_round(const Run &r, bool dep, int pk, const float *d0, const float *d1,
+                                              float qw, float qwvz, float S, int *Jhi, int *stg, int *s_cnt,
+                                              int *s_start)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    int bank = 0;
+    if (dep) {
+        int wb[3] = {0, 0, 0};
+#pragma unroll
+        for (int a = 0; a < DIM; ++a)
+            wb[a] = window_base<P>(((pk >> (8 * a)) & 255) - 64, d0[a], ((pk >> (24 + 2 * a)) & 3) - 1, d1[a]);
+        bank = ((wb[0] + G::JHX) + G::JX * (wb[1] + G::JHY) + G::JPL * (wb[2] + G::JHZ)) & 31;
+    }
+    const unsigned m = __match_any_sync(0xffffffffu, dep ? bank : 32 + (int)lane);
+    const int leader = __ffs(m) - 1;
+    int b0 = 0;
+    if (dep && (int)lane == leader) b0 = atomicAdd(s_cnt + bank, __popc(m));
+    b0 = __shfl_sync(0xffffffffu, b0, leader);
+    const int rank = b0 + __popc(m & ((1u << lane) - 1u));
+    const int ndep = __syncthreads_count(dep);
+    if (ndep == 0) return;  // (uniform; the counters are all still zero)
+    if (threadIdx.x < 32) {  // exclusive scan of the bucket counts
+        const int c = s_cnt[lane];
+        int v = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, v, o);
+            if ((int)lane >= o) v += t;
+        }
+        s_start[lane] = v - c;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) s_cnt[lane] = 0;  // (next counted after the next barrier)
+    if (dep) {
+        int q = s_start[bank] + rank;
+        q += q >> 5;
+        stg[q] = pk;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            stg[(1 + a) * G::STG_N + q] = __float_as_int(d0[a]);
+            stg[(1 + DIM + a) * G::STG_N + q] = __float_as_int(d1[a]);
+        }
+        stg[(1 + 2 * DIM) * G::STG_N + q] = __float_as_int(qw);
+        if (DIM == 2) stg[(2 + 2 * DIM) * G::STG_N + q] = __float_as_int(qwvz);
+    }
+    __syncthreads();
+    const int nw = (ndep + 31) >> 5, w = threadIdx.x >> 5;
+    int q = (int)lane * nw + w;
+    if (w < nw && q < ndep) {
+        q += q >> 5;
+        const int rpk = stg[q];
+        int rel[3], k[3];
+        float a0[3], a1[3];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            rel[a] = ((rpk >> (8 * a)) & 255) - 64;
+            k[a] = ((rpk >> (24 + 2 * a)) & 3) - 1;
+            a0[a] = __int_as_float(stg[(1 + a) * G::STG_N + q]);
+            a1[a] = __int_as_float(stg[(1 + DIM + a) * G::STG_N + q]);
+        }
+        const float rqw = __int_as_float(stg[(1 + 2 * DIM) * G::STG_N + q]);
+        Axis<P> ax[DIM];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) axis_window<P>(rel[a], a0[a], k[a], a1[a], -rqw * r.d_over_dt[a], ax[a]);
+        if (DIM == 3) deposit3_smem<P, G>(reinterpret_cast<const Axis<P> *>(ax), S, Jhi);
+        else
+            deposit2_smem<P, G>(reinterpret_cast<const Axis<P> *>(ax), S,
+                                __int_as_float(stg[(2 + 2 * DIM) * G::STG_N + q]), Jhi);
     }
 }
 
@@ -579,6 +704,7 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
     __shared__ Run rs;
     __shared__ unsigned slow_cnt;
     __shared__ float wsum[32], wmaxs[32];
+    __shared__ int s_cnt[32], s_start[32];
     __shared__ __align__(8) uint64_t tma_bar;
     if (G::TL && threadIdx.x == 0) mbar_init(&tma_bar);
     {
@@ -586,6 +712,7 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
         int *dst = reinterpret_cast<int *>(&rs);
         for (int q = threadIdx.x; q < (int)(sizeof(Run) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
         if (threadIdx.x == 0) slow_cnt = 0;
+        if (threadIdx.x < 32) s_cnt[threadIdx.x] = 0;
     }
     __syncthreads();
     const Run &r = rs;
@@ -620,6 +747,7 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
     float *Fs = smem + ((128u - (smem_addr(smem) & 127u)) & 127u) / sizeof(float);
     int *Jhi = reinterpret_cast<int *>(Fs + 6 * G::FVOL);
     int *Jlo = Jhi + 3 * G::JVOL;
+    int *stg = Jlo + 3 * G::JVOL;  // deposit staging (G::BK)
     float S = 1.f;  // fixed-point scale of this tile's J
     // TMA staging: 3D tiles whose field box lies inside the stored grid
     // (boxes that wrap around a periodic or ring boundary are loaded below)
@@ -724,13 +852,21 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
     unsigned my_slow = 0;
     const int D_ = D;
 
+    // rounds of one particle per thread, the same count for every thread (the
+    // bucketed deposit synchronises the CTA once per round)
+    const int nrounds = (int)((p1 - p0 + blockDim.x - 1) / blockDim.x);
     long long i = p0 + threadIdx.x;
     ParticleIn cur, nxt;
+    cur.cell = -1;
     if (i < p1) load_particle(pb, DIM, i, r.w_const, cur);
-    for (; i < p1; i += blockDim.x) {
+    for (int rd = 0; rd < nrounds; ++rd, i += blockDim.x) {
         const long long inext = i + blockDim.x;
+        nxt.cell = -1;
         if (inext < p1) load_particle(pb, DIM, inext, r.w_const, nxt);
         const int32_t pc = cur.cell;
+        bool dep = false;  // this particle deposits in the round's bucketed deposit
+        int dpk = 0;
+        float dd0[3] = {0.f, 0.f, 0.f}, dd1[3] = {0.f, 0.f, 0.f}, dqw = 0.f, dqz = 0.f;
         if (pc >= 0) {
             int c[3];
             unpack_cell(r, pc, c[0], c[1], c[2]);
@@ -769,15 +905,25 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
                         bool moves = DIM == 2 && u[2] != 0.f;
 #pragma unroll
                         for (int a = 0; a < DIM; ++a) moves = moves || k[a] != 0 || d1[a] != d[a];
-                        if (__any_sync(__activemask(), moves)) {
+                        if (G::BK && tile_item) {
+                            dep = moves;
+                            dqw = r.q * cur.w;
+                            dqz = dqw * u[2] * ig;
+#pragma unroll
+                            for (int a = 0; a < DIM; ++a) {
+                                dpk |= ((rel[a] + 64) << (8 * a)) | ((k[a] + 1) << (24 + 2 * a));
+                                dd0[a] = d[a];
+                                dd1[a] = d1[a];
+                            }
+                        } else if (__any_sync(__activemask(), moves)) {
                             const float qw = r.q * cur.w;
                             Axis<P> ax[DIM];
 #pragma unroll
                             for (int a = 0; a < DIM; ++a)
                                 axis_window<P>(rel[a], d[a], k[a], d1[a], -qw * r.d_over_dt[a], ax[a]);
-                            if (DIM == 3) deposit3_smem<P, G>(reinterpret_cast<const Axis<P> *>(ax), S, Jhi, Jlo);
+                            if (DIM == 3) deposit3_smem<P, G>(reinterpret_cast<const Axis<P> *>(ax), S, Jhi);
                             else
-                                deposit2_smem<P, G>(reinterpret_cast<const Axis<P> *>(ax), S, qw * u[2] * ig, Jhi, Jlo);
+                                deposit2_smem<P, G>(reinterpret_cast<const Axis<P> *>(ax), S, qw * u[2] * ig, Jhi);
                         }
 #pragma unroll
                         for (int a = 0; a < DIM; ++a) d[a] = d1[a];
@@ -816,6 +962,7 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
             }
         }
         cur = nxt;
+        if (G::BK && tile_item) deposit_round<DIM, P, G>(r, dep, dpk, dd0, dd1, dqw, dqz, S, Jhi, stg, s_cnt, s_start);
     }
     if (my_slow) atomicAdd(&slow_cnt, my_slow);
     __syncthreads();
@@ -1004,7 +1151,10 @@ __global__ void __launch_bounds__(kZeroThreads, 3) push_zero_kernel(const Run *_
         }
         if (slow) atomicAdd(&s_slow, slow);
         __syncthreads();
-        if (threadIdx.x == 0 && s_slow) atomicAdd(&r.state->slow, (unsigned long long)s_slow);
+        if (threadIdx.x == 0) {
+            if (s_slow) atomicAdd(&r.state->slow, (unsigned long long)s_slow);
+            atomicAdd(&r.state->streamed, (unsigned long long)(p1 - p0));
+        }
     }
 }
 

@@ -229,3 +229,27 @@ def test_bunch_3d_cubic_hot_spot():
     assert d["n_particles"] == orc.np
     _fields_close(gpu, orc, 1e-4, group_norm=True)
     gpu.close()
+
+
+@pytest.mark.parametrize("dim,order", [(2, 1), (2, 2), (2, 3), (3, 1), (3, 2), (3, 3)])
+def test_charge_density_matches_oracle(dim, order):
+    """pic_read_fields(PIC_RHO) against the oracle's charge deposit, node by
+    node: on the loaded particles (identical positions on both sides: FP64
+    accumulation rounded to FP32, so within 1e-6 of max |rho|), and after a
+    few steps (positions then agree to FP32 rounding of the moves)."""
+    if dim == 2:
+        w = inputs.thermal_2d(n=(40, 24), order=order)
+        w.uth = 0.05
+    else:
+        w = inputs.thermal_3d(n=(16, 12, 20), order=order)
+    parts = inputs.background(w)
+    gpu, orc = pair(w, parts)
+    for steps, tol in ((0, 1e-6), (4, 1e-5)):
+        gpu.step(steps)
+        orc.step(steps) if steps else None
+        ref = orc.charge().reshape(orc.shape)
+        got = gpu.field("rho").astype(np.float64)
+        scale = np.max(np.abs(ref))
+        assert scale > 0
+        assert np.max(np.abs(got - ref)) <= tol * scale, (steps, np.max(np.abs(got - ref)) / scale)
+    gpu.close()

@@ -6,8 +6,9 @@ allocate once it runs.  pic_charge_density_static serves them from a static
 device scratch array.  This test calls it through the C ABI twice in a row on
 the same particles (the second call must clear what the first left in the
 shared array) and compares both results with pic_read_fields(PIC_RHO) of a
-handle holding the same particles, at the tolerance of the charge checks
-(FP64 accumulation rounded to FP32: max difference <= 1e-6 of max |rho|).
+handle holding the same particles and with the FP64 oracle's charge deposit
+of the same particles, at the tolerance of the charge checks (FP64
+accumulation rounded to FP32: max difference <= 1e-6 of max |rho|).
 The file name makes pytest collect it after every other test.
 """
 import ctypes
@@ -15,6 +16,7 @@ import ctypes
 import numpy as np
 import pytest
 
+from gpu_helpers import load_oracle, oracle_for
 from paper_1310_0930_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -59,9 +61,14 @@ def test_static_scratch_charge_matches_regular_path_twice(case):
     sim.load(parts)
     ref = sim.field("rho").reshape(-1).astype(np.float64)
     sim.close()
-    scale = np.max(np.abs(ref))
+    orc = oracle_for(w, nthreads=2)
+    load_oracle(orc, w, parts)
+    ref64 = orc.charge()
+    scale = np.max(np.abs(ref64))
     assert scale > 0
+    assert np.max(np.abs(ref - ref64)) <= 1e-6 * scale
     for use_w in (False, True):
         for out in _static_rho_twice(w, parts, use_w):
             assert np.all(np.isfinite(out))
             assert np.max(np.abs(out.astype(np.float64) - ref)) <= 1e-6 * scale
+            assert np.max(np.abs(out.astype(np.float64) - ref64)) <= 1e-6 * scale
