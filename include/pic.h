@@ -10,8 +10,8 @@
  *   cell's lower vertex (Sec. 5.1);
  *   charge-conserving current deposit on the straight segment (Sec. 5.2,
  *   Esirkepov's decomposition);
- *   Yee FDTD update B(1/2) -> E -> B(1/2) (Sec. 2, Sec. 3 "local field
- *   solver").
+ *   Yee FDTD update B(1/2) -> E -> B(1/2) (Sec. 2; Sec. 3: a local field
+ *   solver).
  * Normalised units, c = 1: dE/dt = curl B - J, dB/dt = -curl E, div E = rho.
  * Lengths in c/omega, fields in m c omega / e, charge and mass in units of
  * the electron's magnitude.  A particle's weight w is a density (n / ppc):
@@ -84,8 +84,8 @@ extern "C" {
 
 /* Grid: dim = 2 or 3; n cells per axis (n[2] ignored in 2D); d cell sizes;
  * dt must satisfy the Yee Courant condition dt * sqrt(sum 1/d^2) < 1
- * (Sec. 2: "the time step is then chosen according to the Courant
- * condition").  bc_last: PIC_BC_PERIODIC or PIC_BC_OPEN. */
+ * (Sec. 2: the time step is set by the Courant limit of the field
+ * solver).  bc_last: PIC_BC_PERIODIC or PIC_BC_OPEN. */
 typedef struct {
     int32_t dim;
     int32_t n[3];
@@ -196,7 +196,7 @@ typedef struct {
 
 typedef struct {
     int32_t abi_version; /* PIC_ABI_VERSION */
-    int32_t shape_order; /* B-spline order 1, 2 or 3 (Table 3 "interpolation level") */
+    int32_t shape_order; /* B-spline order 1, 2 or 3 (Table 3 varies it) */
     pic_grid grid;
     int32_t n_species;   /* must be 1 */
     int32_t track_ids;   /* 1: keep a per-particle int32 id through sorts */

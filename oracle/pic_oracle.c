@@ -18,7 +18,7 @@
  *   5. charge-conserving current deposit, read as Esirkepov's density
  *      decomposition on the full straight segment (Sec. 5.2, the
  *      charge-conserving method it cites),
- *   6. Yee FDTD update of E and B (Sec. 2, Sec. 3 "local field solver").
+ *   6. Yee FDTD update of E and B (Sec. 2; Sec. 3: a local field solver).
  * The deposit runs the paper's shared-memory algorithm literally: n_T threads
  * each own a private copy of the current grid, followed by a threaded
  * reduction of the copies (Sec. 3.1).
@@ -74,8 +74,8 @@ typedef struct {
 } or_sim;
 
 /* ------------------------------------------------------------------ */
-/* B-spline shape functions (Sec. 5.2 step i; Table 3 "interpolation   */
-/* level" 1..4).  S_p is the p-fold convolution of the unit box.        */
+/* B-spline shape functions (Sec. 5.2 step i; Table 3 varies the order  */
+/* from 1 to 4).  S_p is the p-fold convolution of the unit box.        */
 /* ------------------------------------------------------------------ */
 double or_bspline(int p, double t)
 {
@@ -168,7 +168,7 @@ void or_gather(const or_sim *s, const double *E, const double *B, const double *
 }
 
 /* ------------------------------------------------------------------ */
-/* Relativistic push (Sec. 2 "fully relativistic equations of motion",  */
+/* Relativistic push (Sec. 2: the relativistic equations of motion;     */
 /* Sec. 5.2 step iii), read as the Boris scheme: half electric kick,     */
 /* magnetic rotation with tan(theta/2) = |t|, half electric kick.        */
 /* u = gamma*beta; eb = (E0,E1,E2,B0,B1,B2) at the particle.            */
@@ -315,8 +315,9 @@ void or_deposit_current(const or_sim *s, double qw, const double *x_old, const d
 /* towards +last axis, polarised along laser_pol, with                   */
 /*   E_inc = a0 exp(-r^2/w0^2) exp(-2 ln2 (xi - t_peak)^2 / fwhm^2)      */
 /*           cos(omega0 (xi - t_peak)),  xi = t - (z - z_plane),         */
-/* the envelope being Gaussian in intensity with the given FWHM (Sec. 2  */
-/* "laser driver"; Sec. 6 names the lasers; the shape is a reading).     */
+/* the envelope being Gaussian in intensity with the given FWHM (Sec. 2: */
+/* the laser drives the wake; Sec. 6 names the lasers; the shape is a   */
+/* reading).                                                             */
 /* ------------------------------------------------------------------ */
 static double laser_field(const or_sim *s, double r2, double xi)
 {
@@ -358,7 +359,7 @@ static int laser_active(const or_sim *s)
 }
 
 /* ------------------------------------------------------------------ */
-/* Yee FDTD (Sec. 2; Sec. 3 "local field solver"; Sec. 5.1 "Yee grid"): */
+/* Yee FDTD (Sec. 2; Sec. 3: a local field solver; Sec. 5.1: Yee mesh):  */
 /* B -= h curl E with forward differences of E.  h = dt/2 per half step.*/
 /* On an open last axis the B components at half-integer positions with */
 /* index n-1 lie outside the domain and stay zero.                      */
@@ -549,10 +550,11 @@ static double profile_density(const or_sim *s, double zlab)
     return s->knots[i] * (1.0 - r) + s->knots[i + 1] * r;
 }
 
-/* Moving window (Sec. 2 "moving window that follows the laser"): shift  */
-/* every field one cell back along the last axis, zero the new front     */
-/* plane, move every particle one cell back, drop those leaving the kept */
-/* region and inject a cold, regularly placed layer at the front.        */
+/* Moving window (Sec. 2: the box moves along with the laser pulse):    */
+/* shift every field one cell back along the last axis, zero the new     */
+/* front plane, move every particle one cell back, drop those leaving    */
+/* the kept region and inject a cold, regularly placed layer at the      */
+/* front.                                                                */
 static void window_shift(or_sim *s, double *E, double *B, double *x, double *u, double *w,
                          int64_t *np, int64_t cap)
 {

@@ -1,4 +1,4 @@
-// fields.cu -- Yee FDTD update (Sec. 2, Sec. 3 "local field solver"), the
+// fields.cu -- Yee FDTD update (Sec. 2; Sec. 3: a local field solver), the
 // open last axis (first-order Mur fields), the laser antenna (one-way plane
 // source) and the moving window (Sec. 2) on device-resident state.
 //

@@ -836,14 +836,19 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
         }
         const float B = 1.01f * fabsf(r.q) * wtot, M = fabsf(r.q) * wmax;
         S = B > 0.f ? fminf(1073741824.f / B, kMaxScaled / M) : 1.f;
+        bool done = true;
         if (tma) {  // bounded wait for the field tile; a timeout is latched in the status
-            bool done = false;
+            done = false;
             for (int it = 0; it < kTmaSpin && !done; ++it) done = mbar_try_wait(&tma_bar, 0);
             if (!done) {
                 if (threadIdx.x == 0) atomicOr(&stp->status, kStatusTimeout);
                 for (int it = 0; it < kTmaSpin && !done; ++it) done = mbar_try_wait(&tma_bar, 0);
             }
         }
+        // a field tile that did not arrive in time: the whole CTA leaves the
+        // tile's particles and current as they are (the latched status reports
+        // the incomplete step) rather than push with a partly written tile
+        if (__syncthreads_or(!done)) return;
         live = __syncthreads_or(nzbits != 0u) != 0;
     }
 
