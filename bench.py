@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="lwfa_3d",
-                    choices=["lwfa_3d", "warm_3d", "thermal_2d", "bunch_3d", "scan_2d", "adjoint_2d"])
+                    choices=["lwfa_3d", "warm_3d", "thermal_2d", "bunch_3d", "scan_2d", "adjoint_2d", "order_sweep"])
     ap.add_argument("--order", type=int, default=0, help="shape order override (warm_3d)")
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     ap.add_argument("--scan-runs", type=int, default=64)
@@ -393,6 +393,71 @@ def adjoint_bench(args):
     return 0
 
 
+# Table 3 of the paper: the warm-plasma benchmark (128^3 cells, 8 ppc,
+# u_th = 0.1) on one 8-core Intel E5-2680 (AVX, FP32): full PIC step time
+# per particle per CPU for interpolation orders 1 to 4, context for the
+# per-GPU figure (the quartic per-core entry is garbled in the source; the
+# per-CPU time is used).
+TABLE3_NS_PER_PARTICLE_PER_CPU = {1: 7.4, 2: 13.6, 3: 24.8, 4: 61.5}
+
+
+def order_sweep(args):
+    """Shape orders 1 to 4 on the warm-plasma benchmark of Table 3: 128^3
+    cells, 8 ppc (16,777,216 electrons), u_th = 0.1, periodic, every particle
+    moving: particle-steps/s and ns per particle per GPU for each order, the
+    push phase's share, and the paper's per-CPU time beside it."""
+    import torch
+    from paper_1310_0930_gb300 import inputs
+    from paper_1310_0930_gb300.sim import Simulation, TorchMemory
+
+    torch.cuda.set_device(0)
+    tuning = json.loads(args.tuning) if args.tuning else None
+    rows = {}
+    for order in (1, 2, 3, 4):
+        w = inputs.thermal_3d(n=(128, 128, 128), order=order)
+        w.name = "warm_3d"
+        w.uth = 0.1
+        parts = inputs.background(w)
+        mem = TorchMemory()
+        sim = Simulation(w, tuning=tuning, memory=mem)
+        sim.load(parts)
+        sim.step(args.warmup)
+        sim.sync()
+        clocks = Clocks(0)
+        sim.profile_begin(args.steps)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(mem.stream)
+        sim.step(args.steps)
+        e1.record(mem.stream)
+        torch.cuda.synchronize()
+        phases, _ = sim.profile_end()
+        clk = clocks.stop()
+        ms = e0.elapsed_time(e1) / args.steps
+        d = sim.diagnostics()
+        sim.close()
+        n = parts.n
+        rows[order] = {"particle_steps_per_s": n / (ms / 1e3), "ms_per_step": ms,
+                       "push_ms_per_step": phases["push"] / args.steps,
+                       "ns_per_particle": ms * 1e6 / n, "clocks": clk, "status": d["status"],
+                       "paper_ns_per_particle_per_cpu": TABLE3_NS_PER_PARTICLE_PER_CPU[order]}
+        rows[order]["gpu_over_cpu"] = rows[order]["paper_ns_per_particle_per_cpu"] / rows[order]["ns_per_particle"]
+    base = rows[1]["ms_per_step"]
+    for order in rows:
+        rows[order]["time_over_linear"] = rows[order]["ms_per_step"] / base
+    line = {"metric": METRIC, "value": rows[2]["particle_steps_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": rows[2]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "order_sweep: warm plasma 128^3 cells, 8 ppc, u_th 0.1, periodic, orders 1-4 "
+                                   "(value: quadratic)", "particles": 16777216},
+            "orders": rows, "clocks": rows[2]["clocks"]}
+    print(json.dumps(line), flush=True)
+    if args.out:
+        with open(args.out, "w") as f:
+            f.write(json.dumps(line) + "\n")
+    return 0
+
+
 def reference_arm(args):
     """The FP64 oracle timed on the host cores on the native arm's workload
     (a bounded crop; the whole run takes about a minute).  Under torchrun
@@ -401,7 +466,7 @@ def reference_arm(args):
     if rank != 0:
         return 0
     w = workload(args.workload, args.scale, args.order)
-    if args.workload in ("scan_2d", "adjoint_2d"):
+    if args.workload in ("scan_2d", "adjoint_2d", "order_sweep"):
         print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the single-run workloads only"}))
         return 0
     cb = cpu_baseline(w, 45.0, steps=max(1, args.steps), warmup=args.warmup)
@@ -428,6 +493,8 @@ def main():
         return scan_bench(args)
     if args.workload == "adjoint_2d":
         return adjoint_bench(args)
+    if args.workload == "order_sweep":
+        return order_sweep(args)
     import torch
     import torch.distributed as dist
 

@@ -162,7 +162,7 @@ typedef void (*pic_free_fn)(void *ptr, void *ctx);
  * work queue, largest runs first, 2 = one CTA per tile.
  * Compiled (tile, drift) pairs: 2D 16x16 with drift 1, 2 (default) or 3,
  * 8x8 with 1, 32x32 with 2; 3D 8x8x8 with 1 (default) or 2, 8x8x4 with 1; any other pair
- * is PIC_EINVAL.
+ * is PIC_EINVAL.  Shape order 4: 2D 16x16 with drift 2, 3D 8x8x8 with drift 1 only.
  * use_graph: capture each step kind in a CUDA graph and replay it.
  * sort_sub: sub-buckets per tile in the sort, 0 = default (1 = none),
  * else a power of two <= 32: slot i of a tile's particles goes to sub-bucket
@@ -196,7 +196,9 @@ typedef struct {
 
 typedef struct {
     int32_t abi_version; /* PIC_ABI_VERSION */
-    int32_t shape_order; /* B-spline order 1, 2 or 3 (Table 3 varies it) */
+    int32_t shape_order; /* B-spline order 1, 2, 3 or 4 (Table 3 varies it); order 4 with
+                            the default tile and drift of each dimension, no TMA staging
+                            and no adjoint form */
     pic_grid grid;
     int32_t n_species;   /* must be 1 */
     int32_t track_ids;   /* 1: keep a per-particle int32 id through sorts */

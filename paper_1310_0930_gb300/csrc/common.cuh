@@ -219,6 +219,39 @@ struct Shape<3> {
     }
 };
 
+template <>
+struct Shape<4> {
+    // quartic B-spline at the five nodes nearest the particle, t = position
+    // minus the middle node, t in [-1/2, 1/2):
+    //   |s| <= 1/2:        (115 - 120 s^2 + 48 s^4) / 192
+    //   1/2 <= |s| <= 3/2: (55 + 20 |s| - 120 s^2 + 80 |s|^3 - 16 s^4) / 96
+    //   3/2 <= |s| < 5/2:  (5/2 - |s|)^4 / 24
+    static __device__ __forceinline__ float mid(float s)
+    {
+        return (55.f + s * (20.f + s * (-120.f + s * (80.f - 16.f * s)))) * (1.f / 96.f);
+    }
+    static __device__ __forceinline__ void q(float t, float *w)
+    {
+        const float a = 0.5f - t, b = 0.5f + t, t2 = t * t;
+        w[0] = (a * a) * (a * a) * (1.f / 24.f);
+        w[1] = mid(1.f + t);
+        w[2] = (115.f + t2 * (-120.f + 48.f * t2)) * (1.f / 192.f);
+        w[3] = mid(1.f - t);
+        w[4] = (b * b) * (b * b) * (1.f / 24.f);
+    }
+    static __device__ __forceinline__ void node(int c, float d, int &base, float *w)
+    {
+        int h = d >= 0.5f ? 1 : 0;
+        base = c + h - 2;
+        q(d - (float)h, w);
+    }
+    static __device__ __forceinline__ void half(int c, float d, int &base, float *w)
+    {
+        base = c - 2;
+        q(d - 0.5f, w);
+    }
+};
+
 // Reach of the stencils relative to the particle's cell c, per axis:
 // gather touches [c - GLO, c + GHI]; the deposit window of a move of less
 // than one cell touches nodes [c - DLO, c + DHI].
@@ -235,6 +268,10 @@ struct Reach<2> {
 template <>
 struct Reach<3> {
     static constexpr int GLO = 2, GHI = 2, DLO = 2, DHI = 3;
+};
+template <>
+struct Reach<4> {
+    static constexpr int GLO = 2, GHI = 3, DLO = 3, DHI = 4;
 };
 
 }  // namespace pic

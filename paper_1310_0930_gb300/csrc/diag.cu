@@ -260,11 +260,13 @@ cudaError_t launch_charge(int dim, int order, const Run *run, double *rho, long 
     if (dim == 2) {
         if (order == 1) charge_kernel<2, 1><<<g, kBlock, 0, st>>>(run, rho, cap);
         else if (order == 2) charge_kernel<2, 2><<<g, kBlock, 0, st>>>(run, rho, cap);
-        else charge_kernel<2, 3><<<g, kBlock, 0, st>>>(run, rho, cap);
+        else if (order == 3) charge_kernel<2, 3><<<g, kBlock, 0, st>>>(run, rho, cap);
+        else charge_kernel<2, 4><<<g, kBlock, 0, st>>>(run, rho, cap);
     } else {
         if (order == 1) charge_kernel<3, 1><<<g, kBlock, 0, st>>>(run, rho, cap);
         else if (order == 2) charge_kernel<3, 2><<<g, kBlock, 0, st>>>(run, rho, cap);
-        else charge_kernel<3, 3><<<g, kBlock, 0, st>>>(run, rho, cap);
+        else if (order == 3) charge_kernel<3, 3><<<g, kBlock, 0, st>>>(run, rho, cap);
+        else charge_kernel<3, 4><<<g, kBlock, 0, st>>>(run, rho, cap);
     }
     return cudaGetLastError();
 }

@@ -127,7 +127,8 @@ cudaError_t launch_charge_static(int order, GridArgs g, double q, double w_const
     const unsigned blocks = (unsigned)((n + kBlock - 1) / kBlock);
     if (order == 1) charge_static_kernel<DIM, 1><<<blocks, kBlock, 0, st>>>(g, q, w_const, n, cell, off, w, s);
     else if (order == 2) charge_static_kernel<DIM, 2><<<blocks, kBlock, 0, st>>>(g, q, w_const, n, cell, off, w, s);
-    else charge_static_kernel<DIM, 3><<<blocks, kBlock, 0, st>>>(g, q, w_const, n, cell, off, w, s);
+    else if (order == 3) charge_static_kernel<DIM, 3><<<blocks, kBlock, 0, st>>>(g, q, w_const, n, cell, off, w, s);
+    else charge_static_kernel<DIM, 4><<<blocks, kBlock, 0, st>>>(g, q, w_const, n, cell, off, w, s);
     return cudaGetLastError();
 }
 
@@ -139,7 +140,7 @@ extern "C" int pic_charge_density_static(const pic_grid *grid, int32_t shape_ord
                                          float *rho, void *stream)
 {
     using namespace pic;
-    if (!grid || (grid->dim != 2 && grid->dim != 3) || shape_order < 1 || shape_order > 3 || n < 0 || !rho)
+    if (!grid || (grid->dim != 2 && grid->dim != 3) || shape_order < 1 || shape_order > 4 || n < 0 || !rho)
         return PIC_EINVAL;
     if (n > 0 && (!cell || !off)) return PIC_EINVAL;
     long long ncell = 1;

@@ -167,7 +167,7 @@ int validate(const pic_config *c)
     if (!c || c->abi_version != PIC_ABI_VERSION) return PIC_EINVAL;
     const pic_grid &g = c->grid;
     if (g.dim != 2 && g.dim != 3) return PIC_EINVAL;
-    if (c->shape_order < 1 || c->shape_order > 3) return PIC_EINVAL;
+    if (c->shape_order < 1 || c->shape_order > 4) return PIC_EINVAL;
     double s = 0.0;
     long long ncell = 1;
     int bits = 0;
@@ -1099,6 +1099,7 @@ int pic_adjoint_begin(pic_t *h, int32_t total_steps, int32_t checkpoint_every)
     if (h->started || h->adj || h->nruns != 1) return PIC_ESTATE;
     HostRun &hr = h->runs[0];
     if (!hr.cfg.track_ids || !hr.sp.per_particle_weight || hr.r.window_on || !hr.r.P[0].cell) return PIC_EINVAL;
+    if (h->order > 3) return PIC_EINVAL;  // (the reverse kernels are compiled for orders 1 to 3)
     RunState st;
     int rc = read_state(h, 0, &st);
     if (rc) return rc;

@@ -18,6 +18,9 @@ int stage_push_3d_a(int, const int *, int, int *, int *);
 int stage_push_3d_b(int, const int *, int, int *, int *);
 int stage_push_3d_tma(int, const int *, int, int *, int *);
 int box_push_3d_tma(int, const int *, int, int *);
+cudaError_t launch_push_q(int, const int *, int, const PushArgs &, cudaStream_t);
+size_t smem_push_q(int, const int *, int);
+int stage_push_q(int, const int *, int, int *, int *);
 
 int push_default_drift(int dim, const int *tile)
 {
@@ -29,6 +32,7 @@ int push_default_drift(int dim, const int *tile)
 
 size_t push_smem_bytes(int dim, int order, const int *tile, int drift, bool tma)
 {
+    if (order == 4) return tma ? 0 : smem_push_q(dim, tile, drift);
     if (dim == 2) return tma ? 0 : smem_push_2d(order, tile, drift);
     if (tma) return smem_push_3d_tma(order, tile, drift);
     size_t s = smem_push_3d_a(order, tile, drift);
@@ -37,11 +41,12 @@ size_t push_smem_bytes(int dim, int order, const int *tile, int drift, bool tma)
 
 int push_tma_box(int dim, int order, const int *tile, int drift, int *box)
 {
-    return dim == 3 ? box_push_3d_tma(order, tile, drift, box) : 0;
+    return dim == 3 && order <= 3 ? box_push_3d_tma(order, tile, drift, box) : 0;
 }
 
 int push_stage_extent(int dim, int order, const int *tile, int drift, bool tma, int *lo, int *len)
 {
+    if (order == 4) return tma ? 0 : stage_push_q(dim, tile, drift, lo, len);
     if (dim == 2) return tma ? 0 : stage_push_2d(order, tile, drift, lo, len);
     if (tma) return stage_push_3d_tma(order, tile, drift, lo, len);
     return stage_push_3d_a(order, tile, drift, lo, len) || stage_push_3d_b(order, tile, drift, lo, len);
@@ -49,6 +54,7 @@ int push_stage_extent(int dim, int order, const int *tile, int drift, bool tma, 
 
 cudaError_t launch_push(int dim, int order, const int *tile, int drift, bool tma, const PushArgs &a, cudaStream_t st)
 {
+    if (order == 4) return tma ? cudaErrorInvalidValue : launch_push_q(dim, tile, drift, a, st);
     if (dim == 2) return launch_push_2d(order, tile, drift, a, st);
     if (tma) return launch_push_3d_tma(order, tile, drift, a, st);
     if (smem_push_3d_a(order, tile, drift)) return launch_push_3d_a(order, tile, drift, a, st);
@@ -148,11 +154,13 @@ cudaError_t launch_push_zero(int dim, int order, const Run *runs, const Item *ze
     if (dim == 2) {
         if (order == 1) return launch_zero<2, 1>(runs, zero, count, max_items, num_sms, st);
         if (order == 2) return launch_zero<2, 2>(runs, zero, count, max_items, num_sms, st);
-        return launch_zero<2, 3>(runs, zero, count, max_items, num_sms, st);
+        if (order == 3) return launch_zero<2, 3>(runs, zero, count, max_items, num_sms, st);
+        return launch_zero<2, 4>(runs, zero, count, max_items, num_sms, st);
     }
     if (order == 1) return launch_zero<3, 1>(runs, zero, count, max_items, num_sms, st);
     if (order == 2) return launch_zero<3, 2>(runs, zero, count, max_items, num_sms, st);
-    return launch_zero<3, 3>(runs, zero, count, max_items, num_sms, st);
+    if (order == 3) return launch_zero<3, 3>(runs, zero, count, max_items, num_sms, st);
+    return launch_zero<3, 4>(runs, zero, count, max_items, num_sms, st);
 }
 
 }  // namespace pic

@@ -70,8 +70,11 @@ def test_validation_rejects_bad_configs_before_touching_the_device():
     cfg, keep = make_config(w)
     cfg.grid.dt = 1.0 / math.sqrt(2 / 0.2 ** 2) * 1.0001
     assert _create(cfg)[0] == abi.PIC_EINVAL
-    # unsupported shape order
+    # unsupported shape order (quartic: the default tiles only)
     cfg, keep = make_config(w)
+    cfg.shape_order = 5
+    assert _create(cfg)[0] == abi.PIC_EINVAL
+    cfg, keep = make_config(w, tuning={"tile": (8, 8)})
     cfg.shape_order = 4
     assert _create(cfg)[0] == abi.PIC_EINVAL
     # more than one species

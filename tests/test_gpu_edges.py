@@ -30,7 +30,7 @@ def _compare_particles(gpu, orc, n, dims, tol_u=1e-5, tol_x=4e-6):
     assert np.max(np.abs(dx)) < tol_x, np.max(np.abs(dx))
 
 
-@pytest.mark.parametrize("order", [1, 2, 3])
+@pytest.mark.parametrize("order", [1, 2, 3, 4])
 def test_face_offsets_and_relativistic_momenta_3d(order):
     """Offsets 0 and the largest float below 1 on every axis, |u| up to 50
     (gamma ~ 50, moves close to the Courant limit), 4 steps in smooth fields."""
@@ -91,7 +91,7 @@ def test_load_beyond_capacity_is_refused():
     sim.close()
 
 
-@pytest.mark.parametrize("order", [1, 2, 3])
+@pytest.mark.parametrize("order", [1, 2, 3, 4])
 def test_fields_in_part_of_the_grid_3d(order):
     """Smooth fields in the lower half of z only, exact zeros elsewhere; moving
     particles everywhere.  Tiles whose staged fields are all zero take the

@@ -97,7 +97,7 @@ def test_thermal_2d_100_steps_fields_energy_gauss():
     gpu.close()
 
 
-@pytest.mark.parametrize("order", [1, 2, 3])
+@pytest.mark.parametrize("order", [1, 2, 3, 4])
 def test_thermal_3d_orders(order):
     w = inputs.thermal_3d(n=(16, 16, 16), steps=20, order=order)
     parts = inputs.background(w)
@@ -109,7 +109,7 @@ def test_thermal_3d_orders(order):
     gpu.close()
 
 
-@pytest.mark.parametrize("order", [1, 3])
+@pytest.mark.parametrize("order", [1, 3, 4])
 def test_thermal_2d_other_orders_ragged_tiles(order):
     """40x36 cells with 16x16 tiles: partial tiles on both axes."""
     w = inputs.thermal_2d(n=(40, 36), steps=30, order=order)
@@ -231,7 +231,7 @@ def test_bunch_3d_cubic_hot_spot():
     gpu.close()
 
 
-@pytest.mark.parametrize("dim,order", [(2, 1), (2, 2), (2, 3), (3, 1), (3, 2), (3, 3)])
+@pytest.mark.parametrize("dim,order", [(2, 1), (2, 2), (2, 3), (2, 4), (3, 1), (3, 2), (3, 3), (3, 4)])
 def test_charge_density_matches_oracle(dim, order):
     """pic_read_fields(PIC_RHO) against the oracle's charge deposit, node by
     node: on the loaded particles (identical positions on both sides: FP64

@@ -64,7 +64,7 @@ def test_lwfa_3d_streamed_tiles_equal_staged_and_oracle():
     staged.close()
 
 
-@pytest.mark.parametrize("order", [1, 2, 3])
+@pytest.mark.parametrize("order", [1, 2, 3, 4])
 def test_fields_written_into_a_streamed_region_are_gathered(order):
     """A cold plasma in zero fields is streamed; fields written afterwards
     from the host into half of the box must reach the particles there at the
