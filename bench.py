@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="lwfa_3d",
-                    choices=["lwfa_3d", "warm_3d", "thermal_2d", "bunch_3d", "scan_2d", "adjoint_2d", "order_sweep"])
+                    choices=["lwfa_3d", "warm_3d", "thermal_2d", "bunch_3d", "scan_2d", "adjoint_2d", "order_sweep",
+                             "frozen_3d"])
     ap.add_argument("--order", type=int, default=0, help="shape order override (warm_3d)")
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     ap.add_argument("--scan-runs", type=int, default=64)
@@ -458,6 +459,100 @@ def order_sweep(args):
     return 0
 
 
+# Table 2 of the paper: frozen (zero-temperature) plasma on the full Jaguar
+# machine, linear (s1) and quadratic (s2) interpolation: 1463.5 and 784.0
+# G particles/s at 516.9 and 736.1 TFlop/s, i.e. about 2.7x the operations
+# per particle for quadratic at about 1.8x the time.
+TABLE2_FROZEN = {"linear_gparts_per_s": 1463.5, "quadratic_gparts_per_s": 784.0,
+                 "quadratic_over_linear_time": 1463.5 / 784.0,
+                 "quadratic_over_linear_ops": (736.1 / 784.0) / (516.9 / 1463.5)}
+
+
+def frozen_bench(args):
+    """The frozen-plasma asymptotic test of Table 2: a zero-temperature plasma
+    (256^3 cells, 8 ppc, 134,217,728 electrons, periodic) at linear and
+    quadratic order.  (a) No fields, as in the paper: nothing moves and every
+    tile takes the zero-field streaming kernel (the step's asymptotic limit is
+    the particle state's HBM traffic).  (b) The same plasma, immobile (mass
+    1e30 electron masses) in imposed smooth E and B: every tile is staged and
+    every particle gathers E and B and is pushed, but none moves, so no
+    current is deposited -- the gather-and-push cost whose order dependence
+    the paper's remark on operations and time is about."""
+    import torch
+    from paper_1310_0930_gb300 import inputs
+    from paper_1310_0930_gb300.sim import Simulation, TorchMemory
+
+    torch.cuda.set_device(0)
+    n = tuple(max(16, int(round(256 * args.scale / 8)) * 8) for _ in range(3))
+    rows = {}
+    for case in ("no_fields", "imposed_fields"):
+        for order in (1, 2):
+            w = inputs.thermal_3d(n=n, order=order)
+            w.name = "frozen_3d"
+            w.uth = 0.0
+            if case == "imposed_fields":
+                w.mass = 1e30
+            parts = inputs.background(w)
+            mem = TorchMemory()
+            sim = Simulation(w, memory=mem)
+            sim.load(parts)
+            if case == "imposed_fields":
+                z, y, x = np.meshgrid(*[np.arange(m, dtype=np.float64) for m in reversed(n)], indexing="ij")
+                for c, name in enumerate(("Ex", "Ey", "Ez", "Bx", "By", "Bz")):
+                    k = 2 * np.pi * (c + 1) / n[0]
+                    f = 0.01 * (1.5 + np.cos(k * x + 0.3 * c) * np.cos(k * y) * np.cos(k * z + 0.7))
+                    sim.set_field(name, f.astype(np.float32))
+                del x, y, z
+            sim.step(args.warmup)
+            sim.sync()
+            d0 = sim.diagnostics()
+            clocks = Clocks(0)
+            sim.profile_begin(args.steps)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(mem.stream)
+            sim.step(args.steps)
+            e1.record(mem.stream)
+            torch.cuda.synchronize()
+            phases, _ = sim.profile_end()
+            clk = clocks.stop()
+            d1 = sim.diagnostics()
+            ms = e0.elapsed_time(e1) / args.steps
+            sim.close()
+            _, push_bytes, sp = algorithmic_bytes(w, parts.n)
+            push_ms = phases["push"] / args.steps
+            rows["%s_order%d" % (case, order)] = {
+                "particle_steps_per_s": parts.n / (ms / 1e3), "ms_per_step": ms, "push_ms_per_step": push_ms,
+                "push_zero_ms_per_step": phases["push_zero"] / args.steps,
+                "streamed_fraction": (d1["streamed"] - d0["streamed"]) / (parts.n * args.steps),
+                "push_roofline_frac": push_bytes / (push_ms / 1e3) / 1e9 / _peak(),
+                "clocks": clk, "status": d1["status"]}
+    for case in ("no_fields", "imposed_fields"):
+        a, b = rows[case + "_order1"], rows[case + "_order2"]
+        rows[case + "_quadratic_over_linear_time"] = b["ms_per_step"] / a["ms_per_step"]
+        rows[case + "_quadratic_over_linear_push_time"] = b["push_ms_per_step"] / a["push_ms_per_step"]
+    v = rows["no_fields_order2"]
+    line = {"metric": METRIC, "value": v["particle_steps_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": v["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "frozen_3d: zero-temperature plasma %s cells, 8 ppc, periodic, orders 1 and 2, "
+                                   "without fields and (immobile) in imposed fields (value: quadratic, no fields)"
+                                   % "x".join(map(str, n)), "particles": int(np.prod(n)) * 8},
+            "cases": rows, "paper_table2": TABLE2_FROZEN, "clocks": v["clocks"]}
+    print(json.dumps(line), flush=True)
+    if args.out:
+        with open(args.out, "w") as f:
+            f.write(json.dumps(line) + "\n")
+    return 0
+
+
+def _peak():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0))
+    except Exception:
+        return 6800.0
+
+
 def reference_arm(args):
     """The FP64 oracle timed on the host cores on the native arm's workload
     (a bounded crop; the whole run takes about a minute).  Under torchrun
@@ -466,7 +561,7 @@ def reference_arm(args):
     if rank != 0:
         return 0
     w = workload(args.workload, args.scale, args.order)
-    if args.workload in ("scan_2d", "adjoint_2d", "order_sweep"):
+    if args.workload in ("scan_2d", "adjoint_2d", "order_sweep", "frozen_3d"):
         print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the single-run workloads only"}))
         return 0
     cb = cpu_baseline(w, 45.0, steps=max(1, args.steps), warmup=args.warmup)
@@ -495,6 +590,8 @@ def main():
         return adjoint_bench(args)
     if args.workload == "order_sweep":
         return order_sweep(args)
+    if args.workload == "frozen_3d":
+        return frozen_bench(args)
     import torch
     import torch.distributed as dist
 

@@ -1101,7 +1101,7 @@ __global__ void __launch_bounds__(kZeroThreads, 3) push_zero_kernel(const Run *_
         z.last_shift = DIM == 3 ? r.bits[0] + r.bits[1] : r.bits[0];
         const int t = it.a;
         const long long p0 = r.tile_off[t], p1 = r.tile_off[t + 1];
-        unsigned slow = 0;
+        bool moving = false;  // this thread left a moving particle for the second pass
         // four consecutive slots per thread with 16-byte accesses where every
         // array is 16-byte aligned; slot by slot elsewhere
         uintptr_t al = (uintptr_t)pb.cell | (uintptr_t)pb.u[0] | (uintptr_t)pb.u[1] | (uintptr_t)pb.u[2];
@@ -1119,23 +1119,16 @@ __global__ void __launch_bounds__(kZeroThreads, 3) push_zero_kernel(const Run *_
             int32_t cl[4] = {c4.x, c4.y, c4.z, c4.w};
             float uu[4][3] = {{u4[0].x, u4[1].x, u4[2].x}, {u4[0].y, u4[1].y, u4[2].y},
                               {u4[0].z, u4[1].z, u4[2].z}, {u4[0].w, u4[1].w, u4[2].w}};
-            unsigned movers = 0;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) movers |= zero_slot<DIM>(r, z, cl[q], uu[q]) ? 1u << q : 0u;
-            // (a moving slot's values are written back unchanged; the slow path
-            // below then overwrites them)
+            for (int q = 0; q < 4; ++q) moving = zero_slot<DIM>(r, z, cl[q], uu[q]) || moving;
+            // (a moving slot's values are written back unchanged; the second
+            // pass advances it)
             reinterpret_cast<int4 *>(pb.cell)[g] = make_int4(cl[0], cl[1], cl[2], cl[3]);
 #pragma unroll
             for (int a = 0; a < DIM; ++a) reinterpret_cast<float4 *>(pb.off[a])[g] = o4[a];
 #pragma unroll
             for (int a = 0; a < 3; ++a)
                 reinterpret_cast<float4 *>(pb.u[a])[g] = make_float4(uu[0][a], uu[1][a], uu[2][a], uu[3][a]);
-            while (movers) {  // rare: a moving particle deposits, so its fields are soon non-zero
-                const int q = __ffs(movers) - 1;
-                movers &= movers - 1;
-                ++slow;
-                zero_mover<DIM, P>(r, z, pb, 4 * g + q);
-            }
         }
         // the ragged ends (and every slot when an array is not 16-byte aligned)
         const long long ends = (v0 - p0) + (p1 - v1);
@@ -1143,18 +1136,27 @@ __global__ void __launch_bounds__(kZeroThreads, 3) push_zero_kernel(const Run *_
             const long long i = e < v0 - p0 ? p0 + e : v1 + (e - (v0 - p0));
             int32_t cl = pb.cell[i];
             float uu[3] = {pb.u[0][i], pb.u[1][i], pb.u[2][i]};
-            const bool moves = zero_slot<DIM>(r, z, cl, uu);
+            moving = zero_slot<DIM>(r, z, cl, uu) || moving;
             pb.cell[i] = cl;
             if (cl >= 0) {
 #pragma unroll
                 for (int a = 0; a < 3; ++a) pb.u[a][i] = uu[a];
             }
-            if (moves) {
+        }
+        // second pass, rare (a moving particle deposits, so its tile's fields
+        // are soon non-zero): the tile's moving particles take the slow path,
+        // reloaded one at a time so that the streaming loop above carries no
+        // call (and no spilled state)
+        if (__syncthreads_or(moving)) {
+            unsigned slow = 0;
+            for (long long i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
+                if (pb.cell[i] < 0) continue;
+                if (pb.u[0][i] == 0.f && pb.u[1][i] == 0.f && pb.u[2][i] == 0.f) continue;
                 ++slow;
                 zero_mover<DIM, P>(r, z, pb, i);
             }
+            if (slow) atomicAdd(&s_slow, slow);
         }
-        if (slow) atomicAdd(&s_slow, slow);
         __syncthreads();
         if (threadIdx.x == 0) {
             if (s_slow) atomicAdd(&r.state->slow, (unsigned long long)s_slow);

@@ -77,6 +77,7 @@ class Workload:
     knots: Optional[np.ndarray] = None   # density profile knots (lab frame, last axis)
     knot_z: tuple = (0.0, 0.0)
     bunch: Optional[dict] = None
+    mass: float = 1.0    # particle mass in electron masses (charge -1)
 
     @property
     def n_cells(self) -> int:

@@ -35,7 +35,7 @@ def make_config(w: Workload, *, tuning: Optional[dict] = None, track_ids=False, 
     cfg.grid.dt = float(w.dt)
     cfg.grid.bc_last = abi.PIC_BC_OPEN if w.open_last else abi.PIC_BC_PERIODIC
     sp = abi.pic_species()
-    sp.q, sp.m = -1.0, 1.0
+    sp.q, sp.m = -1.0, float(getattr(w, "mass", 1.0))
     ppc = list(w.ppc) + [1] * (3 - len(w.ppc))
     for a in range(3):
         sp.ppc[a] = int(ppc[a])

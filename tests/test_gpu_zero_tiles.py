@@ -114,3 +114,35 @@ def test_cold_plasma_in_zero_fields_stays_bit_identical_when_streamed():
     for name in FIELD_NAMES + ["Jx", "Jy", "Jz"]:
         assert not np.any(gpu.field(name)), name
     gpu.close()
+
+
+def test_immobile_plasma_in_imposed_fields_gathers_and_stays():
+    """Particles of 1e30 electron masses in smooth imposed fields (the
+    frozen-plasma bench in fields): every tile is staged and gathers, no
+    particle moves, no current is deposited, and the fields evolve as in
+    vacuum, as in the oracle."""
+    w = inputs.thermal_3d(n=(16, 16, 24), order=2)
+    w.uth = 0.0
+    w.mass = 1e30
+    parts = inputs.background(w)
+    gpu = Simulation(w, track_ids=True)
+    gpu.load(parts)
+    import oracle
+    orc = oracle.Sim(3, w.n, w.d, w.dt, w.order, m=1e30, nthreads=2)
+    x = np.zeros((3, parts.n))
+    x[:3] = parts.positions64()
+    orc.load(x, parts.u.astype(np.float64), parts.w.astype(np.float64))
+    for name, arr in smooth_fields(w, amp=0.05, seed=3).items():
+        gpu.set_field(name, arr)
+        orc.field(name)[...] = arr.astype(np.float64)
+    p0 = _by_id(gpu.particles())
+    gpu.step(4)
+    orc.step(4)
+    p1 = _by_id(gpu.particles())
+    assert np.array_equal(p0["cell"], p1["cell"]) and np.array_equal(p0["off"], p1["off"])
+    assert np.max(np.abs(p1["u"])) < 1e-25
+    for name in ("Jx", "Jy", "Jz"):
+        assert not np.any(gpu.field(name)), name
+    for name in FIELD_NAMES:
+        assert rel_l2(gpu.field(name), orc.field(name)) <= 1e-5, name
+    gpu.close()
