@@ -688,6 +688,7 @@ def main():
     del sim
 
     # ---- the configured run from its first step to its last ----------------
+    torch.cuda.empty_cache()
     full = None
     if world == 1 and not args.no_full_run and w.steps > args.steps:
         mem_f = TorchMemory(device=local)
@@ -751,6 +752,9 @@ def main():
         del sim2, pinned
 
     # ---- the metric's other half: batched scan and adjoint against plain runs --
+    # (memory the caching allocator kept from the runs above goes back first,
+    # so that the adjoint finds the free memory it sizes its records by)
+    torch.cuda.empty_cache()
     scan = adj = None
     if world == 1 and not args.no_scan:
         scan = scan_measure(args, args.scan_steps, 5, window_moves=True)
