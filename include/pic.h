@@ -343,6 +343,23 @@ PIC_API int pic_adjoint_backward(pic_t *h, const pic_objective *obj, double *L, 
  * pic_adjoint_backward, exposed for transpose (dot-product) checks. */
 PIC_API int pic_adjoint_fields(pic_t *h, float *lam, float *lam_j, double t);
 
+/* Transpose of the particle part of one step (Sec. 5.2 steps i-v: gather,
+ * Boris push, move, charge-conserving deposit) at the handle's current
+ * state: the map (E, B, x, u, w) -> (x', u', J) that the next pic_step's
+ * particle phase would apply, linearised at the particles and fields the
+ * handle holds now, transposed and applied to the adjoints of its outputs.
+ * In (by particle id, n ids): lam_x[dim][n] of the new positions (cells),
+ * lam_u[3][n] of the new momenta; lam_j[3][n0*n1*n2] of the deposited
+ * current (the order of pic_read_fields).  Out, overwritten: lam_x, lam_u
+ * (of the old positions and momenta), lam_w[n] (of the weights) and
+ * lam_f[6][n0*n1*n2] (of Ex..Bz).  Host arrays.  Requirements as for the
+ * adjoint form (one run, track_ids, per_particle_weight, orders 1-3, no
+ * moving window); n is the number of particles loaded.  A building block of
+ * pic_adjoint_backward, exposed for transpose (dot-product) checks; it
+ * allocates its scratch arrays for the call. */
+PIC_API int pic_adjoint_particles(pic_t *h, float *lam_x, float *lam_u, const float *lam_j, double *lam_w,
+                                  float *lam_f, int64_t n);
+
 /* Charge density without any device allocation, for callers that cannot
  * allocate device memory (a host framework that passes the library only its
  * own buffers, a memory budget that forbids new allocations, a loop that

@@ -96,6 +96,7 @@ SIGNATURES = {
     "pic_adjoint_backward": (c_int32, [_handle, _P(pic_objective), _P(c_double), _P(c_double), c_void_p, c_int32,
                                        c_void_p]),
     "pic_adjoint_fields": (c_int32, [_handle, c_void_p, c_void_p, c_double]),
+    "pic_adjoint_particles": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64]),
     "pic_charge_density_static": (c_int32, [_P(pic_grid), c_int32, c_double, c_double, c_int64, c_void_p, c_void_p,
                                             c_void_p, c_void_p, c_void_p]),
 }

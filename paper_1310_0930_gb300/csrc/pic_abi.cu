@@ -1370,6 +1370,96 @@ int pic_adjoint_backward(pic_t *h, const pic_objective *obj, double *L, double *
     return PIC_OK;
 }
 
+int pic_adjoint_particles(pic_t *h, float *lam_x, float *lam_u, const float *lam_j, double *lam_w, float *lam_f,
+                          int64_t n)
+{
+    if (!h || !lam_x || !lam_u || !lam_j || !lam_w || !lam_f || n < 1) return PIC_EINVAL;
+    if (h->nruns != 1) return PIC_ESTATE;
+    HostRun &hr = h->runs[0];
+    if (!hr.cfg.track_ids || !hr.sp.per_particle_weight || hr.r.window_on || h->order > 3 || !hr.r.P[0].cell)
+        return PIC_EINVAL;
+    if (!h->started) {
+        int rc = first_step_setup(h);
+        if (rc) return rc;
+    }
+    RunState st;
+    int rc = read_state(h, 0, &st);
+    if (rc) return rc;
+    const Run &r = hr.r;
+    const int dim = r.dim;
+    const long long ns = st.n_total, nc = r.ncell;
+    if (ns < 1) return PIC_EINVAL;
+    std::vector<void *> bufs;
+    bool ok = true;
+    auto F = [&](long long cnt) {
+        void *p = dev_alloc(h, sizeof(float) * (size_t)cnt);
+        ok = ok && p;
+        bufs.push_back(p);
+        return (float *)p;
+    };
+    auto D = [&](long long cnt) {
+        void *p = dev_alloc(h, sizeof(double) * (size_t)cnt);
+        ok = ok && p;
+        bufs.push_back(p);
+        return (double *)p;
+    };
+    AdjPtrs A{};
+    for (int c = 0; c < 3; ++c) {
+        A.lE[c] = F(nc);
+        A.lB[c] = F(nc);
+        A.lJ[c] = F(nc);
+        A.lu[c] = F(n);
+        A.su[c] = F(ns);
+        if (c < dim) {
+            A.lx[c] = F(n);
+            A.sx[c] = F(ns);
+        }
+    }
+    A.lw = D(n);
+    A.sw = D(ns);
+    cudaError_t e = ok ? cudaSuccess : cudaErrorMemoryAllocation;
+    cudaStream_t s = h->stream;
+    for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+        e = cudaMemsetAsync(A.lE[c], 0, sizeof(float) * nc, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(A.lB[c], 0, sizeof(float) * nc, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(A.lJ[c], lam_j + c * nc, sizeof(float) * nc, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(A.lu[c], lam_u + c * n, sizeof(float) * n, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && c < dim)
+            e = cudaMemcpyAsync(A.lx[c], lam_x + c * n, sizeof(float) * n, cudaMemcpyHostToDevice, s);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(A.lw, 0, sizeof(double) * n, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(A.sw, 0, sizeof(double) * ns, s);
+    const ParticleBuf &pb = r.P[st.buf];
+    // adjoints by id -> by slot, the flat reverse kernel over every slot, back by id
+    if (e == cudaSuccess) e = launch_adj_perm(dim, A, pb.id, ns, 1, s);
+    TrajStep ts{};
+    ts.cell = pb.cell;
+    for (int c = 0; c < 3; ++c) {
+        ts.off[c] = c < dim ? pb.off[c] : nullptr;
+        ts.u[c] = pb.u[c];
+        ts.E[c] = r.E[c];
+        ts.B[c] = r.B[c];
+    }
+    ts.w = pb.w;
+    ts.id = pb.id;
+    ts.n = ns;
+    if (e == cudaSuccess) e = launch_adj_particles(dim, h->order, h->d_runs, r, A, ts, 0, s);
+    if (e == cudaSuccess) e = launch_adj_perm(dim, A, pb.id, ns, 0, s);
+    for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+        e = cudaMemcpyAsync(lam_f + c * nc, A.lE[c], sizeof(float) * nc, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(lam_f + (3 + c) * nc, A.lB[c], sizeof(float) * nc, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(lam_u + c * n, A.lu[c], sizeof(float) * n, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && c < dim)
+            e = cudaMemcpyAsync(lam_x + c * n, A.lx[c], sizeof(float) * n, cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(lam_w, A.lw, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (void *p : bufs) dev_free(h, p);
+    if (!ok) return PIC_ENOMEM;
+    return e == cudaSuccess ? PIC_OK : PIC_ECUDA;
+}
+
 int pic_adjoint_fields(pic_t *h, float *lam, float *lam_j, double t)
 {
     if (!h || !lam) return PIC_EINVAL;

@@ -200,6 +200,21 @@ class Simulation:
         abi.check(abi.lib().pic_adjoint_fields(self.h, _ptr(lam), _ptr(lj), float(t)), "pic_adjoint_fields")
         return lam, lj
 
+    def adjoint_particles(self, lam_x: np.ndarray, lam_u: np.ndarray, lam_j: np.ndarray):
+        """Transpose of the next step's particle part at the current state,
+        applied to the adjoints of the new positions (cells) and momenta (by
+        id) and of the deposited current; returns the adjoints of the old
+        positions, momenta, weights and of E, B (six components)."""
+        n = lam_u.shape[1]
+        lx = np.ascontiguousarray(lam_x, dtype=np.float32).copy()
+        lu = np.ascontiguousarray(lam_u, dtype=np.float32).copy()
+        lj = np.ascontiguousarray(lam_j, dtype=np.float32)
+        lw = np.zeros(n, np.float64)
+        lf = np.zeros((6,) + tuple(lj.shape[1:]), np.float32)
+        abi.check(abi.lib().pic_adjoint_particles(self.h, _ptr(lx), _ptr(lu), _ptr(lj), _ptr(lw), _ptr(lf), int(n)),
+                  "pic_adjoint_particles")
+        return lx, lu, lw, lf
+
     def profile_begin(self, max_steps: int):
         abi.pic_profile_begin(self.h, int(max_steps))
 
