@@ -72,6 +72,7 @@ class OrSim(ctypes.Structure):
         ("knots", ctypes.POINTER(ctypes.c_double)), ("z0", ctypes.c_double), ("z1", ctypes.c_double),
         ("time", ctypes.c_double), ("step", ctypes.c_int64), ("shifts", ctypes.c_int64),
         ("nthreads", ctypes.c_int32), ("pad2", ctypes.c_int32),
+        ("split", ctypes.c_int32), ("pad3", ctypes.c_int32),
     ]
 
 
@@ -90,6 +91,8 @@ def lib():
             L.or_deposit_rho.argtypes = [ctypes.POINTER(OrSim), ctypes.c_double, _dp, _dp]
             L.or_deposit_current.argtypes = [ctypes.POINTER(OrSim), ctypes.c_double, _dp, _dp,
                                              ctypes.c_double, _dp]
+            L.or_deposit_current_split.argtypes = [ctypes.POINTER(OrSim), ctypes.c_double, _dp, _dp,
+                                                   ctypes.c_double, _dp]
             L.or_yee_b.argtypes = [ctypes.POINTER(OrSim), _dp, _dp, ctypes.c_double]
             L.or_yee_e.argtypes = [ctypes.POINTER(OrSim), _dp, _dp, _dp]
             L.or_step.restype = ctypes.c_int
@@ -132,7 +135,7 @@ class Sim:
     """
 
     def __init__(self, dim, n, d, dt, order, q=-1.0, m=1.0, open_last=False, nthreads=None,
-                 laser=None, window=None):
+                 laser=None, window=None, split=False):
         self.s = OrSim()
         s = self.s
         s.dim = dim
@@ -146,6 +149,7 @@ class Sim:
         s.open_last = int(bool(open_last))
         s.q, s.m = float(q), float(m)
         s.nthreads = int(nthreads or os.cpu_count() or 1)
+        s.split = int(bool(split))
         self._knots = None
         if laser is not None:
             s.laser_on = 1
@@ -233,6 +237,17 @@ class Sim:
         xo[: len(x_old)] = x_old
         xn[: len(x_new)] = x_new
         lib().or_deposit_current(ctypes.byref(self.s), float(qw), _p(xo), _p(xn), float(vz), _p(J))
+        return J
+
+    def deposit_current_split(self, qw, x_old, x_new, vz, J=None) -> np.ndarray:
+        """The same move deposited as virtual trajectories (split at the
+        boundaries between nearest grid points)."""
+        J = np.zeros(3 * self.ncell) if J is None else J
+        xo = np.zeros(3)
+        xn = np.zeros(3)
+        xo[: len(x_old)] = x_old
+        xn[: len(x_new)] = x_new
+        lib().or_deposit_current_split(ctypes.byref(self.s), float(qw), _p(xo), _p(xn), float(vz), _p(J))
         return J
 
     def deposit_rho(self, qw, x3, rho=None) -> np.ndarray:

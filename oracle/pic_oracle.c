@@ -71,6 +71,10 @@ typedef struct {
     int64_t shifts;
     int32_t nthreads;
     int32_t pad2;
+    /* deposit of each move: 0 = one charge-conserving deposit of the whole */
+    /* straight move; 1 = virtual trajectories (or_deposit_current_split)    */
+    int32_t split;
+    int32_t pad3;
 } or_sim;
 
 /* ------------------------------------------------------------------ */
@@ -306,6 +310,47 @@ void or_deposit_current(const or_sim *s, double qw, const double *x_old, const d
                 double v = qw * vz * f;
                 if (v != 0.0) Jz[cell_index(s, lo[0] + qx, lo[1] + qy, 0)] += v;
             }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Virtual trajectories (Sec. 5.2 step iv: up to four per particle in    */
+/* 3D).  The straight move is cut at every point where it crosses a      */
+/* boundary between the grid points nearest the particle -- the          */
+/* half-integer positions for even orders, the cell faces for odd ones   */
+/* -- along any axis, and each piece is deposited by or_deposit_current  */
+/* as a move of its own, its out-of-plane current (2D) weighted by the   */
+/* piece's share of the time step.  Each piece conserves charge, so the  */
+/* sum does; for linear shapes every piece stays in one cell and its     */
+/* current is Villasenor and Buneman's.                                  */
+/* ------------------------------------------------------------------ */
+void or_deposit_current_split(const or_sim *s, double qw, const double *x_old, const double *x_new,
+                              double vz, double *J)
+{
+    const int dim = s->dim;
+    const double off = (s->order % 2 == 0) ? 0.5 : 0.0; /* boundaries at j + off */
+    double ts[3];
+    int nt = 0;
+    for (int a = 0; a < dim; ++a) {
+        const double lo = x_old[a] < x_new[a] ? x_old[a] : x_new[a];
+        const double hi = x_old[a] < x_new[a] ? x_new[a] : x_old[a];
+        const double b = floor(lo - off) + 1.0 + off; /* first boundary above lo */
+        if (b < hi) ts[nt++] = (b - x_old[a]) / (x_new[a] - x_old[a]);
+    }
+    for (int i = 1; i < nt; ++i) /* ascending */
+        for (int j = i; j > 0 && ts[j] < ts[j - 1]; --j) {
+            double t = ts[j];
+            ts[j] = ts[j - 1];
+            ts[j - 1] = t;
+        }
+    double xs[3] = {x_old[0], x_old[1], x_old[2]}, t0 = 0.0;
+    for (int i = 0; i <= nt; ++i) {
+        const double t1 = i < nt ? ts[i] : 1.0;
+        double xe[3];
+        for (int a = 0; a < 3; ++a) xe[a] = i < nt ? x_old[a] + t1 * (x_new[a] - x_old[a]) : x_new[a];
+        if (t1 > t0) or_deposit_current(s, qw, xs, xe, vz * (t1 - t0), J);
+        for (int a = 0; a < 3; ++a) xs[a] = xe[a];
+        t0 = t1;
     }
 }
 
@@ -657,7 +702,8 @@ int or_step(or_sim *s, double *E, double *B, double *J, double *x, double *u, do
                 or_boris(s->q / s->m, s->dt, eb, up);
                 double gam = sqrt(1.0 + up[0] * up[0] + up[1] * up[1] + up[2] * up[2]);
                 for (int a = 0; a < 3; ++a) xn[a] = a < dim ? xo[a] + s->dt * up[a] / (gam * s->d[a]) : 0.0;
-                or_deposit_current(s, s->q * w[p], xo, xn, up[2] / gam, Jt);
+                if (s->split) or_deposit_current_split(s, s->q * w[p], xo, xn, up[2] / gam, Jt);
+                else or_deposit_current(s, s->q * w[p], xo, xn, up[2] / gam, Jt);
                 keep[p] = (unsigned char)particle_kept(s, xn);
                 for (int a = 0; a < 3; ++a) {
                     u[(int64_t)a * cap + p] = up[a];
