@@ -179,7 +179,14 @@ typedef void (*pic_free_fn)(void *ptr, void *ctx);
  * the device: a tile whose staged field region is all +0 (E = B = 0 at every
  * particle, as ahead of a laser front) is advanced by a streaming kernel
  * without shared-memory tiles, the others by the staged kernel; 2 = every
- * tile through the staged kernel. */
+ * tile through the staged kernel.
+ * deposit: 0 = default: Esirkepov's decomposition on the whole straight move;
+ * 1 = virtual trajectories (Sec. 5.2 step iv): the move is cut where it
+ * crosses a boundary between the grid points nearest the particle (half-
+ * integer positions for even orders, cell faces for odd ones) and each piece
+ * is deposited on its own; for linear shapes this is Villasenor and
+ * Buneman's scheme.  Compiled for the default tile of each dimension, orders
+ * 1-3, without TMA staging (otherwise PIC_EINVAL). */
 typedef struct {
     int32_t tile[3];
     int32_t sort_interval;
@@ -192,6 +199,7 @@ typedef struct {
     int32_t adjoint_keep;
     int32_t sort_policy;
     int32_t stream_zero_tiles;
+    int32_t deposit;
 } pic_tuning;
 
 typedef struct {
@@ -307,7 +315,8 @@ PIC_API int pic_profile_end(pic_t *h, double *ms, int32_t n_phases, int64_t *lau
  *   L = sum w K sigma / sum w sigma,  K = m (gamma - 1),
  *   sigma(z) = logistic((z - z_lo)/width) * logistic((z_hi - z)/width).
  * Requirements: a single run, track_ids = 1, per_particle_weight = 1, no
- * moving window, particles loaded, no step taken yet. */
+ * moving window, shape order 1-3 with the default deposit, particles loaded,
+ * no step taken yet. */
 typedef struct {
     double z_lo, z_hi, width;
 } pic_objective;

@@ -16,6 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpic_gb300.so")
 SOURCES = ["pic_abi.cu", "push.cu", "push_2d.cu", "push_3d_a.cu", "push_3d_b.cu", "push_3d_tma.cu", "push_q.cu",
+           "push_split.cu",
            "fields.cu", "sort.cu", "diag.cu", "noalloc.cu", "adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

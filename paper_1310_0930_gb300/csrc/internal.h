@@ -36,14 +36,16 @@ constexpr int kScanThreads = 256, kScanItems = 16, kScanChunk = kScanThreads * k
 // Particle kernel (push.cuh) over the compiled tile menu (push_menu.h).
 // push_smem_bytes returns 0 for a (tile, drift) pair that is not compiled.
 int push_default_drift(int dim, const int *tile);
-// tma: the entry compiled with TMA staging of the field tile (3D only)
-size_t push_smem_bytes(int dim, int order, const int *tile, int drift, bool tma);
+// variant: 0 = field tile staged by plain loads, 1 = staged by TMA (3D
+// only), 2 = plain staging with the virtual-trajectory deposit (the default
+// tiles, orders 1-3)
+size_t push_smem_bytes(int dim, int order, const int *tile, int drift, int variant);
 // 3D: extents of the TMA box that loads one component of the field tile
 // (returns 0 for 2D or an entry not compiled with TMA staging)
 int push_tma_box(int dim, int order, const int *tile, int drift, int *box);
 // the field region a tile stages: lo[a] cells before the tile origin, len[a]
 // cells long, per axis (returns 0 for an entry that is not compiled)
-int push_stage_extent(int dim, int order, const int *tile, int drift, bool tma, int *lo, int *len);
+int push_stage_extent(int dim, int order, const int *tile, int drift, int variant, int *lo, int *len);
 
 // One launch of the staged particle kernel.
 struct PushArgs {
@@ -57,7 +59,8 @@ struct PushArgs {
                           // taking items from this device counter (reset by the launch)
     int persistent_ctas;
 };
-cudaError_t launch_push(int dim, int order, const int *tile, int drift, bool tma, const PushArgs &a, cudaStream_t st);
+cudaError_t launch_push(int dim, int order, const int *tile, int drift, int variant, const PushArgs &a,
+                        cudaStream_t st);
 
 // Per-step tile classification (push.cu): the tile items items[n_tail,
 // n_items) are split into live tiles, appended to `live` after its n_tail
@@ -66,8 +69,8 @@ cudaError_t launch_push(int dim, int order, const int *tile, int drift, bool tma
 // then advanced by the streaming kernel (launch_push_zero).
 cudaError_t launch_classify(const Run *runs, const Item *items, int n_tail, int n_items, const int *stage_lo,
                             const int *stage_len, Item *live, Item *zero, int *cnt, cudaStream_t st);
-cudaError_t launch_push_zero(int dim, int order, const Run *runs, const Item *zero, const int *count, int max_items,
-                             int num_sms, cudaStream_t st);
+cudaError_t launch_push_zero(int dim, int order, bool split, const Run *runs, const Item *zero, const int *count,
+                             int max_items, int num_sms, cudaStream_t st);
 
 // fields.cu
 cudaError_t launch_zero_j(const Run *runs, Seg cells, cudaStream_t st);

@@ -93,6 +93,8 @@ struct pic_s {
     Seg seg_cells{}, seg_planes{}, seg_parts{}, seg_inject{}, seg_keys{};
     int sort_sub = 1;
     bool use_tma = false;
+    bool split = false;  // virtual-trajectory deposit (pic_tuning.deposit = 1)
+    int variant() const { return use_tma ? 1 : (split ? 2 : 0); }
     bool sort_adaptive = true;  // the device decides when to sort (sort_decide_kernel)
     int adjoint_keep = 0;
     bool yee_quad = true;  // every run: rows of a multiple of 4 cells, 16-byte aligned field arrays
@@ -207,6 +209,7 @@ int validate(const pic_config *c)
     if (t.sort_policy < 0 || t.sort_policy > 1) return PIC_EINVAL;
     if (t.persistent < 0 || t.persistent > 2) return PIC_EINVAL;
     if (t.stream_zero_tiles < 0 || t.stream_zero_tiles > 2) return PIC_EINVAL;
+    if (t.deposit < 0 || t.deposit > 1 || (t.deposit == 1 && t.tma > 0)) return PIC_EINVAL;
     return PIC_OK;
 }
 
@@ -416,14 +419,14 @@ int enqueue_step(pic_s *h, bool sort, bool adaptive)
                                 h->d_cnt, st);
         const PushArgs a{R, h->d_live, h->n_tail, h->d_cnt, n_tiles, h->block, h->tail_block,
                          h->persistent ? h->d_cnt + 2 : nullptr, h->num_sms};
-        if (e == cudaSuccess) e = launch_push(h->dim, h->order, h->tile, h->drift, h->use_tma, a, st);
+        if (e == cudaSuccess) e = launch_push(h->dim, h->order, h->tile, h->drift, h->variant(), a, st);
         if (ev && e == cudaSuccess) e = cudaEventRecord(ev[kMarkZero], st);
         if (e == cudaSuccess)
-            e = launch_push_zero(h->dim, h->order, R, h->d_zero, h->d_cnt + 1, n_tiles, h->num_sms, st);
+            e = launch_push_zero(h->dim, h->order, h->split, R, h->d_zero, h->d_cnt + 1, n_tiles, h->num_sms, st);
     } else {
         const PushArgs a{R, h->d_items, h->n_items, nullptr, 0, h->block, h->tail_block,
                          h->persistent ? h->d_queue : nullptr, h->num_sms};
-        if (e == cudaSuccess) e = launch_push(h->dim, h->order, h->tile, h->drift, h->use_tma, a, st);
+        if (e == cudaSuccess) e = launch_push(h->dim, h->order, h->tile, h->drift, h->variant(), a, st);
         if (ev && e == cudaSuccess) e = cudaEventRecord(ev[kMarkZero], st);
     }
     mark(PIC_PH_YEE_B1);
@@ -481,7 +484,7 @@ int first_step_setup(pic_s *h)
     }
     // sets the push kernel's shared-memory limit outside any graph capture
     const PushArgs a0{h->d_runs, h->d_items, 0, nullptr, 0, h->block, kTail, nullptr, 1};
-    cudaError_t e = launch_push(h->dim, h->order, h->tile, h->drift, h->use_tma, a0, h->stream);
+    cudaError_t e = launch_push(h->dim, h->order, h->tile, h->drift, h->variant(), a0, h->stream);
     if (e != cudaSuccess) return PIC_ECUDA;
     h->started = true;
     return PIC_OK;
@@ -673,15 +676,16 @@ int create_common(const pic_config *cfgs, int n, pic_t **out)
     h->persistent = t.persistent == 1 || (t.persistent == 0 && n > 1);
     h->sort_sub = t.sort_sub ? t.sort_sub : 1;
     h->use_tma = t.tma > 0;
+    h->split = t.deposit == 1;
     h->adjoint_keep = t.adjoint_keep;
     h->classify = t.stream_zero_tiles != 2;
     if (h->sort_sub < 1 || h->sort_sub > 32 || (h->sort_sub & (h->sort_sub - 1))) {
         delete h;
         return PIC_EINVAL;
     }
-    h->push_smem = push_smem_bytes(h->dim, h->order, h->tile, h->drift, h->use_tma);
+    h->push_smem = push_smem_bytes(h->dim, h->order, h->tile, h->drift, h->variant());
     if (h->push_smem == 0 ||  // (tile, drift) not among the compiled configurations
-        !push_stage_extent(h->dim, h->order, h->tile, h->drift, h->use_tma, h->stage_lo, h->stage_len)) {
+        !push_stage_extent(h->dim, h->order, h->tile, h->drift, h->variant(), h->stage_lo, h->stage_len)) {
         delete h;
         return PIC_EINVAL;
     }
@@ -1100,6 +1104,7 @@ int pic_adjoint_begin(pic_t *h, int32_t total_steps, int32_t checkpoint_every)
     HostRun &hr = h->runs[0];
     if (!hr.cfg.track_ids || !hr.sp.per_particle_weight || hr.r.window_on || !hr.r.P[0].cell) return PIC_EINVAL;
     if (h->order > 3) return PIC_EINVAL;  // (the reverse kernels are compiled for orders 1 to 3)
+    if (h->split) return PIC_EINVAL;      // (they transpose the undivided deposit)
     RunState st;
     int rc = read_state(h, 0, &st);
     if (rc) return rc;
@@ -1376,7 +1381,8 @@ int pic_adjoint_particles(pic_t *h, float *lam_x, float *lam_u, const float *lam
     if (!h || !lam_x || !lam_u || !lam_j || !lam_w || !lam_f || n < 1) return PIC_EINVAL;
     if (h->nruns != 1) return PIC_ESTATE;
     HostRun &hr = h->runs[0];
-    if (!hr.cfg.track_ids || !hr.sp.per_particle_weight || hr.r.window_on || h->order > 3 || !hr.r.P[0].cell)
+    if (!hr.cfg.track_ids || !hr.sp.per_particle_weight || hr.r.window_on || h->order > 3 || h->split ||
+        !hr.r.P[0].cell)
         return PIC_EINVAL;
     if (!h->started) {
         int rc = first_step_setup(h);

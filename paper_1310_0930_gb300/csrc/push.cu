@@ -21,6 +21,9 @@ int box_push_3d_tma(int, const int *, int, int *);
 cudaError_t launch_push_q(int, const int *, int, const PushArgs &, cudaStream_t);
 size_t smem_push_q(int, const int *, int);
 int stage_push_q(int, const int *, int, int *, int *);
+cudaError_t launch_push_split(int, int, const int *, int, const PushArgs &, cudaStream_t);
+size_t smem_push_split(int, int, const int *, int);
+int stage_push_split(int, int, const int *, int, int *, int *);
 
 int push_default_drift(int dim, const int *tile)
 {
@@ -30,8 +33,10 @@ int push_default_drift(int dim, const int *tile)
     return 2;
 }
 
-size_t push_smem_bytes(int dim, int order, const int *tile, int drift, bool tma)
+size_t push_smem_bytes(int dim, int order, const int *tile, int drift, int variant)
 {
+    if (variant == 2) return smem_push_split(dim, order, tile, drift);
+    const bool tma = variant == 1;
     if (order == 4) return tma ? 0 : smem_push_q(dim, tile, drift);
     if (dim == 2) return tma ? 0 : smem_push_2d(order, tile, drift);
     if (tma) return smem_push_3d_tma(order, tile, drift);
@@ -44,16 +49,21 @@ int push_tma_box(int dim, int order, const int *tile, int drift, int *box)
     return dim == 3 && order <= 3 ? box_push_3d_tma(order, tile, drift, box) : 0;
 }
 
-int push_stage_extent(int dim, int order, const int *tile, int drift, bool tma, int *lo, int *len)
+int push_stage_extent(int dim, int order, const int *tile, int drift, int variant, int *lo, int *len)
 {
+    if (variant == 2) return stage_push_split(dim, order, tile, drift, lo, len);
+    const bool tma = variant == 1;
     if (order == 4) return tma ? 0 : stage_push_q(dim, tile, drift, lo, len);
     if (dim == 2) return tma ? 0 : stage_push_2d(order, tile, drift, lo, len);
     if (tma) return stage_push_3d_tma(order, tile, drift, lo, len);
     return stage_push_3d_a(order, tile, drift, lo, len) || stage_push_3d_b(order, tile, drift, lo, len);
 }
 
-cudaError_t launch_push(int dim, int order, const int *tile, int drift, bool tma, const PushArgs &a, cudaStream_t st)
+cudaError_t launch_push(int dim, int order, const int *tile, int drift, int variant, const PushArgs &a,
+                        cudaStream_t st)
 {
+    if (variant == 2) return launch_push_split(dim, order, tile, drift, a, st);
+    const bool tma = variant == 1;
     if (order == 4) return tma ? cudaErrorInvalidValue : launch_push_q(dim, tile, drift, a, st);
     if (dim == 2) return launch_push_2d(order, tile, drift, a, st);
     if (tma) return launch_push_3d_tma(order, tile, drift, a, st);
@@ -147,10 +157,20 @@ cudaError_t launch_classify(const Run *runs, const Item *items, int n_tail, int 
     return cudaGetLastError();
 }
 
-cudaError_t launch_push_zero(int dim, int order, const Run *runs, const Item *zero, const int *count, int max_items,
-                             int num_sms, cudaStream_t st)
+cudaError_t launch_push_zero(int dim, int order, bool split, const Run *runs, const Item *zero, const int *count,
+                             int max_items, int num_sms, cudaStream_t st)
 {
     using namespace push_detail;
+    if (split) {  // (moving particles of zero-field tiles deposit as virtual trajectories)
+        if (dim == 2) {
+            if (order == 1) return launch_zero<2, 1, true>(runs, zero, count, max_items, num_sms, st);
+            if (order == 2) return launch_zero<2, 2, true>(runs, zero, count, max_items, num_sms, st);
+            return launch_zero<2, 3, true>(runs, zero, count, max_items, num_sms, st);
+        }
+        if (order == 1) return launch_zero<3, 1, true>(runs, zero, count, max_items, num_sms, st);
+        if (order == 2) return launch_zero<3, 2, true>(runs, zero, count, max_items, num_sms, st);
+        return launch_zero<3, 3, true>(runs, zero, count, max_items, num_sms, st);
+    }
     if (dim == 2) {
         if (order == 1) return launch_zero<2, 1>(runs, zero, count, max_items, num_sms, st);
         if (order == 2) return launch_zero<2, 2>(runs, zero, count, max_items, num_sms, st);

@@ -97,7 +97,12 @@ __device__ __forceinline__ void tma_load_box(void *dst, const void *tmap, int x,
         : "memory");
 }
 
-template <int DIM, int P, int TX, int TY, int TZ, int D, bool T>
+// Kernel variants (template parameter V): the field tile staged by plain
+// loads (0) or by TMA (1); 2: plain staging, current deposited as virtual
+// trajectories (deposit_split).
+constexpr int kVarPlain = 0, kVarTma = 1, kVarSplit = 2;
+
+template <int DIM, int P, int TX, int TY, int TZ, int D, int V>
 struct Geo {
     static constexpr int GLO = Reach<P>::GLO, GHI = Reach<P>::GHI, DLO = Reach<P>::DLO, DHI = Reach<P>::DHI;
     static constexpr int up4(int a) { return (a + 3) / 4 * 4; }
@@ -124,7 +129,8 @@ struct Geo {
     // pair whose tile would not fit next to the J tile is skipped; with none
     // left the rows stay dense.  Otherwise: the rows the stencil needs, with
     // 3D planes padded as for the J tile.
-    static constexpr bool TL = T && DIM == 3;
+    static constexpr bool TL = V == kVarTma && DIM == 3;
+    static constexpr bool SPLIT = V == kVarSplit;
     static constexpr int FHX = TL ? up4(D + GLO) : D + GLO, FHY = D + GLO, FHZ = DIM == 3 ? D + GLO : 0;
     static constexpr int FZ = DIM == 3 ? TZ + 2 * D + GLO + GHI : 1;
     static constexpr int NX = TL ? up4(FHX + TX + D + GHI) : TX + 2 * D + GLO + GHI, NY = TY + 2 * D + GLO + GHI;
@@ -170,7 +176,7 @@ struct Geo {
     // 17.5 -> 15.8 ms but 3D LWFA live tiles 115 -> 121 ps per particle,
     // linear 7.1 -> 8.7 ms), where it fits next to the tiles and the kernel's
     // static shared memory; otherwise each thread deposits its own particle.
-    static constexpr bool BK = P >= 3 && SMEM_TILES + STG_BYTES + 2048 <= 232448;
+    static constexpr bool BK = P >= 3 && !SPLIT && SMEM_TILES + STG_BYTES + 2048 <= 232448;
     static constexpr size_t SMEM = SMEM_TILES + (BK ? STG_BYTES : 0);
 };
 
@@ -292,6 +298,170 @@ __device__ __forceinline__ void axis_window(int c0, float d0, int k, float d1, f
         }
     }
     if (s == 0) ax.Pre[P] = 0.f;
+}
+
+// ---------------------------------------------------------------- virtual trajectories
+// Sec. 5.2 step iv: the straight move is cut into up to DIM + 1 pieces where
+// it crosses a boundary between the grid points nearest the particle (the
+// half-integer positions for even orders, the cell faces for odd ones), and
+// each piece, which stays with one nearest point per axis, is deposited as a
+// move of its own.  Points are kept as (cell, offset) per axis so that the
+// move's own end points and the crossing points (exactly 1/2 or 0 from a
+// cell) carry no rounding; the other axes' coordinates at a crossing are
+// interpolated once and shared by the two pieces that meet there.
+
+// Shape weights of the P + 1 window nodes of a fixed window, tau = the
+// position minus the window's reference node: in [-1/2, 1/2] for even
+// orders (the middle node), in [0, 1] for odd ones (the cell's lower node).
+template <int P>
+__device__ __forceinline__ void weights_at(float tau, float *w);
+template <>
+__device__ __forceinline__ void weights_at<1>(float tau, float *w)
+{
+    tau = fminf(fmaxf(tau, 0.f), 1.f);
+    w[0] = 1.f - tau;
+    w[1] = tau;
+}
+template <>
+__device__ __forceinline__ void weights_at<2>(float tau, float *w)
+{
+    Shape<2>::q(fminf(fmaxf(tau, -0.5f), 0.5f), w);
+}
+template <>
+__device__ __forceinline__ void weights_at<3>(float tau, float *w)
+{
+    Shape<3>::cub(fminf(fmaxf(tau, 0.f), 1.f), w);
+}
+template <>
+__device__ __forceinline__ void weights_at<4>(float tau, float *w)
+{
+    Shape<4>::q(fminf(fmaxf(tau, -0.5f), 0.5f), w);
+}
+
+// reference node of a point (cell c, offset o): the nearest integer for even
+// orders, the cell for odd ones
+template <int P>
+__device__ __forceinline__ int ref_node(int c, float o)
+{
+    return P % 2 == 0 ? c + (o >= 0.5f ? 1 : 0) : c;
+}
+
+// Cut the move (c[a], d0[a]) -> (c[a] + k[a], d1[a]) into pieces and call
+// piece(ax, frac) for each, ax the piece's no-shift Esirkepov windows
+// (coef_a = -q w d_a / dt) and frac its share of the time step.
+template <int DIM, int P, class Piece>
+__device__ __forceinline__ void split_move(const int *c, const float *d0, const int *k, const float *d1,
+                                           const float *coef, const Piece &piece)
+{
+    float tcut[DIM] = {};
+    int acut[DIM] = {}, ncut = 0;
+    int n0[DIM], n1[DIM], bc[DIM];
+    float bo[DIM], dx[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        n0[a] = ref_node<P>(c[a], d0[a]);
+        n1[a] = ref_node<P>(c[a] + k[a], d1[a]);
+        dx[a] = ((float)k[a] + d1[a]) - d0[a];  // displacement in cells
+        bc[a] = c[a];
+        bo[a] = d0[a];
+        if (n1[a] != n0[a]) {  // crossing: the boundary as (cell, offset)
+            const int s = n1[a] - n0[a];
+            if (P % 2 == 0) {
+                bc[a] = s > 0 ? n0[a] : n0[a] - 1;
+                bo[a] = 0.5f;
+            } else {
+                bc[a] = s > 0 ? n0[a] + 1 : n0[a];
+                bo[a] = 0.f;
+            }
+            tcut[ncut] = (((float)(bc[a] - c[a]) + bo[a]) - d0[a]) / dx[a];
+            acut[ncut] = a;
+            ++ncut;
+        }
+    }
+#pragma unroll
+    for (int i = 1; i < DIM; ++i)  // ascending (at most DIM cuts)
+#pragma unroll
+        for (int j = DIM - 1; j >= 1; --j)
+            if (j < ncut && tcut[j] < tcut[j - 1]) {
+                const float t = tcut[j];
+                tcut[j] = tcut[j - 1];
+                tcut[j - 1] = t;
+                const int q = acut[j];
+                acut[j] = acut[j - 1];
+                acut[j - 1] = q;
+            }
+    int sc[DIM];  // start point of the current piece
+    float so[DIM];
+    unsigned done = 0;  // bit a: the axis was crossed before the current piece
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        sc[a] = c[a];
+        so[a] = d0[a];
+    }
+    float t0 = 0.f;
+    // (the remaining cuts are kept in tcut[0..], acut[0..]: shifted down after
+    // each piece, so that every index is a compile-time constant)
+    for (int i = 0; i <= ncut; ++i) {
+        const bool last = i == ncut;
+        const float t1 = last ? 1.f : tcut[0];
+        const int cut_axis = last ? -1 : acut[0];
+        int ec[DIM];
+        float eo[DIM];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            if (last) {
+                ec[a] = c[a] + k[a];
+                eo[a] = d1[a];
+            } else if (a == cut_axis) {
+                ec[a] = bc[a];
+                eo[a] = bo[a];
+            } else {
+                const float o = d0[a] + t1 * dx[a];
+                const float f = floorf(o);
+                ec[a] = c[a] + (int)f;
+                eo[a] = o - f;
+                if (eo[a] >= 1.f) {
+                    eo[a] = 0.f;
+                    ec[a] += 1;
+                }
+            }
+        }
+        Axis<P> ax[DIM];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            const int node = ((done >> a) & 1u) ? n1[a] : n0[a];
+            float S0[P + 1], S1[P + 1];
+            weights_at<P>((float)(sc[a] - node) + so[a], S0);
+            weights_at<P>((float)(ec[a] - node) + eo[a], S1);
+            ax[a].wb = node - P / 2;
+            ax[a].shift = 0;
+            float run = 0.f;
+#pragma unroll
+            for (int q = 0; q < P + 2; ++q) {
+                const float s0 = q <= P ? S0[q] : 0.f, s1 = q <= P ? S1[q] : 0.f;
+                ax[a].DS[q] = s1 - s0;
+                ax[a].A[q] = s0 + 0.5f * ax[a].DS[q];
+                if (q < P + 1) {
+                    run += ax[a].DS[q];
+                    ax[a].Pre[q] = coef[a] * run;
+                }
+            }
+            ax[a].Pre[P] = 0.f;  // (the window's total change is zero)
+        }
+        piece(reinterpret_cast<const Axis<P> *>(ax), t1 - t0);
+        if (!last) done |= 1u << cut_axis;
+#pragma unroll
+        for (int j = 0; j + 1 < DIM; ++j) {
+            tcut[j] = tcut[j + 1];
+            acut[j] = acut[j + 1];
+        }
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            sc[a] = ec[a];
+            so[a] = eo[a];
+        }
+        t0 = t1;
+    }
 }
 
 // Esirkepov deposit (Sec. 5.2 charge-conserving deposit):
@@ -659,7 +829,7 @@ struct SlowOut {
 // Slow path, kept out of line so that the staged fast path gets the
 // registers; arguments by value so that no fast-path variable has its
 // address taken.
-template <int DIM, int P>
+template <int DIM, int P, bool SPLIT = false>
 __device__ __noinline__ SlowOut advance_global(const Run &r, const GlobalFields gf, int c0, int c1, int c2, float e0,
                                                float e1, float e2, float u0, float u1, float u2, float w)
 {
@@ -672,17 +842,28 @@ __device__ __noinline__ SlowOut advance_global(const Run &r, const GlobalFields 
     o.ok = push_move<DIM, P>(r, gather, c, d, u, d1, k, ig);
     if (!o.ok) return o;
     const float qw = r.q * w;
-    Axis<P> ax[DIM];
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) axis_window<P>(c[a], d[a], k[a], d1[a], -qw * r.d_over_dt[a], ax[a]);
     float *J[3] = {r.J[0], r.J[1], r.J[2]};
     const int n0 = gf.n0, n1 = gf.n1, n2 = gf.n2;
-    esirkepov<DIM, P>(ax, qw * u[2] * ig, [&](int comp, int qa, int qb, int qc, float v) {
-        if (v == 0.f) return;
-        const int x = wrapi(ax[0].wb + qa, n0), y = wrapi(ax[1].wb + qb, n1);
-        const int z = DIM == 3 ? wrapi(ax[DIM - 1].wb + qc, n2) : 0;
-        atomicAdd(J[comp] + x + n0 * (y + n1 * z), v);
-    });
+    auto deposit = [&](const Axis<P> *ax, float qwvz) {
+        esirkepov<DIM, P>(ax, qwvz, [&](int comp, int qa, int qb, int qc, float v) {
+            if (v == 0.f) return;
+            const int x = wrapi(ax[0].wb + qa, n0), y = wrapi(ax[1].wb + qb, n1);
+            const int z = DIM == 3 ? wrapi(ax[DIM - 1].wb + qc, n2) : 0;
+            atomicAdd(J[comp] + x + n0 * (y + n1 * z), v);
+        });
+    };
+    if (SPLIT) {
+        float coef[3];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) coef[a] = -qw * r.d_over_dt[a];
+        const float qwvz = qw * u[2] * ig;
+        split_move<DIM, P>(c, d, k, d1, coef, [&](const Axis<P> *ax, float frac) { deposit(ax, qwvz * frac); });
+    } else {
+        Axis<P> ax[DIM];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) axis_window<P>(c[a], d[a], k[a], d1[a], -qw * r.d_over_dt[a], ax[a]);
+        deposit(ax, qw * u[2] * ig);
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         o.d[a] = d1[a];
@@ -696,10 +877,10 @@ constexpr int kStage = 6;  // field-tile rows loaded at once per thread
 
 // One work item: a tile of one run (staged fast path) or a block of that
 // run's unsorted tail (slow path).  Called uniformly by the whole CTA.
-template <int DIM, int P, int TX, int TY, int TZ, int D, bool T>
+template <int DIM, int P, int TX, int TY, int TZ, int D, int V>
 __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const Item it, int tail_block)
 {
-    using G = Geo<DIM, P, TX, TY, TZ, D, T>;
+    using G = Geo<DIM, P, TX, TY, TZ, D, V>;
     extern __shared__ __align__(16) float smem[];
     __shared__ Run rs;
     __shared__ unsigned slow_cnt;
@@ -920,6 +1101,18 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
                                 dd0[a] = d[a];
                                 dd1[a] = d1[a];
                             }
+                        } else if (G::SPLIT && __any_sync(__activemask(), moves)) {
+                            // virtual trajectories, each deposited with a no-shift window
+                            const float qw = r.q * cur.w;
+                            float coef[3];
+#pragma unroll
+                            for (int a = 0; a < DIM; ++a) coef[a] = -qw * r.d_over_dt[a];
+                            const float qwvz = qw * u[2] * ig;
+                            if (moves)
+                                split_move<DIM, P>(rel, d, k, d1, coef, [&](const Axis<P> *ax, float frac) {
+                                    if (DIM == 3) deposit3_smem<P, G>(ax, S, Jhi);
+                                    else deposit2_smem<P, G>(ax, S, qwvz * frac, Jhi);
+                                });
                         } else if (__any_sync(__activemask(), moves)) {
                             const float qw = r.q * cur.w;
                             Axis<P> ax[DIM];
@@ -935,7 +1128,7 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
                     }
                 } else {
                     ++my_slow;
-                    const SlowOut so = advance_global<DIM, P>(r, gf, c[0], c[1], c[2], d[0], d[1], d[2], u[0], u[1],
+                    const SlowOut so = advance_global<DIM, P, G::SPLIT>(r, gf, c[0], c[1], c[2], d[0], d[1], d[2], u[0], u[1],
                                                               u[2], cur.w);
                     ok = so.ok != 0;
 #pragma unroll
@@ -1042,7 +1235,7 @@ __device__ __forceinline__ bool zero_slot(const Run &r, const ZeroCtx &z, int32_
 
 // The slow path for one moving particle of a zero-field tile (reloaded from
 // its slot, so that no other state lives across the call).
-template <int DIM, int P>
+template <int DIM, int P, bool SPLIT>
 __device__ __forceinline__ void zero_mover(const Run &r, const ZeroCtx &z, const ParticleBuf &pb, long long i)
 {
     RunState *stp = r.state;
@@ -1050,7 +1243,7 @@ __device__ __forceinline__ void zero_mover(const Run &r, const ZeroCtx &z, const
     int c[3];
     unpack_cell(r, pb.cell[i], c[0], c[1], c[2]);
     const float w = pb.w ? pb.w[i] : r.w_const;
-    const SlowOut so = advance_global<DIM, P>(r, gf, c[0], c[1], c[2], pb.off[0][i], pb.off[1][i],
+    const SlowOut so = advance_global<DIM, P, SPLIT>(r, gf, c[0], c[1], c[2], pb.off[0][i], pb.off[1][i],
                                               DIM == 3 ? pb.off[2][i] : 0.f, pb.u[0][i], pb.u[1][i], pb.u[2][i], w);
     if (!so.ok) {  // non-finite or over-long move: drop the particle, latch the status
         pb.cell[i] = -1;
@@ -1072,7 +1265,7 @@ __device__ __forceinline__ void zero_mover(const Run &r, const ZeroCtx &z, const
     for (int a = 0; a < 3; ++a) pb.u[a][i] = so.u[a];
 }
 
-template <int DIM, int P>
+template <int DIM, int P, bool SPLIT>
 __global__ void __launch_bounds__(kZeroThreads, 3) push_zero_kernel(const Run *__restrict__ runs,
                                                                     const Item *__restrict__ list,
                                                                     const int *__restrict__ count)
@@ -1153,7 +1346,7 @@ __global__ void __launch_bounds__(kZeroThreads, 3) push_zero_kernel(const Run *_
                 if (pb.cell[i] < 0) continue;
                 if (pb.u[0][i] == 0.f && pb.u[1][i] == 0.f && pb.u[2][i] == 0.f) continue;
                 ++slow;
-                zero_mover<DIM, P>(r, z, pb, i);
+                zero_mover<DIM, P, SPLIT>(r, z, pb, i);
             }
             if (slow) atomicAdd(&s_slow, slow);
         }
@@ -1169,17 +1362,17 @@ __global__ void __launch_bounds__(kZeroThreads, 3) push_zero_kernel(const Run *_
 // its loop state does not compete with the item body for registers.
 // live_cnt (may be null): the items past the first n_fixed are counted on
 // the device; CTAs past the count return at once.
-template <int DIM, int P, int TX, int TY, int TZ, int D, bool T>
+template <int DIM, int P, int TX, int TY, int TZ, int D, int V>
 __global__ void __launch_bounds__(512) push_kernel(const Run *__restrict__ runs, const Item *__restrict__ items,
                                                    int tail_block, int n_fixed, const int *__restrict__ live_cnt)
 {
     if (live_cnt && (int)blockIdx.x >= n_fixed + *live_cnt) return;
-    process_item<DIM, P, TX, TY, TZ, D, T>(runs, items[blockIdx.x], tail_block);
+    process_item<DIM, P, TX, TY, TZ, D, V>(runs, items[blockIdx.x], tail_block);
 }
 
 // Persistent grid: CTAs take items from the device work queue (items
 // ordered largest first) until it is empty.
-template <int DIM, int P, int TX, int TY, int TZ, int D, bool T>
+template <int DIM, int P, int TX, int TY, int TZ, int D, int V>
 __global__ void __launch_bounds__(512) push_queue_kernel(const Run *__restrict__ runs,
                                                          const Item *__restrict__ items, int nitems, int tail_block,
                                                          int *queue, const int *__restrict__ live_cnt)
@@ -1192,20 +1385,20 @@ __global__ void __launch_bounds__(512) push_queue_kernel(const Run *__restrict__
         const int idx = s_item;
         __syncthreads();
         if (idx >= nitems) break;
-        process_item<DIM, P, TX, TY, TZ, D, T>(runs, items[idx], tail_block);
+        process_item<DIM, P, TX, TY, TZ, D, V>(runs, items[idx], tail_block);
         __syncthreads();
     }
 }
 
 // nitems: items of the launch (with live_cnt: the fixed leading items; the
 // device count of the others is added on the device, up to max_extra).
-template <int DIM, int P, int TX, int TY, int TZ, int D, bool T>
+template <int DIM, int P, int TX, int TY, int TZ, int D, int V>
 cudaError_t launch_t(const Run *runs, const Item *items, int nitems, int block, int tail_block, int *queue,
                      int persistent_ctas, cudaStream_t st, const int *live_cnt = nullptr, int max_extra = 0)
 {
-    using G = Geo<DIM, P, TX, TY, TZ, D, T>;
-    auto k = push_kernel<DIM, P, TX, TY, TZ, D, T>;
-    auto kq = push_queue_kernel<DIM, P, TX, TY, TZ, D, T>;
+    using G = Geo<DIM, P, TX, TY, TZ, D, V>;
+    auto k = push_kernel<DIM, P, TX, TY, TZ, D, V>;
+    auto kq = push_queue_kernel<DIM, P, TX, TY, TZ, D, V>;
     static bool attr_set = false;  // raise the opt-in shared-memory limit once
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
@@ -1230,17 +1423,18 @@ cudaError_t launch_t(const Run *runs, const Item *items, int nitems, int block, 
     return cudaGetLastError();
 }
 
-template <int DIM, int P>
+template <int DIM, int P, bool SPLIT = false>
 cudaError_t launch_zero(const Run *runs, const Item *list, const int *count, int max_items, int num_sms,
                         cudaStream_t st)
 {
     if (max_items <= 0) return cudaSuccess;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, push_zero_kernel<DIM, P>, kZeroThreads, 0);
+    cudaError_t e =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, push_zero_kernel<DIM, P, SPLIT>, kZeroThreads, 0);
     if (e != cudaSuccess) return e;
     int grid = num_sms * (per_sm > 0 ? per_sm : 1);
     grid = grid < max_items ? grid : max_items;
-    push_zero_kernel<DIM, P><<<grid, kZeroThreads, 0, st>>>(runs, list, count);
+    push_zero_kernel<DIM, P, SPLIT><<<grid, kZeroThreads, 0, st>>>(runs, list, count);
     return cudaGetLastError();
 }
 

@@ -81,6 +81,7 @@ def make_config(w: Workload, *, tuning: Optional[dict] = None, track_ids=False, 
     cfg.tuning.adjoint_keep = int(t.get("adjoint_keep", 0))
     cfg.tuning.sort_policy = int(t.get("sort_policy", 0))
     cfg.tuning.stream_zero_tiles = int(t.get("stream_zero_tiles", 0))
+    cfg.tuning.deposit = int(t.get("deposit", 0))
     if alloc is not None:
         cfg.alloc = alloc
         cfg.free = free

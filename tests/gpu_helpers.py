@@ -16,7 +16,7 @@ def rel_l2(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
-def oracle_for(w: inputs.Workload, capacity=None, nthreads=None):
+def oracle_for(w: inputs.Workload, capacity=None, nthreads=None, split=False):
     laser = window = None
     if w.laser is not None:
         L = w.laser
@@ -27,7 +27,7 @@ def oracle_for(w: inputs.Workload, capacity=None, nthreads=None):
         if w.knots is not None:
             window.update(knots=w.knots, z0=w.knot_z[0], z1=w.knot_z[1])
     return oracle.Sim(w.dim, w.n, w.d, w.dt, w.order, open_last=w.open_last, laser=laser, window=window,
-                      nthreads=nthreads)
+                      nthreads=nthreads, split=split)
 
 
 def load_oracle(sim, w, parts: inputs.Particles, extra=0):
@@ -58,7 +58,7 @@ def pair(w, parts, *, fields=None, tuning=None, track_ids=True, extra=0, nthread
     gpu = Simulation(w, tuning=tuning, track_ids=track_ids, per_particle_weight=per_particle_weight)
     if parts is not None and parts.n:
         gpu.load(parts)
-    orc = oracle_for(w, nthreads=nthreads)
+    orc = oracle_for(w, nthreads=nthreads, split=bool((tuning or {}).get("deposit", 0)))
     if parts is not None:
         load_oracle(orc, w, parts, extra=extra)
     if fields:
