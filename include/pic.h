@@ -186,7 +186,11 @@ typedef void (*pic_free_fn)(void *ptr, void *ctx);
  * integer positions for even orders, cell faces for odd ones) and each piece
  * is deposited on its own; for linear shapes this is Villasenor and
  * Buneman's scheme.  Compiled for the default tile of each dimension, orders
- * 1-3, without TMA staging (otherwise PIC_EINVAL). */
+ * 1-3, without TMA staging (otherwise PIC_EINVAL).
+ * j_layout: 0 = default: the current as three component arrays; 1 = one
+ * array of four-component nodes (x, y, z, unused; Sec. 5.1), each tile's
+ * current added to it by one 16-byte vector atomic per node.  Reads of
+ * PIC_JX..PIC_JZ return the same values either way. */
 typedef struct {
     int32_t tile[3];
     int32_t sort_interval;
@@ -200,6 +204,7 @@ typedef struct {
     int32_t sort_policy;
     int32_t stream_zero_tiles;
     int32_t deposit;
+    int32_t j_layout;
 } pic_tuning;
 
 typedef struct {

@@ -71,6 +71,10 @@ struct Run {
     int margin;        // particles kept while margin <= phys_last < n_last - margin
     int drift;         // fast-path allowance outside the tile (cells)
     float *E[3], *B[3], *J[3];
+    // current layout: jst = 1: J[c] are three component arrays; jst = 4: one
+    // array of float4 (x, y, z, unused) per node, J[c] = its c-th lane
+    // (Sec. 5.1's four-component current), flushed by 16-byte vector atomics
+    int jst;
     double *rho0;      // initial electron charge density (neutralising background), FP64 diagnostic
     float *mur;        // saved tangential E planes for Mur: [2][4][plane]
     ParticleBuf P[2];

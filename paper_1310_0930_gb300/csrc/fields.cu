@@ -152,9 +152,10 @@ __global__ void yee_e_kernel(const Run *__restrict__ runs, Seg seg)
         dBx_dz = (bx - Bx[mz]) * r.inv_d[2];
     }
     float nv[3];
-    nv[0] = Ex[idx] + dt * (dBz_dy - dBy_dz - r.J[0][idx]);
-    nv[1] = Ey[idx] + dt * (dBx_dz - dBz_dx - r.J[1][idx]);
-    nv[2] = Ez[idx] + dt * (dBy_dx - dBx_dy - r.J[2][idx]);
+    const long long ji = (long long)idx * r.jst;
+    nv[0] = Ex[idx] + dt * (dBz_dy - dBy_dz - r.J[0][ji]);
+    nv[1] = Ey[idx] + dt * (dBx_dz - dBz_dx - r.J[1][ji]);
+    nv[2] = Ez[idx] + dt * (dBy_dx - dBx_dy - r.J[2][ji]);
     const int nl = r.n[DIM - 1];
     const int il = phys_last(r, s, DIM == 3 ? k : j);
     if (r.open_last) {
@@ -324,9 +325,19 @@ __global__ void yee_e_quad_kernel(const Run *__restrict__ runs, Seg seg)
     unpack4(ld4(r.E[0] + idx0), ex);
     unpack4(ld4(r.E[1] + idx0), ey);
     unpack4(ld4(r.E[2] + idx0), ez);
-    unpack4(ld4(r.J[0] + idx0), jx);
-    unpack4(ld4(r.J[1] + idx0), jy);
-    unpack4(ld4(r.J[2] + idx0), jz);
+    if (r.jst == 4) {  // four-component nodes: one 16-byte load per cell
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float4 q = ld4(r.J[0] + 4ll * (idx0 + e));
+            jx[e] = q.x;
+            jy[e] = q.y;
+            jz[e] = q.z;
+        }
+    } else {
+        unpack4(ld4(r.J[0] + idx0), jx);
+        unpack4(ld4(r.J[1] + idx0), jy);
+        unpack4(ld4(r.J[2] + idx0), jz);
+    }
     const int nl = r.n[DIM - 1];
     const int il = phys_last(r, s, DIM == 3 ? k : j);
     const bool tang = r.open_last && (il == 0 || il == nl - 1);  // tangential: set by the Mur update
@@ -372,6 +383,10 @@ __global__ void zero_j_kernel(const Run *__restrict__ runs, Seg seg)
     const Run &r = runs[ri];
     const int idx = (blockIdx.x - seg.start[ri]) * blockDim.x + threadIdx.x;
     if (idx >= r.ncell) return;
+    if (r.jst == 4) {
+        reinterpret_cast<float4 *>(r.J[0])[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
     r.J[0][idx] = 0.f;
     r.J[1][idx] = 0.f;
     r.J[2][idx] = 0.f;

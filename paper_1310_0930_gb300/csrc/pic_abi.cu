@@ -94,6 +94,7 @@ struct pic_s {
     int sort_sub = 1;
     bool use_tma = false;
     bool split = false;  // virtual-trajectory deposit (pic_tuning.deposit = 1)
+    bool j4 = false;     // four-component current nodes (pic_tuning.j_layout = 1)
     int variant() const { return use_tma ? 1 : (split ? 2 : 0); }
     bool sort_adaptive = true;  // the device decides when to sort (sort_decide_kernel)
     int adjoint_keep = 0;
@@ -210,6 +211,7 @@ int validate(const pic_config *c)
     if (t.persistent < 0 || t.persistent > 2) return PIC_EINVAL;
     if (t.stream_zero_tiles < 0 || t.stream_zero_tiles > 2) return PIC_EINVAL;
     if (t.deposit < 0 || t.deposit > 1 || (t.deposit == 1 && t.tma > 0)) return PIC_EINVAL;
+    if (t.j_layout < 0 || t.j_layout > 1) return PIC_EINVAL;
     return PIC_OK;
 }
 
@@ -579,10 +581,12 @@ int init_run(pic_s *h, HostRun &hr, int idx)
     r.drift = h->drift;
     const int nl = r.n[r.dim - 1];
     const int plane = (int)(ncell / nl);
+    r.jst = h->j4 ? 4 : 1;
+    float *j4 = h->j4 ? (float *)dev_alloc(h, sizeof(float) * 4 * ncell) : nullptr;
     for (int a = 0; a < 3; ++a) {
         r.E[a] = (float *)dev_alloc(h, sizeof(float) * ncell);
         r.B[a] = (float *)dev_alloc(h, sizeof(float) * ncell);
-        r.J[a] = (float *)dev_alloc(h, sizeof(float) * ncell);
+        r.J[a] = h->j4 ? (j4 ? j4 + a : nullptr) : (float *)dev_alloc(h, sizeof(float) * ncell);
         if (!r.E[a] || !r.B[a] || !r.J[a]) return PIC_ENOMEM;
     }
     r.rho0 = (double *)dev_alloc(h, sizeof(double) * ncell);
@@ -599,7 +603,8 @@ int init_run(pic_s *h, HostRun &hr, int idx)
     for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
         e = cudaMemsetAsync(r.E[a], 0, sizeof(float) * ncell, h->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(r.B[a], 0, sizeof(float) * ncell, h->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(r.J[a], 0, sizeof(float) * ncell, h->stream);
+        if (e == cudaSuccess && (!h->j4 || a == 0))
+            e = cudaMemsetAsync(r.J[a], 0, sizeof(float) * ncell * r.jst, h->stream);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(r.rho0, 0, sizeof(double) * ncell, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(r.mur, 0, sizeof(float) * 8 * plane, h->stream);
@@ -677,6 +682,7 @@ int create_common(const pic_config *cfgs, int n, pic_t **out)
     h->sort_sub = t.sort_sub ? t.sort_sub : 1;
     h->use_tma = t.tma > 0;
     h->split = t.deposit == 1;
+    h->j4 = t.j_layout == 1;
     h->adjoint_keep = t.adjoint_keep;
     h->classify = t.stream_zero_tiles != 2;
     if (h->sort_sub < 1 || h->sort_sub > 32 || (h->sort_sub & (h->sort_sub - 1))) {
@@ -736,7 +742,7 @@ int create_common(const pic_config *cfgs, int n, pic_t **out)
         bool aligned = hr.r.n[0] % 4 == 0;
         for (int c = 0; c < 3; ++c)
             aligned = aligned && (uintptr_t)hr.r.E[c] % 16 == 0 && (uintptr_t)hr.r.B[c] % 16 == 0 &&
-                      (uintptr_t)hr.r.J[c] % 16 == 0;
+                      (uintptr_t)hr.r.J[hr.r.jst == 4 ? 0 : c] % 16 == 0;
         h->yee_quad = h->yee_quad && aligned;
     }
     int rc = upload_runs(h);
@@ -930,8 +936,13 @@ int pic_read_fields(pic_t *h, int32_t which, float *dst, size_t n_elems, int32_t
     float *src = nullptr;
     if (which < 3) src = hr.r.E[which];
     else if (which < 6) src = hr.r.B[which - 3];
-    else if (which < 9) src = hr.r.J[which - 6];
-    else {
+    else if (which < 9 && hr.r.jst == 1) src = hr.r.J[which - 6];
+    else if (which < 9) {  // one lane of the four-component nodes, gathered into the FP32 scratch
+        cudaError_t e = cudaMemcpy2DAsync(hr.rho32, sizeof(float), hr.r.J[which - 6], 4 * sizeof(float),
+                                          sizeof(float), (size_t)hr.r.ncell, cudaMemcpyDeviceToDevice, h->stream);
+        if (e != cudaSuccess) return PIC_ECUDA;
+        src = hr.rho32;
+    } else {
         if (!h->started) {
             int r2 = upload_runs(h);
             if (r2) return r2;

@@ -849,7 +849,7 @@ __device__ __noinline__ SlowOut advance_global(const Run &r, const GlobalFields 
             if (v == 0.f) return;
             const int x = wrapi(ax[0].wb + qa, n0), y = wrapi(ax[1].wb + qb, n1);
             const int z = DIM == 3 ? wrapi(ax[DIM - 1].wb + qc, n2) : 0;
-            atomicAdd(J[comp] + x + n0 * (y + n1 * z), v);
+            atomicAdd(J[comp] + (long long)(x + n0 * (y + n1 * z)) * r.jst, v);
         });
     };
     if (SPLIT) {
@@ -1181,9 +1181,16 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
             const int gy = modi(org[1] - G::JHY + ly, n1);
             const int gz = DIM == 3 ? modi(org[2] - G::JHZ + lz, n2) : 0;
             const int g = gx + n0 * (gy + n1 * gz);
+            if (r.jst == 4) {  // the node's three components in one 16-byte vector atomic
+                float v[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-                if (hi[c] | lo[c]) atomicAdd(r.J[c] + g, fmaf((float)lo[c], inv_lo, (float)hi[c] * inv));
+                for (int c = 0; c < 3; ++c) v[c] = fmaf((float)lo[c], inv_lo, (float)hi[c] * inv);
+                atomicAdd(reinterpret_cast<float4 *>(r.J[0]) + g, make_float4(v[0], v[1], v[2], 0.f));
+            } else {
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    if (hi[c] | lo[c]) atomicAdd(r.J[c] + g, fmaf((float)lo[c], inv_lo, (float)hi[c] * inv));
+            }
         }
     }
     if (threadIdx.x == 0 && slow_cnt) {

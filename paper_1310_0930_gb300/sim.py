@@ -82,6 +82,7 @@ def make_config(w: Workload, *, tuning: Optional[dict] = None, track_ids=False, 
     cfg.tuning.sort_policy = int(t.get("sort_policy", 0))
     cfg.tuning.stream_zero_tiles = int(t.get("stream_zero_tiles", 0))
     cfg.tuning.deposit = int(t.get("deposit", 0))
+    cfg.tuning.j_layout = int(t.get("j_layout", 0))
     if alloc is not None:
         cfg.alloc = alloc
         cfg.free = free
