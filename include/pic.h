@@ -165,9 +165,9 @@ typedef void (*pic_free_fn)(void *ptr, void *ctx);
  * is PIC_EINVAL.  Shape order 4: 2D 16x16 with drift 2, 3D 8x8x8 with drift 1 only.
  * use_graph: capture each step kind in a CUDA graph and replay it.
  * sort_sub: sub-buckets per tile in the sort, 0 = default (1 = none),
- * else a power of two <= 32: slot i of a tile's particles goes to sub-bucket
- * i mod sort_sub, so that the particles one warp pushes together come from
- * different cells (fewer shared-memory bank conflicts in the deposit).
+ * else a power of two <= 32 (with sort_rows = 0 or 2): slot i of a tile's
+ * particles goes to sub-bucket i mod sort_sub, so that the particles one
+ * warp pushes together come from different cells.
  * tma: 1 = stage the 3D field tile with the tensor-memory accelerator (the
  * entry 8x8x8 with drift 1, whose tile rows are then 16-byte aligned TMA
  * box rows), 0 = default (plain loads into the bank-padded tile).
@@ -190,7 +190,12 @@ typedef void (*pic_free_fn)(void *ptr, void *ctx);
  * j_layout: 0 = default: the current as three component arrays; 1 = one
  * array of four-component nodes (x, y, z, unused; Sec. 5.1), each tile's
  * current added to it by one 16-byte vector atomic per node.  Reads of
- * PIC_JX..PIC_JZ return the same values either way. */
+ * PIC_JX..PIC_JZ return the same values either way.
+ * sort_rows: 0 = default (1 unless sort_sub > 1), 1 = the sort groups each
+ * tile's particles by row of cells along x (their y and z cell in the
+ * tile), so that the particles one warp pushes together lie in one or two
+ * rows and share field-tile addresses; 2 = no order inside a tile.  Only the
+ * assignment of particles to threads changes. */
 typedef struct {
     int32_t tile[3];
     int32_t sort_interval;
@@ -205,6 +210,7 @@ typedef struct {
     int32_t stream_zero_tiles;
     int32_t deposit;
     int32_t j_layout;
+    int32_t sort_rows;
 } pic_tuning;
 
 typedef struct {

@@ -44,7 +44,8 @@ class pic_tuning(ctypes.Structure):
     _fields_ = [("tile", c_int32 * 3), ("sort_interval", c_int32), ("drift", c_int32), ("block", c_int32),
                 ("use_graph", c_int32), ("persistent", c_int32), ("sort_sub", c_int32),
                 ("tma", c_int32), ("adjoint_keep", c_int32), ("sort_policy", c_int32),
-                ("stream_zero_tiles", c_int32), ("deposit", c_int32), ("j_layout", c_int32)]
+                ("stream_zero_tiles", c_int32), ("deposit", c_int32), ("j_layout", c_int32),
+                ("sort_rows", c_int32)]
 
 
 pic_alloc_fn = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p)

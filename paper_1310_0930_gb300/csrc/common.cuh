@@ -81,7 +81,11 @@ struct Run {
     const void *tmap;  // 3D: six TMA tensor maps (E0..2, B0..2, 128 bytes each) for the field tile, or null
     int32_t *tile_off; // [ntiles + 1] particle offsets per tile
     int32_t *tile_cnt; // [ntiles * nsub] sort counters / cursors per (tile, sub-bucket)
-    int nsub;          // sort sub-buckets per tile (power of two): slot i goes to sub-bucket i % nsub
+    int nsub;          // sort sub-buckets per tile (power of two)
+    // sub-bucket of a particle: sort_rows = 1: its row of cells along x in
+    // the tile, y + ty z (y, z its cell in the tile, ty the tile's extent in
+    // y; nsub = ty tz); 0: slot i % nsub
+    int sort_rows;
     // per tile: 1 if some E or B value of the tile's own cells may be non-zero,
     // 0 if all are +0 (cleared by the first B half step, set by the second; set
     // for every tile whenever E or B is written from outside the timestep)

@@ -92,6 +92,7 @@ struct pic_s {
     int *d_scan = nullptr; // per-block sums of the sort's key scan
     Seg seg_cells{}, seg_planes{}, seg_parts{}, seg_inject{}, seg_keys{};
     int sort_sub = 1;
+    bool sort_rows = true;  // each tile's particles grouped by row of cells along x
     bool use_tma = false;
     bool split = false;  // virtual-trajectory deposit (pic_tuning.deposit = 1)
     bool j4 = false;     // four-component current nodes (pic_tuning.j_layout = 1)
@@ -212,6 +213,7 @@ int validate(const pic_config *c)
     if (t.stream_zero_tiles < 0 || t.stream_zero_tiles > 2) return PIC_EINVAL;
     if (t.deposit < 0 || t.deposit > 1 || (t.deposit == 1 && t.tma > 0)) return PIC_EINVAL;
     if (t.j_layout < 0 || t.j_layout > 1) return PIC_EINVAL;
+    if (t.sort_rows < 0 || t.sort_rows > 2 || (t.sort_rows == 1 && t.sort_sub > 1)) return PIC_EINVAL;
     return PIC_OK;
 }
 
@@ -595,6 +597,8 @@ int init_run(pic_s *h, HostRun &hr, int idx)
     r.mur = (float *)dev_alloc(h, sizeof(float) * 8 * plane);
     r.tile_off = (int32_t *)dev_alloc(h, sizeof(int32_t) * (r.ntiles + 1));
     r.nsub = h->sort_sub;
+    r.sort_rows = h->sort_rows ? 1 : 0;
+    if (r.sort_rows) r.nsub = 1 << (r.tlog[1] + (r.dim == 3 ? r.tlog[2] : 0));  // rows of cells along x
     if ((long long)r.ntiles * r.nsub > (1ll << 30)) return PIC_EINVAL;
     r.tile_cnt = (int32_t *)dev_alloc(h, sizeof(int32_t) * ((size_t)r.ntiles * r.nsub + 1));
     r.fz = (uint8_t *)dev_alloc(h, (size_t)r.ntiles);
@@ -680,6 +684,7 @@ int create_common(const pic_config *cfgs, int n, pic_t **out)
     h->use_graph = t.use_graph != 0 && h->stream != nullptr;
     h->persistent = t.persistent == 1 || (t.persistent == 0 && n > 1);
     h->sort_sub = t.sort_sub ? t.sort_sub : 1;
+    h->sort_rows = t.sort_rows == 1 || (t.sort_rows == 0 && h->sort_sub == 1);
     h->use_tma = t.tma > 0;
     h->split = t.deposit == 1;
     h->j4 = t.j_layout == 1;

@@ -170,13 +170,17 @@ struct Geo {
     // deposit_round): STG_W words per particle, one padding word per 32 slots.
     static constexpr int STG_W = 8, STG_N = 512 + 512 / 32;
     static constexpr size_t STG_BYTES = sizeof(int) * STG_W * STG_N;
-    // The staging is used for cubic and higher orders (5^3-node windows: the
-    // conflict-free atomics save more than the round's three barriers cost;
-    // measured on 256^3 warm plasma, 8 ppc: cubic 47.5 -> 30.6 ms, quadratic
-    // 17.5 -> 15.8 ms but 3D LWFA live tiles 115 -> 121 ps per particle,
-    // linear 7.1 -> 8.7 ms), where it fits next to the tiles and the kernel's
-    // static shared memory; otherwise each thread deposits its own particle.
-    static constexpr bool BK = P >= 3 && !SPLIT && SMEM_TILES + STG_BYTES + 2048 <= 232448;
+    // The staging is used from quadratic order up, where it fits next to the
+    // tiles and the kernel's static shared memory; otherwise each thread
+    // deposits its own particle.  Shared-memory atomics of a warp on one
+    // address with different values are serialised like a bank conflict, so
+    // the lanes that share a row of cells (the sort's order, which makes the
+    // gather's loads broadcasts) must not deposit together; dealt by bank the
+    // round's atomics are conflict-free.  Measured with row-ordered tiles
+    // (256^3 warm plasma, 8 ppc): quadratic push 18.4 -> 15.8 ms, 3D LWFA
+    // steps 445-500 32.3 -> 25.7 ms per step; cubic 47.5 -> 30.6 ms before
+    // row ordering.
+    static constexpr bool BK = P >= 2 && !SPLIT && SMEM_TILES + STG_BYTES + 2048 <= 232448;
     static constexpr size_t SMEM = SMEM_TILES + (BK ? STG_BYTES : 0);
 };
 

@@ -3,20 +3,23 @@
 // The GPU counterpart of the paper's particle migration between nodes after
 // the push (Sec. 3): particles that moved are regrouped with the tile that
 // now owns them, dead slots (absorbed particles) are dropped, and the tail
-// of freshly injected plasma is merged.  The key of slot i is
-// (tile, i mod nsub): each tile's particles are split into nsub sub-buckets
-// by slot index, which interleaves the particles of one cell across the
-// tile's range, so that the 32 particles a warp pushes together come from
-// different cells and their deposits hit different shared-memory banks.
+// of freshly injected plasma is merged.  The key of a particle
+// is (tile, sub-bucket).  By default the sub-bucket is the particle's row of
+// cells along x inside the tile (its y and z cell in the tile), so a tile's
+// particles come out grouped by row: the particles a warp pushes together
+// then lie in one or two rows, and their field-tile loads share addresses
+// (broadcast) or fall in adjacent banks.  Optionally (pic_tuning.sort_sub)
+// the sub-bucket of slot i is i mod nsub, which interleaves the particles of
+// a cell over the tile's range.
 // Steps, per run:
 //   1. zero the key counters;
 //   2. histogram of keys, aggregated per warp (match on the key) and per CTA
 //      (a shared-memory key table over a chunk of kSortChunk slots), so that
 //      the global counters see a few atomics per chunk;
 //   3. exclusive scan of the counters in blocks of kScanChunk keys (block
-//      sums, then each block adds the sum of the blocks before it); the
-//      counters become the scatter cursors and tile_off[t] the offset of
-//      key (t, 0);
+//      sums, an exclusive scan of the block sums, then each block adds its
+//      prefix); the counters become the scatter cursors and tile_off[t] the
+//      offset of key (t, 0);
 //   4. scatter every live particle into the alternate buffer at
 //      offset[key] + rank: ranks within the chunk come from the CTA's key
 //      table, and one cursor atomic per (chunk, key) reserves the range;
@@ -52,7 +55,7 @@ __device__ __forceinline__ int next_own_chunk(int from)
 
 // What the tile key of a packed cell depends on, held in registers.
 struct KeyCtx {
-    int b0, b1, m0, m1, t0, t1, t2, nt0, nt1, dim, open_last, origin, nl, lo, hi, nsub;
+    int b0, b1, m0, m1, t0, t1, t2, nt0, nt1, dim, open_last, origin, nl, lo, hi, nsub, rows;
     long long n_total;
 };
 
@@ -76,13 +79,19 @@ __device__ __forceinline__ KeyCtx key_ctx(const Run &r, const RunState &s)
     k.hi = r.n[r.dim - 1] - r.margin;
     k.n_total = s.n_total;
     k.nsub = r.nsub;
+    k.rows = r.sort_rows;
     return k;
 }
 
-// (tile, sub-bucket) key of slot i
-__device__ __forceinline__ int sub_key(const KeyCtx &k, int tile, long long i)
+// (tile, sub-bucket) key of slot i holding packed cell c: the cell's row
+// (y + ty z, cells within the tile) or the slot's interleave class
+__device__ __forceinline__ int sub_key(const KeyCtx &k, int tile, long long i, int32_t c)
 {
-    return tile < 0 ? -1 : tile * k.nsub + (int)(i & (k.nsub - 1));
+    if (tile < 0) return -1;
+    if (!k.rows) return tile * k.nsub + (int)(i & (k.nsub - 1));
+    const int y = (c >> k.b0) & k.m1 & ((1 << k.t1) - 1);
+    const int z = k.dim == 3 ? (c >> (k.b0 + k.b1)) & ((1 << k.t2) - 1) : 0;
+    return tile * k.nsub + y + (z << k.t1);
 }
 
 // tile key of a packed cell, or -1 for a dead slot / a particle outside the
@@ -206,7 +215,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_count_kernel(const Run *__r
         const int lane = threadIdx.x & 31;
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j) {
-            const int key = sub_key(kc, key_of_cell(kc, cell[j]), i0 + j * kSortThreads + threadIdx.x);
+            const int key = sub_key(kc, key_of_cell(kc, cell[j]), i0 + j * kSortThreads + threadIdx.x, cell[j]);
             const unsigned peers = key_peers(key);
             if (key >= 0 && lane == __ffs(peers) - 1) {
                 const int e = table_slot(t, key);
@@ -264,24 +273,51 @@ __global__ void __launch_bounds__(kScanThreads) sort_scan_local_kernel(const Run
     if (threadIdx.x == 0) sums[blockIdx.x] = all;
 }
 
-// Pass 2: block b adds the totals of the run's blocks before it; the
-// counters become the scatter cursors, tile_off[t] = cursor of key (t, 0),
-// and the last block sets tile_off[ntiles] = the run's total.
+// Pass 2: one CTA per run scans the run's block totals in place (exclusive)
+// and sets tile_off[ntiles] = the run's total.
+__global__ void __launch_bounds__(kScanThreads) sort_scan_sums_kernel(const Run *__restrict__ runs, Seg seg,
+                                                                      int *__restrict__ sums)
+{
+    __shared__ int warp_tot[kScanThreads / 32];
+    const int ri = blockIdx.x;
+    const Run &r = runs[ri];
+    if (!r.state->do_sort) return;  // CTA-uniform
+    const int b0 = seg.start[ri], nb = seg.start[ri + 1] - b0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int carry = 0;
+    for (int q0 = 0; q0 < nb; q0 += kScanThreads) {
+        const int q = q0 + threadIdx.x;
+        const int v = q < nb ? sums[b0 + q] : 0;
+        int inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) warp_tot[wid] = inc;
+        __syncthreads();
+        int before = 0, all = 0;
+        for (int w = 0; w < kScanThreads / 32; ++w) {
+            before += w < wid ? warp_tot[w] : 0;
+            all += warp_tot[w];
+        }
+        if (q < nb) sums[b0 + q] = carry + before + inc - v;
+        carry += all;
+        __syncthreads();  // (warp_tot is rewritten by the next slice)
+    }
+    if (threadIdx.x == 0) r.tile_off[r.ntiles] = carry;
+}
+
+// Pass 3: block b adds the exclusive prefix of its run's block totals; the
+// counters become the scatter cursors and tile_off[t] = cursor of key (t, 0).
 __global__ void __launch_bounds__(kScanThreads) sort_scan_add_kernel(const Run *__restrict__ runs, Seg seg,
                                                                      const int *__restrict__ sums)
 {
-    __shared__ int warp_tot[kScanThreads / 32];
     const int ri = seg_run(seg, blockIdx.x);
     const Run &r = runs[ri];
     if (!r.state->do_sort) return;  // CTA-uniform
     const int b0 = seg.start[ri], b = blockIdx.x;
-    int part = 0;
-    for (int q = b0 + threadIdx.x; q < b; q += blockDim.x) part += sums[q];
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if ((threadIdx.x & 31) == 0) warp_tot[threadIdx.x >> 5] = part;
-    __syncthreads();
-    int prefix = 0;
-    for (int w = 0; w < kScanThreads / 32; ++w) prefix += warp_tot[w];
+    const int prefix = sums[b];
     const long long nk = (long long)r.ntiles * r.nsub;
     const long long k0 = (long long)(b - b0) * kScanChunk;
     for (int q = threadIdx.x; q < kScanChunk; q += blockDim.x) {
@@ -291,7 +327,6 @@ __global__ void __launch_bounds__(kScanThreads) sort_scan_add_kernel(const Run *
         r.tile_cnt[k] = c;
         if ((k & (r.nsub - 1)) == 0) r.tile_off[k / r.nsub] = c;
     }
-    if (b == seg.start[ri + 1] - 1 && threadIdx.x == 0) r.tile_off[r.ntiles] = prefix + sums[b];
 }
 
 // Scatter: each CTA ranks its chunk's particles per key in shared memory,
@@ -330,7 +365,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) sort_scatter_kernel(const Run
         int slot[kSortItems], rank[kSortItems];
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j) {
-            const int key = sub_key(kc, key_of_cell(kc, cell[j]), i0 + j * kSortThreads + threadIdx.x);
+            const int key = sub_key(kc, key_of_cell(kc, cell[j]), i0 + j * kSortThreads + threadIdx.x, cell[j]);
             const unsigned peers = key_peers(key);
             const int leader = __ffs(peers) - 1;
             int e = -2, off = 0;
@@ -421,6 +456,7 @@ cudaError_t launch_sort(const Run *runs, int nruns, Seg parts, Seg keys, int *sc
     const int g_scatter = parts.nblocks < 12 * sms ? parts.nblocks : 12 * sms;
     sort_count_kernel<<<g_count > 0 ? g_count : 1, kSortThreads, 0, st>>>(runs, parts);
     sort_scan_local_kernel<<<keys.nblocks, kScanThreads, 0, st>>>(runs, keys, scan_sums);
+    sort_scan_sums_kernel<<<nruns, kScanThreads, 0, st>>>(runs, keys, scan_sums);
     sort_scan_add_kernel<<<keys.nblocks, kScanThreads, 0, st>>>(runs, keys, scan_sums);
     sort_scatter_kernel<<<g_scatter > 0 ? g_scatter : 1, kSortThreads, 0, st>>>(runs, parts, src_out);
     sort_finish_kernel<<<(nruns + 127) / 128, 128, 0, st>>>(runs, nruns);
