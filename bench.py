@@ -496,7 +496,7 @@ def frozen_bench(args):
                 w.mass = 1e30
             parts = inputs.background(w)
             mem = TorchMemory()
-            sim = Simulation(w, memory=mem)
+            sim = Simulation(w, memory=mem, tuning=json.loads(args.tuning) if args.tuning else None)
             sim.load(parts)
             if case == "imposed_fields":
                 z, y, x = np.meshgrid(*[np.arange(m, dtype=np.float64) for m in reversed(n)], indexing="ij")
@@ -526,6 +526,7 @@ def frozen_bench(args):
             rows["%s_order%d" % (case, order)] = {
                 "particle_steps_per_s": parts.n / (ms / 1e3), "ms_per_step": ms, "push_ms_per_step": push_ms,
                 "push_zero_ms_per_step": phases["push_zero"] / args.steps,
+                "sort_ms_per_step": phases["sort"] / args.steps, "sorts": d1["sorts"] - d0["sorts"],
                 "streamed_fraction": (d1["streamed"] - d0["streamed"]) / (parts.n * args.steps),
                 "push_roofline_frac": push_bytes / (push_ms / 1e3) / 1e9 / _peak(),
                 "clocks": clk, "status": d1["status"]}

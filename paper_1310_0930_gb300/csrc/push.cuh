@@ -717,10 +717,11 @@ __device__ __forceinline__ int window_base(int c, float d, int k, float d1)
 // base are the same for every lane, are (mostly) free of bank conflicts.
 // A particle that moves is described by its staged record: packed tile
 // coordinates and cell carries, old and new offsets, q w and (2D) q w v_z.
+// Returns the number of particles of the round that deposited.
 template <int DIM, int P, class G>
-__device__ __forceinline__ void deposit_round(const Run &r, bool dep, int pk, const float *d0, const float *d1,
-                                              float qw, float qwvz, float S, int *Jhi, int *stg, int *s_cnt,
-                                              int *s_start)
+__device__ __forceinline__ int deposit_round(const Run &r, bool dep, int pk, const float *d0, const float *d1,
+                                             float qw, float qwvz, float S, int *Jhi, int *stg, int *s_cnt,
+                                             int *s_start)
 {
     const unsigned lane = threadIdx.x & 31u;
     int bank = 0;
@@ -738,7 +739,7 @@ __device__ __forceinline__ void deposit_round(const Run &r, bool dep, int pk, co
     b0 = __shfl_sync(0xffffffffu, b0, leader);
     const int rank = b0 + __popc(m & ((1u << lane) - 1u));
     const int ndep = __syncthreads_count(dep);
-    if (ndep == 0) return;  // (uniform; the counters are all still zero)
+    if (ndep == 0) return 0;  // (uniform; the counters are all still zero)
     if (threadIdx.x < 32) {  // exclusive scan of the bucket counts
         const int c = s_cnt[lane];
         int v = c;
@@ -787,6 +788,7 @@ __device__ __forceinline__ void deposit_round(const Run &r, bool dep, int pk, co
             deposit2_smem<P, G>(reinterpret_cast<const Axis<P> *>(ax), S,
                                 __int_as_float(stg[(2 + 2 * DIM) * G::STG_N + q]), Jhi);
     }
+    return ndep;
 }
 
 template <int DIM, int P>
@@ -1045,6 +1047,7 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
     // rounds of one particle per thread, the same count for every thread (the
     // bucketed deposit synchronises the CTA once per round)
     const int nrounds = (int)((p1 - p0 + blockDim.x - 1) / blockDim.x);
+    bool dealt = G::BK && tile_item;  // CTA-uniform
     long long i = p0 + threadIdx.x;
     ParticleIn cur, nxt;
     cur.cell = -1;
@@ -1095,7 +1098,7 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
                         bool moves = DIM == 2 && u[2] != 0.f;
 #pragma unroll
                         for (int a = 0; a < DIM; ++a) moves = moves || k[a] != 0 || d1[a] != d[a];
-                        if (G::BK && tile_item) {
+                        if (dealt) {
                             dep = moves;
                             dqw = r.q * cur.w;
                             dqz = dqw * u[2] * ig;
@@ -1164,7 +1167,13 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
             }
         }
         cur = nxt;
-        if (G::BK && tile_item) deposit_round<DIM, P, G>(r, dep, dpk, dd0, dd1, dqw, dqz, S, Jhi, stg, s_cnt, s_start);
+        if (dealt) {
+            const int nd = deposit_round<DIM, P, G>(r, dep, dpk, dd0, dd1, dqw, dqz, S, Jhi, stg, s_cnt, s_start);
+            // a tile none of whose first round's particles moved (a plasma at
+            // rest in fields) deposits thread by thread from then on: no
+            // barrier per round for the few particles that may move later
+            if (rd == 0 && nd == 0) dealt = false;  // (nd is the same in every thread)
+        }
     }
     if (my_slow) atomicAdd(&slow_cnt, my_slow);
     __syncthreads();
