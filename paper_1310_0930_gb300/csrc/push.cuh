@@ -601,19 +601,20 @@ __device__ __forceinline__ void fix_add(int *hi, float ps, float fac, bool on)
 
 // 3D Esirkepov deposit into the shared-memory J tile: a loop over the three
 // components, axis roles (a, b, c) = (comp, comp+1, comp+2) selected per
-// iteration.  The last window node of an axis is visited only if some lane
-// of the warp moved its nearest node along that axis (warp-uniform branch):
-// for the common case of no node change this is 54 values instead of 144;
-// lanes that did not move along that axis skip those values by predication.
+// iteration.  Component a has W-1 prefix-sum values along a (qa) and W
+// window nodes along b and c; along an axis where the lane kept its nearest
+// node the far value (qa = W-2, qb = W-1 or qc = W-1) is zero by structure.
+// The near block is added unconditionally; each far face, edge and corner
+// the lane needs is one branch (one divergent region per face and lane
+// condition, not one per value): for the common case of no node change
+// this is 54 values instead of 144.
 template <int P, class G>
 __device__ __forceinline__ void deposit3_smem(const Axis<P> *ax, float S, int *Jhi)
 {
-    constexpr int W = P + 2;
+    constexpr int W = P + 2, NA = W - 2, NB = W - 1;  // near values: qa < NA; qb, qc < NB
     constexpr int JLO = 3 * G::JVOL;
     const float twelfth = 1.f / 12.f;
-    const unsigned act = __activemask();
     const bool m0 = ax[0].shift != 0, m1 = ax[1].shift != 0, m2 = ax[2].shift != 0;  // this lane
-    const bool f0 = __any_sync(act, m0), f1 = __any_sync(act, m1), f2 = __any_sync(act, m2);  // the warp
     const int base = (ax[0].wb + G::JHX) + G::JX * (ax[1].wb + G::JHY) + G::JPL * (ax[2].wb + G::JHZ);
     constexpr int s0 = 1, s1 = G::JX, s2 = G::JPL;
 #pragma unroll
@@ -624,36 +625,66 @@ __device__ __forceinline__ void deposit3_smem(const Axis<P> *ax, float S, int *J
             if (q < W - 1)
                 pa[q] = S * (comp == 0 ? ax[0].Pre[q] : (comp == 1 ? ax[1].Pre[q] : ax[2].Pre[q]));
             Ab[q] = comp == 0 ? ax[1].A[q] : (comp == 1 ? ax[2].A[q] : ax[0].A[q]);
-            Db[q] = comp == 0 ? ax[1].DS[q] : (comp == 1 ? ax[2].DS[q] : ax[0].DS[q]);
+            Db[q] = (comp == 0 ? ax[1].DS[q] : (comp == 1 ? ax[2].DS[q] : ax[0].DS[q])) * twelfth;
             Ac[q] = comp == 0 ? ax[2].A[q] : (comp == 1 ? ax[0].A[q] : ax[1].A[q]);
             Dc[q] = comp == 0 ? ax[2].DS[q] : (comp == 1 ? ax[0].DS[q] : ax[1].DS[q]);
         }
         const int sa = comp == 0 ? s0 : (comp == 1 ? s1 : s2);
         const int sb = comp == 0 ? s1 : (comp == 1 ? s2 : s0);
         const int sc = comp == 0 ? s2 : (comp == 1 ? s0 : s1);
-        const bool fa = comp == 0 ? f0 : (comp == 1 ? f1 : f2);
-        const bool fb = comp == 0 ? f1 : (comp == 1 ? f2 : f0);
-        const bool fc = comp == 0 ? f2 : (comp == 1 ? f0 : f1);
         const bool ma = comp == 0 ? m0 : (comp == 1 ? m1 : m2);
         const bool mb = comp == 0 ? m1 : (comp == 1 ? m2 : m0);
         const bool mc = comp == 0 ? m2 : (comp == 1 ? m0 : m1);
         int *hb = Jhi + comp * G::JVOL + base;
+        // near block, then the far a-face of each near c row
 #pragma unroll
-        for (int qc = 0; qc < W; ++qc) {
-            if (qc == W - 1 && !fc) continue;
-            const bool oc = qc < W - 1 || mc;
+        for (int qc = 0; qc < NB; ++qc) {
+            float f[NB];
 #pragma unroll
-            for (int qb = 0; qb < W; ++qb) {
-                if (qb == W - 1 && !fb) continue;
-                const bool ob = oc && (qb < W - 1 || mb);
-                const float fac = fmaf(Db[qb] * twelfth, Dc[qc], Ab[qb] * Ac[qc]);
-                const int row = qb * sb + qc * sc;
+            for (int qb = 0; qb < NB; ++qb) {
+                f[qb] = fmaf(Db[qb], Dc[qc], Ab[qb] * Ac[qc]);
 #pragma unroll
-                for (int qa = 0; qa < W - 1; ++qa) {
-                    if (qa == W - 2 && !fa) continue;
-                    fix_add<JLO>(hb + row + qa * sa, pa[qa], fac, ob && (qa < W - 2 || ma));
-                }
+                for (int qa = 0; qa < NA; ++qa) fix_add<JLO>(hb + qa * sa + qb * sb + qc * sc, pa[qa], f[qb], true);
             }
+            if (ma) {
+#pragma unroll
+                for (int qb = 0; qb < NB; ++qb) fix_add<JLO>(hb + NA * sa + qb * sb + qc * sc, pa[NA], f[qb], true);
+            }
+        }
+        // far b-face (qb = NB) over the near c rows, and its a-edge
+        if (mb) {
+            float f[NB];
+#pragma unroll
+            for (int qc = 0; qc < NB; ++qc) {
+                f[qc] = fmaf(Db[NB], Dc[qc], Ab[NB] * Ac[qc]);
+#pragma unroll
+                for (int qa = 0; qa < NA; ++qa) fix_add<JLO>(hb + qa * sa + NB * sb + qc * sc, pa[qa], f[qc], true);
+            }
+            if (ma) {
+#pragma unroll
+                for (int qc = 0; qc < NB; ++qc) fix_add<JLO>(hb + NA * sa + NB * sb + qc * sc, pa[NA], f[qc], true);
+            }
+        }
+        // far c-face (qc = NB) over the near b rows, and its a-edge
+        if (mc) {
+            float f[NB];
+#pragma unroll
+            for (int qb = 0; qb < NB; ++qb) {
+                f[qb] = fmaf(Db[qb], Dc[NB], Ab[qb] * Ac[NB]);
+#pragma unroll
+                for (int qa = 0; qa < NA; ++qa) fix_add<JLO>(hb + qa * sa + qb * sb + NB * sc, pa[qa], f[qb], true);
+            }
+            if (ma) {
+#pragma unroll
+                for (int qb = 0; qb < NB; ++qb) fix_add<JLO>(hb + NA * sa + qb * sb + NB * sc, pa[NA], f[qb], true);
+            }
+        }
+        // the (b, c) far edge and the corner
+        if (mb && mc) {
+            const float f = fmaf(Db[NB], Dc[NB], Ab[NB] * Ac[NB]);
+#pragma unroll
+            for (int qa = 0; qa < NA; ++qa) fix_add<JLO>(hb + qa * sa + NB * sb + NB * sc, pa[qa], f, true);
+            if (ma) fix_add<JLO>(hb + NA * sa + NB * sb + NB * sc, pa[NA], f, true);
         }
     }
 }
