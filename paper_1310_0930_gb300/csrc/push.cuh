@@ -689,17 +689,17 @@ __device__ __forceinline__ void deposit3_smem(const Axis<P> *ax, float S, int *J
     }
 }
 
-// 2D Esirkepov deposit into the shared-memory J tile, same skipping rule.
+// 2D Esirkepov deposit into the shared-memory J tile (J_x, J_y from the
+// in-plane moves, J_z from v_z), same rule: the near block unconditionally,
+// the far x values, the far y values and the corner each under one branch.
 template <int P, class G>
 __device__ __forceinline__ void deposit2_smem(const Axis<P> *ax, float S, float qwvz, int *Jhi)
 {
     constexpr int W = P + 2;
     constexpr int JLO = 3 * G::JVOL;
     const float twelfth = 1.f / 12.f;
-    const unsigned act = __activemask();
     const bool m0 = ax[0].shift != 0, m1 = ax[1].shift != 0;
-    const bool f0 = __any_sync(act, m0), f1 = __any_sync(act, m1);
-    const int base = (ax[0].wb + G::JHX) + G::JX * (ax[1].wb + G::JHY);
+    int *const h0 = Jhi + (ax[0].wb + G::JHX) + G::JX * (ax[1].wb + G::JHY);
     float px[W - 1], py[W - 1];
 #pragma unroll
     for (int q = 0; q < W - 1; ++q) {
@@ -707,22 +707,43 @@ __device__ __forceinline__ void deposit2_smem(const Axis<P> *ax, float S, float 
         py[q] = S * ax[1].Pre[q];
     }
     const float sz = S * qwvz;
+    // J_x at (qa, qb), qa < W - 1 prefix values; J_y at (qa, qb), qb < W - 1;
+    // J_z at every window node
+    auto jx = [&](int qa, int qb) { fix_add<JLO>(h0 + qa + G::JX * qb, px[qa], ax[1].A[qb], true); };
+    auto jy = [&](int qa, int qb) { fix_add<JLO>(h0 + G::JVOL + qa + G::JX * qb, py[qb], ax[0].A[qa], true); };
+    auto jz = [&](int qa, int qb) {
+        fix_add<JLO>(h0 + 2 * G::JVOL + qa + G::JX * qb, sz,
+                     fmaf(ax[0].DS[qa] * twelfth, ax[1].DS[qb], ax[0].A[qa] * ax[1].A[qb]), true);
+    };
 #pragma unroll
-    for (int qb = 0; qb < W; ++qb) {
-        if (qb == W - 1 && !f1) continue;
-        const bool ob = qb < W - 1 || m1;  // A_y, DS_y of this node not zero by structure
+    for (int qb = 0; qb < W - 1; ++qb) {
 #pragma unroll
-        for (int qa = 0; qa < W; ++qa) {
-            if (qa == W - 1 && !f0) continue;
-            const bool oa = qa < W - 1 || m0;
-            int *h = Jhi + base + qa + G::JX * qb;
-            if (qa < W - 1 && !(qa == W - 2 && !f0))
-                fix_add<JLO>(h, px[qa], ax[1].A[qb], ob && (qa < W - 2 || m0));
-            if (qb < W - 1 && !(qb == W - 2 && !f1))
-                fix_add<JLO>(h + G::JVOL, py[qb], ax[0].A[qa], oa && (qb < W - 2 || m1));
-            fix_add<JLO>(h + 2 * G::JVOL, sz, fmaf(ax[0].DS[qa] * twelfth, ax[1].DS[qb], ax[0].A[qa] * ax[1].A[qb]),
-                         oa && ob);
+        for (int qa = 0; qa < W - 1; ++qa) {
+            if (qa < W - 2) jx(qa, qb);
+            if (qb < W - 2) jy(qa, qb);
+            jz(qa, qb);
         }
+    }
+    if (m0) {  // far x: J_x at qa = W - 2, J_y and J_z at qa = W - 1
+#pragma unroll
+        for (int qb = 0; qb < W - 1; ++qb) {
+            jx(W - 2, qb);
+            if (qb < W - 2) jy(W - 1, qb);
+            jz(W - 1, qb);
+        }
+    }
+    if (m1) {  // far y: J_y at qb = W - 2, J_x and J_z at qb = W - 1
+#pragma unroll
+        for (int qa = 0; qa < W - 1; ++qa) {
+            if (qa < W - 2) jx(qa, W - 1);
+            jy(qa, W - 2);
+            jz(qa, W - 1);
+        }
+    }
+    if (m0 && m1) {
+        jx(W - 2, W - 1);
+        jy(W - 1, W - 2);
+        jz(W - 1, W - 1);
     }
 }
 
