@@ -220,7 +220,9 @@ typedef struct {
                             and no adjoint form */
     pic_grid grid;
     int32_t n_species;   /* must be 1 */
-    int32_t track_ids;   /* 1: keep a per-particle int32 id through sorts */
+    int32_t track_ids;   /* 1: keep a per-particle int32 id through sorts: the n loaded
+                            particles 0 .. n-1 in load order, the k-th window shift's
+                            layer of m particles n + (k-1) m + j (-1 past 2^31 - 1) */
     const pic_species *species;
     pic_laser laser;
     pic_window window;
@@ -325,9 +327,13 @@ PIC_API int pic_profile_end(pic_t *h, double *ms, int32_t n_phases, int64_t *lau
  * window" of the last axis, positions in window-frame cells):
  *   L = sum w K sigma / sum w sigma,  K = m (gamma - 1),
  *   sigma(z) = logistic((z - z_lo)/width) * logistic((z_hi - z)/width).
- * Requirements: a single run, track_ids = 1, per_particle_weight = 1, no
- * moving window, shape order 1-3 with the default deposit, particles loaded,
- * no step taken yet. */
+ * Requirements: a single run, track_ids = 1, per_particle_weight = 1, shape
+ * order 1-3 with the default deposit, particles loaded, no step taken yet.
+ * With a moving window the gradient includes the plasma the window injects
+ * (its weights follow the density knots at the lab position of injection);
+ * the forward run's ids then also number the injected particles: the k-th
+ * shift's layer (k = 1, 2, ...) gets ids n + (k - 1) m .. n + k m - 1, n the
+ * loaded particles, m the particles of one layer. */
 typedef struct {
     double z_lo, z_hi, width;
 } pic_objective;
@@ -349,8 +355,8 @@ PIC_API int pic_objective_value(pic_t *h, const pic_objective *obj, double *L);
 
 /* After exactly total_steps forward steps: L, dL/da0 (laser amplitude),
  * dL/dknots[n_knots] (the piecewise-linear density profile of pic_species:
- * w = density(z at load) / prod(ppc)) and dL/dw[n] per particle id (host
- * arrays; any output may be NULL).  The handle is left in a recomputed
+ * w = density(z at load or injection) / prod(ppc)) and dL/dw[n] for the ids
+ * of the n loaded particles (host arrays; any output may be NULL).  The handle is left in a recomputed
  * intermediate state and cannot be stepped further (PIC_ESTATE). */
 PIC_API int pic_adjoint_backward(pic_t *h, const pic_objective *obj, double *L, double *dL_da0, double *dL_dknots,
                                  int32_t n_knots, double *dL_dw);

@@ -749,7 +749,7 @@ __global__ void __launch_bounds__(128, 3) adj_particles_kernel(const Run *__rest
                                                                int origin)
 {
     const Run &r = *run;
-    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long s = ts.first + (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= ts.n) return;
     int c[3] = {0, 0, 0};
     if (!adj_live<DIM>(r, ts.cell[s], origin, c)) return;
@@ -865,11 +865,12 @@ __global__ void __launch_bounds__(128, 3) adj_particles_tiled_kernel(const Run *
     }
 }
 
-__global__ void adj_perm_kernel(AdjPtrs A, const int32_t *__restrict__ id, long long n, int dim, int to_slots)
+__global__ void adj_perm_kernel(AdjPtrs A, const int32_t *__restrict__ id, long long n, long long nid, int dim,
+                                int to_slots)
 {
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
         const int i = id[s];
-        if (i < 0 || i >= n) continue;
+        if (i < 0 || i >= nid) continue;
         if (to_slots) {
             for (int a = 0; a < dim; ++a) A.sx[a][s] = A.lx[a][i];
             for (int a = 0; a < 3; ++a) A.su[a][s] = A.lu[a][i];
@@ -879,6 +880,36 @@ __global__ void adj_perm_kernel(AdjPtrs A, const int32_t *__restrict__ id, long 
             for (int a = 0; a < 3; ++a) A.lu[a][i] = A.su[a][s];
             A.lw[i] = A.sw[s];
         }
+    }
+}
+
+// Transpose of a moving-window shift at the end of a step, applied before
+// that step's field and particle transposes.  The forward set E and B on the
+// new front plane (storage index store_plane of the last axis) to zero, so
+// their adjoints there are zero; and it appended a cold layer of particles
+// at slots slot0 + j with ids id0 + j, whose positions and momenta are
+// constants: only their weights depend on the parameters, so their weight
+// adjoints go to id order and their slot adjoints are cleared (slot0 < 0: the
+// layer's adjoints are already in id order, at a segment's last step).
+__global__ void adj_window_kernel(AdjPtrs A, int plane, int store_plane, long long slot0, long long count,
+                                  long long id0, long long nid)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < plane) {
+        const long long idx = q + (long long)plane * store_plane;
+        for (int c = 0; c < 3; ++c) {
+            A.lE[c][idx] = 0.f;
+            A.lB[c][idx] = 0.f;
+        }
+    }
+    if (slot0 >= 0 && q < count) {
+        const long long slot = slot0 + q, id = id0 + q;
+        if (id < nid) A.lw[id] = A.sw[slot];
+        for (int a = 0; a < 3; ++a) {
+            if (A.sx[a]) A.sx[a][slot] = 0.f;
+            A.su[a][slot] = 0.f;
+        }
+        A.sw[slot] = 0.0;
     }
 }
 
@@ -943,6 +974,7 @@ __global__ void obj_seed_kernel(const Run *__restrict__ run, int origin, ObjArgs
         float w, z, sig, dsig;
         if (!obj_particle(r, pb, i, origin, o, w, z, sig, dsig)) continue;
         const int id = pb.id[i];
+        if (id < 0 || id >= r.adj_nid) continue;
         const float ux = pb.u[0][i], uy = pb.u[1][i], uz = pb.u[2][i];
         const float gam = sqrtf(1.f + ux * ux + uy * uy + uz * uz);
         const float K = r.m * (gam - 1.f);
@@ -985,16 +1017,18 @@ __global__ void knots_kernel(const double *lw, const float *zb, long long n, int
         if (acc[k] != 0.0) atomicAdd(out + k, acc[k]);
 }
 
-// weights and birth positions by id (the load order, before any sort)
-__global__ void adj_init_kernel(const Run *__restrict__ run, float *wid, float *zb, long long n)
+// weights and birth positions by id of the loaded particles (the load
+// order, before any sort; the window's injection writes those of the ids it
+// creates)
+__global__ void adj_init_kernel(const Run *__restrict__ run, float *wid, float *zb, long long n, long long nid)
 {
     const Run &r = *run;
     const RunState &s = *r.state;
     const ParticleBuf pb = r.P[s.buf];
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n && i < s.n_total;
          i += (long long)gridDim.x * blockDim.x) {
         const int id = pb.id[i];
-        if (id < 0 || id >= n) continue;
+        if (id < 0 || id >= nid) continue;
         wid[id] = pb.w ? pb.w[i] : r.w_const;
         int c[3];
         unpack_cell(r, pb.cell[i] < 0 ? 0 : pb.cell[i], c[0], c[1], c[2]);
@@ -1030,8 +1064,17 @@ __device__ __forceinline__ void copy4(int32_t *dc, float *const *doff, float *co
             *reinterpret_cast<float4 *>(du[a] + i) = *reinterpret_cast<const float4 *>(su[a] + i);
         if (dw && sw) *reinterpret_cast<float4 *>(dw + i) = *reinterpret_cast<const float4 *>(sw + i);
         if (did) {
-            if (sid) *reinterpret_cast<int4 *>(did + i) = *reinterpret_cast<const int4 *>(sid + i);
-            else *reinterpret_cast<int4 *>(did + i) = make_int4(-1, -1, -1, -1);
+            int4 v = make_int4(-1, -1, -1, -1);
+            if (sid) {
+                v = *reinterpret_cast<const int4 *>(sid + i);
+                if (fill_dead) {  // (a dead slot keeps no id: its data is stale)
+                    v.x = i < n_live ? v.x : -1;
+                    v.y = i + 1 < n_live ? v.y : -1;
+                    v.z = i + 2 < n_live ? v.z : -1;
+                    v.w = i + 3 < n_live ? v.w : -1;
+                }
+            }
+            *reinterpret_cast<int4 *>(did + i) = v;
         }
         return;
     }
@@ -1042,7 +1085,7 @@ __device__ __forceinline__ void copy4(int32_t *dc, float *const *doff, float *co
 #pragma unroll
         for (int a = 0; a < 3; ++a) du[a][j] = su[a][j];
         if (dw && sw) dw[j] = sw[j];
-        if (did) did[j] = sid ? sid[j] : -1;
+        if (did) did[j] = sid && (!fill_dead || j < n_live) ? sid[j] : -1;
     }
 }
 
@@ -1118,7 +1161,7 @@ cudaError_t launch_adj_t(const Run *run, const Run &hr, const AdjPtrs &A, const 
 {
     constexpr int kAdjBlock = 128;  // matches the kernels' launch bounds
     if (!ts.tile_off) {
-        const unsigned g = (unsigned)((ts.n + kAdjBlock - 1) / kAdjBlock);
+        const unsigned g = (unsigned)((ts.n - ts.first + kAdjBlock - 1) / kAdjBlock);
         adj_particles_kernel<DIM, P><<<g, kAdjBlock, 0, st>>>(run, A, ts, origin);
         return cudaGetLastError();
     }
@@ -1154,7 +1197,7 @@ cudaError_t launch_adj_t(const Run *run, const Run &hr, const AdjPtrs &A, const 
 cudaError_t launch_adj_particles(int dim, int order, const Run *run, const Run &hr, const AdjPtrs &A,
                                  const TrajStep &ts, int origin, cudaStream_t st)
 {
-    if (ts.n <= 0) return cudaSuccess;
+    if (ts.n <= ts.first) return cudaSuccess;
     if (dim == 2) {
         if (order == 1) return launch_adj_t<2, 1>(run, hr, A, ts, origin, st);
         if (order == 2) return launch_adj_t<2, 2>(run, hr, A, ts, origin, st);
@@ -1177,9 +1220,18 @@ cudaError_t launch_objective(const Run *run, int origin, const ObjArgs &o, doubl
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_perm(int dim, const AdjPtrs &A, const int32_t *id, long long n, int to_slots, cudaStream_t st)
+cudaError_t launch_adj_perm(int dim, const AdjPtrs &A, const int32_t *id, long long n, long long nid, int to_slots,
+                            cudaStream_t st)
 {
-    adj_perm_kernel<<<blocks_for(n), kBlock, 0, st>>>(A, id, n, dim, to_slots);
+    adj_perm_kernel<<<blocks_for(n), kBlock, 0, st>>>(A, id, n, nid, dim, to_slots);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_window(const AdjPtrs &A, int plane, int store_plane, long long slot0, long long count,
+                              long long id0, long long nid, cudaStream_t st)
+{
+    const long long m = plane > count ? plane : count;
+    adj_window_kernel<<<blocks_for(m), kBlock, 0, st>>>(A, plane, store_plane, slot0, count, id0, nid);
     return cudaGetLastError();
 }
 
@@ -1210,9 +1262,9 @@ cudaError_t launch_record(int dim, const Run *run, const PartCopy &pc, long long
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_init(const Run *run, float *wid, float *zb, long long n, cudaStream_t st)
+cudaError_t launch_adj_init(const Run *run, float *wid, float *zb, long long n, long long nid, cudaStream_t st)
 {
-    adj_init_kernel<<<blocks_for(n), kBlock, 0, st>>>(run, wid, zb, n);
+    adj_init_kernel<<<blocks_for(n), kBlock, 0, st>>>(run, wid, zb, n, nid);
     return cudaGetLastError();
 }
 

@@ -102,6 +102,14 @@ struct Run {
     const double *knots;  // device copy of the density knots (may be nullptr)
     int n_knots;
     double z0, z1;
+    // particle ids (track_ids): the loaded particles have ids 0 .. id_base-1;
+    // the injection of shift k (1, 2, ...) gives its layer of `count`
+    // particles the ids id_base + (k - 1) count + j
+    long long id_base;
+    // adjoint form armed: birth positions (lab frame, last axis) by id, which
+    // the injection writes for the ids it creates (< adj_nid); else null
+    float *adj_zb;
+    long long adj_nid;
     RunState *state;
 };
 

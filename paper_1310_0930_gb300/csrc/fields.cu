@@ -502,7 +502,8 @@ __device__ double profile_density(const Run &r, double z)
 }
 
 // Inject one cold, regularly placed layer of cells at physical last-axis
-// index nl - margin - 1 (appended to the unsorted tail).
+// index nl - margin - 1 (appended to the unsorted tail, slot n_total + j for
+// the j-th particle of the layer).
 __global__ void window_inject_kernel(const Run *__restrict__ runs, Seg seg)
 {
     const int ri = seg_run(seg, blockIdx.x);
@@ -542,11 +543,13 @@ __global__ void window_inject_kernel(const Run *__restrict__ runs, Seg seg)
     pb.u[0][slot] = 0.f;
     pb.u[1][slot] = 0.f;
     pb.u[2][slot] = 0.f;
-    if (pb.w) {
-        const double zlab = ((double)kcell + (double)off_last + (double)s.shifts) * r.d_last_d;
-        pb.w[slot] = (float)(profile_density(r, zlab) / ppc_t);
+    const double zlab = ((double)kcell + (double)off_last + (double)s.shifts) * r.d_last_d;
+    if (pb.w) pb.w[slot] = (float)(profile_density(r, zlab) / ppc_t);
+    if (pb.id) {
+        const long long id = r.id_base + (long long)(s.shifts - 1) * count + q;
+        pb.id[slot] = id < 2147483647ll ? (int32_t)id : -1;
+        if (r.adj_zb && id < r.adj_nid) r.adj_zb[id] = (float)zlab;
     }
-    if (pb.id) pb.id[slot] = -1;
 }
 
 __global__ void window_commit_kernel(const Run *__restrict__ runs, int nruns)

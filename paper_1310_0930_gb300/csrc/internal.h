@@ -130,6 +130,7 @@ struct TrajStep {
     const int32_t *src;       // slot each particle had before the sort of this step (null: no sort);
                               // outputs then go to ox/ou/ow at that slot
     long long n;
+    long long first;  // flat kernel: slots [first, n)
     const float *E[3];
     const float *B[3];
 };
@@ -146,7 +147,8 @@ cudaError_t launch_objective(const Run *run, int origin, const ObjArgs &o, doubl
                              const AdjPtrs &A, cudaStream_t st);
 cudaError_t launch_knots(const double *lw, const float *zb, long long n, int n_knots, double z0, double z1,
                          double ppc_t, double *out, cudaStream_t st);
-cudaError_t launch_adj_init(const Run *run, float *wid, float *zb, long long n, cudaStream_t st);
+// n: particle slots to read, nid: ids the arrays hold
+cudaError_t launch_adj_init(const Run *run, float *wid, float *zb, long long n, long long nid, cudaStream_t st);
 struct PartCopy {
     int32_t *cell;
     float *off[3];
@@ -169,6 +171,13 @@ struct FieldCopy {
 cudaError_t launch_record(int dim, const Run *run, const PartCopy &pc, long long n, const FieldCopy &fc,
                           cudaStream_t st);
 // move the particle adjoints between id order and the slot order of a record
-cudaError_t launch_adj_perm(int dim, const AdjPtrs &A, const int32_t *id, long long n, int to_slots, cudaStream_t st);
+// slot adjoints of n slots to (to_slots = 0) or from (1) id order, ids < nid
+cudaError_t launch_adj_perm(int dim, const AdjPtrs &A, const int32_t *id, long long n, long long nid, int to_slots,
+                            cudaStream_t st);
+// transpose of a window shift: field adjoints zeroed on storage plane
+// store_plane of the last axis (plane cells each); the injected layer at
+// slots slot0 .. slot0+count-1 (ids id0 + j) moved to id order (slot0 < 0: skip)
+cudaError_t launch_adj_window(const AdjPtrs &A, int plane, int store_plane, long long slot0, long long count,
+                              long long id0, long long nid, cudaStream_t st);
 
 }  // namespace pic

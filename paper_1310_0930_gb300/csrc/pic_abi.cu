@@ -35,6 +35,7 @@ struct HostRun {
     std::vector<double> knots;
     Run r;
     long long inject_per_shift = 0;
+    long long loaded = 0;   // particles loaded (their ids are 0 .. loaded-1)
     double *rho = nullptr;  // diagnostics scratch (charge density, FP64)
     float *rho32 = nullptr; // FP32 copy for pic_read_fields(PIC_RHO)
 };
@@ -51,12 +52,15 @@ struct Rec {
     int32_t *src;       // after a sort: the slot each particle had before it
     float *E[3], *B[3];
     int32_t *tile_off;  // tile offsets of the last sort (the slots' grouping)
+    RunState *st;       // the run state the push of this step starts from (device)
     double time;
     bool sorted;  // a tile sort ran just before this record (slot order changed)
 };
 struct Adj {
     int K = 1, total = 0, nck = 0;
-    long long nid = 0;
+    long long nid = 0;     // particle ids the adjoint arrays hold (loaded + injected during the run)
+    long long nslot = 0;   // particle slots the records and slot adjoints hold
+    long long nload = 0;   // loaded particles (ids 0 .. nload-1; dL/dw is reported for them)
     AdjPtrs A{};
     float *zb = nullptr;
     double *la0 = nullptr, *red = nullptr, *dk = nullptr;
@@ -409,7 +413,8 @@ int enqueue_step(pic_s *h, bool sort, bool adaptive)
         fc.toff_src = r0.tile_off;
         fc.toff_dst = rc.tile_off;
         fc.nt = r0.ntiles + 1;
-        e = launch_record(h->dim, R, rc.pc, h->adj->nid, fc, st);
+        e = launch_record(h->dim, R, rc.pc, h->adj->nslot, fc, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(rc.st, h->d_states, sizeof(RunState), cudaMemcpyDeviceToDevice, st);
     }
     mark(PIC_PH_ZERO_J);
     if (e == cudaSuccess) e = launch_zero_j(R, h->seg_cells, st);
@@ -457,6 +462,7 @@ int first_step_setup(pic_s *h)
     std::vector<long long> parts(h->nruns), inj(h->nruns);
     for (int i = 0; i < h->nruns; ++i) {
         HostRun &hr = h->runs[i];
+        hr.r.id_base = hr.loaded;  // the window's injected particles are numbered after the loaded ones
         if (!hr.r.P[0].cell) {  // never loaded: give it the injection room only
             long long cap = (long long)(h->sort_interval + 2) * hr.inject_per_shift + 4096;
             int rc = alloc_particles(h, hr, cap, 0, 0);
@@ -820,6 +826,7 @@ int pic_load_particles(pic_t *h, int32_t species, int64_t n, const int32_t *cell
     if (e == cudaSuccess) e = launch_set_count(h->d_runs + h->cur, need, 0, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     dev_free(h, stage);
+    hr.loaded = need;
     if (e != cudaSuccess) return PIC_ECUDA;
     if (cudaMemcpy(&st, h->d_states + h->cur, sizeof(RunState), cudaMemcpyDeviceToHost) != cudaSuccess)
         return PIC_ECUDA;
@@ -845,7 +852,7 @@ int pic_step(pic_t *h, int32_t nsteps)
             h->steps_done / h->adj->K < h->adj->nck) {
             Ckpt &ck = h->adj->ck[h->steps_done / h->adj->K];
             const Run &r0 = h->runs[0].r;
-            cudaError_t e = launch_part_copy(h->dim, h->d_runs, ck.pc, h->adj->nid, 0, h->stream);
+            cudaError_t e = launch_part_copy(h->dim, h->d_runs, ck.pc, h->adj->nslot, 0, h->stream);
             for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
                 e = cudaMemcpyAsync(ck.E[c], r0.E[c], sizeof(float) * r0.ncell, cudaMemcpyDeviceToDevice, h->stream);
                 if (e == cudaSuccess)
@@ -1118,23 +1125,36 @@ int pic_adjoint_begin(pic_t *h, int32_t total_steps, int32_t checkpoint_every)
     if (!h || total_steps < 1 || checkpoint_every < 1) return PIC_EINVAL;
     if (h->started || h->adj || h->nruns != 1) return PIC_ESTATE;
     HostRun &hr = h->runs[0];
-    if (!hr.cfg.track_ids || !hr.sp.per_particle_weight || hr.r.window_on || !hr.r.P[0].cell) return PIC_EINVAL;
+    if (!hr.cfg.track_ids || !hr.sp.per_particle_weight || !hr.r.P[0].cell) return PIC_EINVAL;
     if (h->order > 3) return PIC_EINVAL;  // (the reverse kernels are compiled for orders 1 to 3)
     if (h->split) return PIC_EINVAL;      // (they transpose the undivided deposit)
     RunState st;
     int rc = read_state(h, 0, &st);
     if (rc) return rc;
     if (st.n_total <= 0) return PIC_EINVAL;
+    Run &r = hr.r;
+    // ids: the loaded particles, and with a moving window the layers it can
+    // inject during the run; slots: with a window every slot of the buffers
+    const long long n0 = st.n_total;
+    long long nid = n0, nslot = n0;
+    if (r.window_on) {
+        const double travel = r.window_v * (st.time + (double)total_steps * r.dt_d - r.window_t0);
+        const long long max_shifts = travel > 0.0 ? (long long)(travel / r.d_last_d) + 2 : 0;
+        nid = n0 + max_shifts * hr.inject_per_shift;
+        nslot = r.capacity;
+        if (nid >= 2147483647ll) return PIC_EINVAL;  // (ids are int32)
+    }
     Adj *a = new (std::nothrow) Adj();
     if (!a) return PIC_ENOMEM;
     h->adj = a;
-    const Run &r = hr.r;
-    const long long n = st.n_total, nc = r.ncell;
+    const long long n = nslot, nc = r.ncell;
     const int dim = r.dim;
     a->K = checkpoint_every;
     a->total = total_steps;
     a->nck = (total_steps + checkpoint_every - 1) / checkpoint_every;
-    a->nid = n;
+    a->nid = nid;
+    a->nslot = nslot;
+    a->nload = n0;
     auto F = [&](long long cnt) { return (float *)dev_alloc(h, sizeof(float) * cnt); };
     bool ok = true;
     for (int c = 0; c < 3; ++c) {
@@ -1143,8 +1163,8 @@ int pic_adjoint_begin(pic_t *h, int32_t total_steps, int32_t checkpoint_every)
         a->A.lJ[c] = F(nc);
         a->A.T[c] = F(nc);
         a->A.nE[c] = F(nc);
-        a->A.lu[c] = F(n);
-        a->A.lx[c] = c < dim ? F(n) : nullptr;
+        a->A.lu[c] = F(nid);
+        a->A.lx[c] = c < dim ? F(nid) : nullptr;
         a->A.su[c] = F(n);
         a->A.sx[c] = c < dim ? F(n) : nullptr;
         a->A.ou[c] = F(n);
@@ -1153,12 +1173,12 @@ int pic_adjoint_begin(pic_t *h, int32_t total_steps, int32_t checkpoint_every)
              (c >= dim || a->A.lx[c]) && a->A.su[c] && (c >= dim || a->A.sx[c]) && a->A.ou[c] &&
              (c >= dim || a->A.ox[c]);
     }
-    a->A.lw = (double *)dev_alloc(h, sizeof(double) * n);
+    a->A.lw = (double *)dev_alloc(h, sizeof(double) * nid);
     a->A.sw = (double *)dev_alloc(h, sizeof(double) * n);
     a->A.ow = (double *)dev_alloc(h, sizeof(double) * n);
     ok = ok && a->A.sw && a->A.ow;
-    a->A.wid = F(n);
-    a->zb = F(n);
+    a->A.wid = F(nid);
+    a->zb = F(nid);
     a->la0 = (double *)dev_alloc(h, sizeof(double) * 4);
     a->red = (double *)dev_alloc(h, sizeof(double) * 4);
     a->dk = (double *)dev_alloc(h, sizeof(double) * 1024);
@@ -1190,7 +1210,8 @@ int pic_adjoint_begin(pic_t *h, int32_t total_steps, int32_t checkpoint_every)
         rc2.pc = part(true);
         rc2.tile_off = (int32_t *)dev_alloc(h, sizeof(int32_t) * (r.ntiles + 1));
         rc2.src = (int32_t *)dev_alloc(h, sizeof(int32_t) * n);
-        bool good = rc2.tile_off && rc2.src && rc2.pc.cell && rc2.pc.id && rc2.pc.u[2];
+        rc2.st = (RunState *)dev_alloc(h, sizeof(RunState));
+        bool good = rc2.tile_off && rc2.src && rc2.st && rc2.pc.cell && rc2.pc.id && rc2.pc.u[2];
         for (int c = 0; c < 3; ++c) {
             rc2.E[c] = F(nc);
             rc2.B[c] = F(nc);
@@ -1227,9 +1248,12 @@ int pic_adjoint_begin(pic_t *h, int32_t total_steps, int32_t checkpoint_every)
     }
     a->keep = keep;
     a->keep_base = (a->nck - keep) * a->K;
+    r.id_base = n0;  // (as the first step sets it)
+    r.adj_zb = a->zb;
+    r.adj_nid = nid;
     rc = upload_runs(h);
     if (rc) return rc;
-    cudaError_t e = launch_adj_init(h->d_runs, a->A.wid, a->zb, n, h->stream);
+    cudaError_t e = launch_adj_init(h->d_runs, a->A.wid, a->zb, n, nid, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return PIC_ECUDA;
     // checkpoints are taken between graph replays; the recording steps of
@@ -1286,17 +1310,17 @@ int pic_adjoint_backward(pic_t *h, const pic_objective *obj, double *L, double *
     int rc = objective_reduce(h, obj, &Lv);
     if (rc) return rc;
     if (L) *L = Lv;
-    const long long n = a.nid, nc = r.ncell;
+    const long long n = a.nslot, nid = a.nid, nc = r.ncell;
     const int dim = r.dim;
     cudaStream_t st = h->stream;
     cudaError_t e = cudaSuccess;
     for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
         e = cudaMemsetAsync(a.A.lE[c], 0, sizeof(float) * nc, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(a.A.lB[c], 0, sizeof(float) * nc, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(a.A.lu[c], 0, sizeof(float) * n, st);
-        if (e == cudaSuccess && c < dim) e = cudaMemsetAsync(a.A.lx[c], 0, sizeof(float) * n, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(a.A.lu[c], 0, sizeof(float) * nid, st);
+        if (e == cudaSuccess && c < dim) e = cudaMemsetAsync(a.A.lx[c], 0, sizeof(float) * nid, st);
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(a.A.lw, 0, sizeof(double) * n, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.A.lw, 0, sizeof(double) * nid, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.la0, 0, sizeof(double), st);
     const ObjArgs o{(float)obj->z_lo, (float)obj->z_hi, (float)obj->width};
     RunState cur;
@@ -1306,6 +1330,10 @@ int pic_adjoint_backward(pic_t *h, const pic_objective *obj, double *L, double *
     if (e != cudaSuccess) return PIC_ECUDA;
     const int plane = r.ncell / r.n[dim - 1];
     a.rec_on = false;
+    // window shifts: the step before a record whose shift count is larger
+    // ended with a shift (at most one per step)
+    int next_shifts = cur.shifts;
+    std::vector<RunState> hst(a.K);
     for (int seg = a.nck - 1; seg >= 0; --seg) {
         const int s0 = seg * a.K, s1 = s0 + a.K < a.total ? s0 + a.K : a.total;
         const bool kept = seg >= a.nck - a.keep;  // recorded by the forward run
@@ -1331,14 +1359,35 @@ int pic_adjoint_backward(pic_t *h, const pic_objective *obj, double *L, double *
         a.rec_on = false;
         if (rc) return rc;
         }
+        // the run states the segment's pushes started from (origin, slot counts)
+        for (int s = s0; s < s1 && e == cudaSuccess; ++s)
+            e = cudaMemcpyAsync(&hst[s - s0], a.rec[s - rb].st, sizeof(RunState), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         // particle adjoints follow the slot order of each record: they move to
         // the slots before a sort through the sort's record of them, and
         // through id order at segment ends
-        e = launch_adj_perm(dim, a.A, a.rec[s1 - 1 - rb].pc.id, n, 1, st);
+        for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+            e = cudaMemsetAsync(a.A.su[c], 0, sizeof(float) * n, st);
+            if (e == cudaSuccess && c < dim) e = cudaMemsetAsync(a.A.sx[c], 0, sizeof(float) * n, st);
+        }
+        if (e == cudaSuccess) e = cudaMemsetAsync(a.A.sw, 0, sizeof(double) * n, st);
+        if (e == cudaSuccess) e = launch_adj_perm(dim, a.A, a.rec[s1 - 1 - rb].pc.id, n, nid, 1, st);
         if (e != cudaSuccess) return PIC_ECUDA;
         for (int s = s1 - 1; s >= s0; --s) {
             const Rec &rc2 = a.rec[s - rb];
-            e = launch_adj_fields(dim, h->d_runs, a.A, (int)nc, plane, 0, rc2.time, r.dt_d, r.laser_on, a.la0, st);
+            const RunState &rs = hst[s - s0];
+            if (next_shifts > rs.shifts) {
+                // the step ended with a window shift: zeroed front plane (storage
+                // index = this step's origin) and an injected layer appended at
+                // slot rs.n_total; inside the segment its slot adjoints go to id
+                // order here, at the segment's last step they are there already
+                e = launch_adj_window(a.A, plane, rs.origin, s < s1 - 1 ? rs.n_total : -1, hr.inject_per_shift,
+                                      r.id_base + (long long)(next_shifts - 1) * hr.inject_per_shift, nid, st);
+                if (e != cudaSuccess) return PIC_ECUDA;
+            }
+            next_shifts = rs.shifts;
+            e = launch_adj_fields(dim, h->d_runs, a.A, (int)nc, plane, rs.origin, rc2.time, r.dt_d, r.laser_on, a.la0,
+                                  st);
             TrajStep ts{};
             ts.cell = rc2.pc.cell;
             for (int c = 0; c < 3; ++c) {
@@ -1351,6 +1400,7 @@ int pic_adjoint_backward(pic_t *h, const pic_objective *obj, double *L, double *
             ts.w = rc2.pc.w;
             ts.tile_off = rc2.tile_off;
             ts.n = n;
+            ts.first = 0;
             // after a sort inside the segment the kernel writes the adjoints at
             // the slots of the previous record (zero for particles the sort dropped)
             const bool moved = s > s0 && rc2.sorted;
@@ -1360,7 +1410,16 @@ int pic_adjoint_backward(pic_t *h, const pic_objective *obj, double *L, double *
                 if (e == cudaSuccess && c < dim) e = cudaMemsetAsync(a.A.ox[c], 0, sizeof(float) * n, st);
             }
             if (e == cudaSuccess && moved) e = cudaMemsetAsync(a.A.ow, 0, sizeof(double) * n, st);
-            if (e == cudaSuccess) e = launch_adj_particles(dim, r.order, h->d_runs, r, a.A, ts, 0, st);
+            if (e == cudaSuccess) e = launch_adj_particles(dim, r.order, h->d_runs, r, a.A, ts, rs.origin, st);
+            if (e == cudaSuccess && rs.n_total > rs.n_sorted) {
+                // the unsorted tail (particles the window injected since the
+                // last sort), pushed by the tail items in the forward step
+                TrajStep tt = ts;
+                tt.tile_off = nullptr;
+                tt.first = rs.n_sorted;
+                tt.n = rs.n_total;
+                e = launch_adj_particles(dim, r.order, h->d_runs, r, a.A, tt, rs.origin, st);
+            }
             if (moved) {
                 for (int c = 0; c < 3; ++c) {
                     std::swap(a.A.sx[c], a.A.ox[c]);
@@ -1369,7 +1428,7 @@ int pic_adjoint_backward(pic_t *h, const pic_objective *obj, double *L, double *
                 std::swap(a.A.sw, a.A.ow);
             }
             // the segment's first record: back to id order for the previous segment
-            if (e == cudaSuccess && s == s0) e = launch_adj_perm(dim, a.A, rc2.pc.id, n, 0, st);
+            if (e == cudaSuccess && s == s0) e = launch_adj_perm(dim, a.A, rc2.pc.id, n, nid, 0, st);
             if (e != cudaSuccess) return PIC_ECUDA;
         }
     }
@@ -1380,11 +1439,12 @@ int pic_adjoint_backward(pic_t *h, const pic_objective *obj, double *L, double *
         e = cudaMemsetAsync(a.dk, 0, sizeof(double) * n_knots, st);
         const double ppc_t = (double)r.ppc[0] * r.ppc[1] * (dim == 3 ? r.ppc[2] : 1);
         if (e == cudaSuccess)
-            e = launch_knots(a.A.lw, a.zb, n, n_knots, hr.sp.profile_z0, hr.sp.profile_z1, ppc_t, a.dk, st);
+            e = launch_knots(a.A.lw, a.zb, nid, n_knots, hr.sp.profile_z0, hr.sp.profile_z1, ppc_t, a.dk, st);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(dL_dknots, a.dk, sizeof(double) * n_knots, cudaMemcpyDeviceToHost, st);
     }
-    if (e == cudaSuccess && dL_dw) e = cudaMemcpyAsync(dL_dw, a.A.lw, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && dL_dw)
+        e = cudaMemcpyAsync(dL_dw, a.A.lw, sizeof(double) * a.nload, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return PIC_ECUDA;
     if (dL_da0) *dL_da0 = la0;
@@ -1453,7 +1513,7 @@ int pic_adjoint_particles(pic_t *h, float *lam_x, float *lam_u, const float *lam
     if (e == cudaSuccess) e = cudaMemsetAsync(A.sw, 0, sizeof(double) * ns, s);
     const ParticleBuf &pb = r.P[st.buf];
     // adjoints by id -> by slot, the flat reverse kernel over every slot, back by id
-    if (e == cudaSuccess) e = launch_adj_perm(dim, A, pb.id, ns, 1, s);
+    if (e == cudaSuccess) e = launch_adj_perm(dim, A, pb.id, ns, n, 1, s);
     TrajStep ts{};
     ts.cell = pb.cell;
     for (int c = 0; c < 3; ++c) {
@@ -1466,7 +1526,7 @@ int pic_adjoint_particles(pic_t *h, float *lam_x, float *lam_u, const float *lam
     ts.id = pb.id;
     ts.n = ns;
     if (e == cudaSuccess) e = launch_adj_particles(dim, h->order, h->d_runs, r, A, ts, 0, s);
-    if (e == cudaSuccess) e = launch_adj_perm(dim, A, pb.id, ns, 0, s);
+    if (e == cudaSuccess) e = launch_adj_perm(dim, A, pb.id, ns, n, 0, s);
     for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
         e = cudaMemcpyAsync(lam_f + c * nc, A.lE[c], sizeof(float) * nc, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess)

@@ -59,17 +59,20 @@ def _adjoint_case():
 
 
 def _oracle_L(w, knots, a0, obj):
-    """Objective after w.steps oracle steps, FP64 weights from the knots."""
+    """Objective after w.steps oracle steps, FP64 weights from the knots (for
+    the loaded plasma and, with a moving window, the plasma it injects)."""
     w = inputs.Workload(**{**w.__dict__})
     w.laser = inputs.Laser(**{**w.laser.__dict__})
     w.laser.a0 = a0
+    w.knots = np.asarray(knots, dtype=np.float64)
     parts = inputs.background(w)
     x = np.zeros((3, parts.n))
     x[: w.dim] = parts.positions64()
     zlab = x[w.dim - 1] * w.d[-1]
     wt = np.interp(zlab, np.linspace(w.knot_z[0], w.knot_z[1], len(knots)), knots) / w.ppc_total
     sim = oracle_for(w)
-    sim.load(x, parts.u.astype(np.float64), wt, capacity=parts.n + 16)
+    layer = int(np.prod(w.n[:-1])) * w.ppc_total  # particles one window shift injects
+    sim.load(x, parts.u.astype(np.float64), wt, capacity=parts.n + 16 + (w.steps * layer if w.window else 0))
     sim.step(w.steps)
     xx, uu, ww = sim.particles()
     z = xx[w.dim - 1]
@@ -110,6 +113,77 @@ def test_gradient_matches_fp64_oracle_finite_differences(keep):
     assert abs(res["dL_da0"] - fd_a0) <= 1e-3 * abs(fd_a0), (res["dL_da0"], fd_a0)
     # per-particle weights: the knot gradient is their linear image
     assert res["dL_dw"] is not None and np.all(np.isfinite(res["dL_dw"]))
+
+
+def _window_case():
+    """2D LWFA (64 cells along z, pulse of FWHM 3) whose window starts moving
+    at t = 12, once the pulse is in the box, and shifts 53 times in the 100
+    steps: the layers injected at the front drift back through the pulse
+    (cells 0 to 30), and the objective's window (cells 3 to 50) holds loaded
+    and injected plasma.  Knots over lab z 0 to 36: the loaded plasma spans
+    0 to 19, the injected layers 19 to 34, so the last two knots reach the
+    objective only through injected particles (their weights and the fields
+    they drive)."""
+    knots = np.array([0.010, 0.013, 0.008, 0.012, 0.009])
+    w = inputs.lwfa_2d(nx=32, nz=64, ppc=(2, 2), density=0.01, a0=1.2, waist=6.0, steps=100, seed=9)
+    w.laser.fwhm = 3.0
+    w.window.t0 = 12.0
+    w.knots = knots
+    w.knot_z = (0.0, 36.0)
+    obj = dict(z_lo=3.0, z_hi=50.0, width=2.0)
+    return w, obj
+
+
+@pytest.mark.parametrize("keep", [0, -1])
+def test_gradient_through_the_moving_window(keep):
+    """keep 0: every segment recorded by the forward run; -1: every segment
+    recomputed from its checkpoint (window origin, shifts and the unsorted
+    tail restored)."""
+    w, obj = _window_case()
+    parts = inputs.background(w)
+    sim = Simulation(w, track_ids=True, per_particle_weight=True, tuning={"adjoint_keep": keep})
+    sim.load(parts)
+    sim.adjoint_begin(w.steps, 16)
+    sim.step(w.steps)
+    d = sim.diagnostics()
+    assert d["shifts"] >= 50 and d["status"] == 0
+    # ids: the loaded particles keep 0 .. n-1, each shift's layer of m
+    # particles gets n + (k - 1) m + j
+    p = sim.particles()
+    layer = w.n[0] * w.ppc_total
+    ids = p["id"]
+    assert len(np.unique(ids)) == len(ids) and ids.min() >= 0
+    assert ids.max() < parts.n + d["shifts"] * layer
+    assert np.count_nonzero(ids >= parts.n + (d["shifts"] - 1) * layer) == layer  # the newest layer
+    res = sim.adjoint_backward(obj["z_lo"], obj["z_hi"], obj["width"], n_knots=len(w.knots), n_ids=parts.n)
+    sim.close()
+    knots = np.asarray(w.knots, dtype=np.float64)
+    a0 = w.laser.a0
+    L0 = _oracle_L(w, knots, a0, obj)
+    assert abs(res["L"] - L0) <= 1e-4 * abs(L0), (res["L"], L0)
+    fd = []
+    for k in range(len(knots)):
+        h = 1e-3 * knots[k]
+        kp, km = knots.copy(), knots.copy()
+        kp[k] += h
+        km[k] -= h
+        fd.append((_oracle_L(w, kp, a0, obj) - _oracle_L(w, km, a0, obj)) / (2 * h))
+    fd = np.array(fd)
+    g = np.asarray(res["dL_dknots"])
+    assert np.max(np.abs(g - fd)) <= 1e-3 * np.max(np.abs(fd)), (g, fd)
+    # the last two knots lie beyond the loaded plasma: only injected layers carry them
+    assert np.min(np.abs(fd[-2:])) > 1e-2 * np.max(np.abs(fd)), fd
+    # a0 moves particles across the window's rear margin, where they are
+    # dropped: L(a0) has small jumps, and its central differences vary by
+    # about 1 % with the step (the knot differences agree to 1e-5); the
+    # adjoint, the derivative of the smooth part, must lie within their range
+    fa = []
+    for rel in (1e-2, 3e-3, 1e-3, 3e-4, 1e-4):
+        h = rel * a0
+        fa.append((_oracle_L(w, knots, a0 + h, obj) - _oracle_L(w, knots, a0 - h, obj)) / (2 * h))
+    lo, hi = min(fa), max(fa)
+    tol = 1e-3 * max(abs(lo), abs(hi))
+    assert lo - tol <= res["dL_da0"] <= hi + tol, (res["dL_da0"], fa)
 
 
 def test_torch_autograd_function():
