@@ -331,16 +331,16 @@ def scan_bench(args):
 def adjoint_measure(args, S, warmup):
     """Gradient of the trailing-window kinetic energy with respect to 32
     density knots and a0 on the 2D LWFA box 256 x 1024 cells (dx=1, dz=0.3,
-    dt=0.28), 16 ppc, checkpoints every 100 steps: the plain forward run
-    against the forward run with checkpoints plus the reverse sweep."""
+    dt=0.28), 16 ppc, window moving at c from t = 120 (the knots span the
+    lab-frame plasma length, box plus window travel), checkpoints every 100
+    steps: the plain forward run against the forward run with checkpoints
+    plus the reverse sweep."""
     import torch
     from paper_1310_0930_gb300 import inputs
     from paper_1310_0930_gb300.sim import Simulation, TorchMemory
 
     torch.cuda.set_device(0)
     w = inputs.adjoint_2d(steps=S)
-    w.window = None
-    w.knot_z = (0.0, w.n[-1] * w.d[-1])
     parts = inputs.background(w)
     obj = (100.0, 300.0, 2.0)
 
@@ -370,7 +370,7 @@ def adjoint_measure(args, S, warmup):
     sim.close()
     n = parts.n
     return {"workload": "adjoint_2d: 2D LWFA 256x1024 cells, 16 ppc, 32 density knots, a0=3, %d steps, "
-                        "checkpoint every 100, gradient w.r.t. knots and a0" % S,
+                        "moving window from t=120, checkpoint every 100, gradient w.r.t. knots and a0" % S,
             "particles": n, "steps": S, "tuning": tuning, "forward_s": t_fwd, "forward_clocks": clk_f,
             "forward_with_checkpoints_s": t_fwd_ck, "reverse_s": t_bwd, "gradient_clocks": clk_g,
             "gradient_over_forward": (t_fwd_ck + t_bwd) / t_fwd,

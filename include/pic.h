@@ -173,7 +173,7 @@ typedef void (*pic_free_fn)(void *ptr, void *ctx);
  * box rows), 0 = default (plain loads into the bank-padded tile).
  * adjoint_keep: checkpoint segments whose per-step records the forward run
  * keeps, so that the reverse sweep recomputes only the others: 0 = default
- * (as many as 60 % of the free device memory holds), -1 = none (every
+ * (as many as 75 % of the free device memory holds), -1 = none (every
  * segment recomputed), n = at most n.
  * stream_zero_tiles: 0 = default (1), 1 = each step, classify the tiles on
  * the device: a tile whose staged field region is all +0 (E = B = 0 at every

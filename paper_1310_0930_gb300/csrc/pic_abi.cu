@@ -1227,7 +1227,7 @@ int pic_adjoint_begin(pic_t *h, int32_t total_steps, int32_t checkpoint_every)
     if (!ok) return PIC_ENOMEM;
     // Segments kept from the forward run (their records are taken while it
     // runs, so the reverse sweep does not recompute them): as many as the
-    // request allows and 60 % of the free device memory holds.
+    // request allows and 75 % of the free device memory holds.
     const int req = h->adjoint_keep;
     int keep = req < 0 ? 0 : (req == 0 ? a->nck : (req < a->nck ? req : a->nck));
     if (keep > 1) {
@@ -1235,7 +1235,7 @@ int pic_adjoint_begin(pic_t *h, int32_t total_steps, int32_t checkpoint_every)
         const size_t rec_bytes = sizeof(int32_t) * (size_t)n * 3 + sizeof(float) * (size_t)n * (dim + 4) +
                                  sizeof(float) * 6 * (size_t)nc + sizeof(int32_t) * (r.ntiles + 1) + 6 * 256;
         if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = 0;
-        const long long fit = (long long)(0.6 * (double)fr / ((double)rec_bytes * a->K));
+        const long long fit = (long long)(0.75 * (double)fr / ((double)rec_bytes * a->K));
         keep = (int)(keep - 1 < fit ? keep : fit + 1);
     }
     for (int q = a->K; q < keep * a->K; ++q) {
