@@ -24,7 +24,7 @@ constexpr int kBlock = 256;
 // Tile sort (sort.cu): one CTA of kSortThreads threads ranks a chunk of
 // kSortChunk particle slots in a shared-memory key table of kSortHash
 // entries; the particle segments of the sort are in units of chunks.
-constexpr int kSortThreads = 256, kSortItems = 8, kSortGroup = 2, kSortChunk = kSortThreads * kSortItems;
+constexpr int kSortThreads = 256, kSortItems = 8, kSortChunk = kSortThreads * kSortItems;
 constexpr int kSortHashLog = 9, kSortHash = 1 << kSortHashLog, kSortProbe = 32;
 // adaptive sort: sort once strays (particles outside their tile's drift
 // region) add up to n_total / kSortSlowDiv particle-steps since the last sort

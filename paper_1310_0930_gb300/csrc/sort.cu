@@ -186,6 +186,38 @@ __device__ __forceinline__ int table_slot(KeyTable &t, int key)
     return -1;
 }
 
+// Slot of item j (0 .. kSortItems-1) of this thread in the chunk at i0: two
+// groups of four consecutive slots, so that each thread loads its particles
+// with 16-byte vector accesses.
+__device__ __forceinline__ long long item_slot(long long i0, int j)
+{
+    return i0 + (j >> 2) * (kSortChunk / 2) + 4 * threadIdx.x + (j & 3);
+}
+
+// Four consecutive 32-bit values at p + s0 (valid ones only past n).
+template <class T, class T4>
+__device__ __forceinline__ void load4(const T *p, long long s0, long long n, T *out)
+{
+    if (s0 + 3 < n) {
+        const T4 v = *reinterpret_cast<const T4 *>(p + s0);
+        out[0] = v.x;
+        out[1] = v.y;
+        out[2] = v.z;
+        out[3] = v.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) out[q] = s0 + q < n ? p[s0 + q] : T(0);
+    }
+}
+
+// The four cells of slots s0 .. s0+3; dead (-1) past n.
+__device__ __forceinline__ void load_cells4(const int32_t *cell, long long s0, long long n, int32_t *out)
+{
+    load4<int32_t, int4>(cell, s0, n, out);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[q] = s0 + q < n ? out[q] : -1;
+}
+
 // Tile histogram: each CTA counts a chunk of kSortChunk slots in shared
 // memory (one shared atomic per warp and key), then adds its per-key totals
 // to the global counters: a handful of global atomics per chunk.  All the
@@ -206,16 +238,13 @@ __global__ void __launch_bounds__(kSortThreads) sort_count_kernel(const Run *__r
         const int32_t *cells = r.P[r.state->buf].cell;
         int32_t cell[kSortItems];
 #pragma unroll
-        for (int j = 0; j < kSortItems; ++j) {
-            const long long i = i0 + j * kSortThreads + threadIdx.x;
-            cell[j] = i < kc.n_total ? cells[i] : -1;
-        }
+        for (int g = 0; g < kSortItems / 4; ++g) load_cells4(cells, item_slot(i0, 4 * g), kc.n_total, cell + 4 * g);
         table_init(t);
         __syncthreads();
         const int lane = threadIdx.x & 31;
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j) {
-            const int key = sub_key(kc, key_of_cell(kc, cell[j]), i0 + j * kSortThreads + threadIdx.x, cell[j]);
+            const int key = sub_key(kc, key_of_cell(kc, cell[j]), item_slot(i0, j), cell[j]);
             const unsigned peers = key_peers(key);
             if (key >= 0 && lane == __ffs(peers) - 1) {
                 const int e = table_slot(t, key);
@@ -329,13 +358,16 @@ __global__ void __launch_bounds__(kScanThreads) sort_scan_add_kernel(const Run *
     }
 }
 
-// Scatter: each CTA ranks its chunk's particles per key in shared memory,
-// reserves one contiguous range per key in the destination with one global
-// atomic on the tile cursor, then copies every live particle to
-// range start + rank.  Warps whose keys agree write 32 consecutive slots.
-// Cells, table slots and ranks stay in registers; the copy loads a group of
-// 2 particles per thread before storing them.
-__global__ void __launch_bounds__(kSortThreads, 3) sort_scatter_kernel(const Run *__restrict__ runs, Seg seg,
+// Scatter: each CTA ranks its chunk's particles per key in shared memory
+// (key table, warp match, shared atomics), reserves one contiguous range per
+// key in the destination with one global atomic on its cursor, and copies
+// every live particle to range start + rank.  Loads are 16-byte vector loads
+// of four consecutive slots per thread (128 registers, two CTAs per SM: the
+// kernel is bound by memory latency, and this keeps more bytes in flight than
+// scalar loads at three CTAs per SM); for item j the lanes of a warp holding
+// one key have consecutive ranks, so each store instruction writes a run of
+// consecutive destination slots per key.
+__global__ void __launch_bounds__(kSortThreads, 2) sort_scatter_kernel(const Run *__restrict__ runs, Seg seg,
                                                                     int32_t *__restrict__ src_out)
 {
     __shared__ KeyTable t;
@@ -354,10 +386,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) sort_scatter_kernel(const Run
         const ParticleBuf dst = r.P[buf ^ 1];
         int32_t cell[kSortItems];
 #pragma unroll
-        for (int j = 0; j < kSortItems; ++j) {
-            const long long i = i0 + j * kSortThreads + threadIdx.x;
-            cell[j] = i < kc.n_total ? src.cell[i] : -1;
-        }
+        for (int g = 0; g < kSortItems / 4; ++g) load_cells4(src.cell, item_slot(i0, 4 * g), kc.n_total, cell + 4 * g);
         table_init(t);
         __syncthreads();
         const int lane = threadIdx.x & 31;
@@ -365,7 +394,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) sort_scatter_kernel(const Run
         int slot[kSortItems], rank[kSortItems];
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j) {
-            const int key = sub_key(kc, key_of_cell(kc, cell[j]), i0 + j * kSortThreads + threadIdx.x, cell[j]);
+            const int key = sub_key(kc, key_of_cell(kc, cell[j]), item_slot(i0, j), cell[j]);
             const unsigned peers = key_peers(key);
             const int leader = __ffs(peers) - 1;
             int e = -2, off = 0;
@@ -384,40 +413,31 @@ __global__ void __launch_bounds__(kSortThreads, 3) sort_scatter_kernel(const Run
         __syncthreads();
         const bool d3 = kc.dim == 3;
 #pragma unroll
-        for (int g = 0; g < kSortItems; g += kSortGroup) {
-            float v[kSortGroup][6];
-            float wv[kSortGroup];
-            int32_t idv[kSortGroup];
+        for (int g = 0; g < kSortItems / 4; ++g) {
+            const long long s0 = item_slot(i0, 4 * g);
+            float o[3][4], u[3][4], wv[4];
+            int32_t idv[4] = {0, 0, 0, 0};
+            load4<float, float4>(src.off[0], s0, kc.n_total, o[0]);
+            load4<float, float4>(src.off[1], s0, kc.n_total, o[1]);
+            if (d3) load4<float, float4>(src.off[2], s0, kc.n_total, o[2]);
 #pragma unroll
-            for (int q = 0; q < kSortGroup; ++q) {
-                const int j = g + q;
-                const long long i = i0 + j * kSortThreads + threadIdx.x;
-                if (slot[j] != -2) {
-                    v[q][0] = src.off[0][i];
-                    v[q][1] = src.off[1][i];
-                    v[q][2] = d3 ? src.off[2][i] : 0.f;
-                    v[q][3] = src.u[0][i];
-                    v[q][4] = src.u[1][i];
-                    v[q][5] = src.u[2][i];
-                    wv[q] = src.w ? src.w[i] : 0.f;
-                    idv[q] = src.id ? src.id[i] : 0;
-                }
-            }
+            for (int a = 0; a < 3; ++a) load4<float, float4>(src.u[a], s0, kc.n_total, u[a]);
+            if (src.w) load4<float, float4>(src.w, s0, kc.n_total, wv);
+            if (src.id) load4<int32_t, int4>(src.id, s0, kc.n_total, idv);
 #pragma unroll
-            for (int q = 0; q < kSortGroup; ++q) {
-                const int j = g + q;
+            for (int q = 0; q < 4; ++q) {
+                const int j = 4 * g + q;
                 if (slot[j] == -2) continue;
-                const long long o = slot[j] >= 0 ? (long long)t.base[slot[j]] + rank[j] : (long long)rank[j];
-                dst.cell[o] = cell[j];
-                dst.off[0][o] = v[q][0];
-                dst.off[1][o] = v[q][1];
-                if (d3) dst.off[2][o] = v[q][2];
-                dst.u[0][o] = v[q][3];
-                dst.u[1][o] = v[q][4];
-                dst.u[2][o] = v[q][5];
-                if (src.w) dst.w[o] = wv[q];
-                if (src.id) dst.id[o] = idv[q];
-                if (src_out) src_out[o] = (int32_t)(i0 + j * kSortThreads + threadIdx.x);
+                const long long d = slot[j] >= 0 ? (long long)t.base[slot[j]] + rank[j] : (long long)rank[j];
+                dst.cell[d] = cell[j];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    if (a < 2 || d3) dst.off[a][d] = o[a][q];
+                    dst.u[a][d] = u[a][q];
+                }
+                if (src.w) dst.w[d] = wv[q];
+                if (src.id) dst.id[d] = idv[q];
+                if (src_out) src_out[d] = (int32_t)(s0 + q);
             }
         }
         __syncthreads();  // (the next chunk re-initialises the table)
@@ -453,7 +473,7 @@ cudaError_t launch_sort(const Run *runs, int nruns, Seg parts, Seg keys, int *sc
         if (sms <= 0) sms = 1;
     }
     const int g_count = parts.nblocks < 16 * sms ? parts.nblocks : 16 * sms;
-    const int g_scatter = parts.nblocks < 12 * sms ? parts.nblocks : 12 * sms;
+    const int g_scatter = parts.nblocks < 8 * sms ? parts.nblocks : 8 * sms;
     sort_count_kernel<<<g_count > 0 ? g_count : 1, kSortThreads, 0, st>>>(runs, parts);
     sort_scan_local_kernel<<<keys.nblocks, kScanThreads, 0, st>>>(runs, keys, scan_sums);
     sort_scan_sums_kernel<<<nruns, kScanThreads, 0, st>>>(runs, keys, scan_sums);
