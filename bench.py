@@ -97,7 +97,7 @@ def particle_chunks(w):
 # processed, scaled to the timed launches by their slot counts (the kernel's
 # traffic grows in proportion to its slots).
 ZERO_PROFILE = {
-    ("lwfa_3d", 2): (51.8, 1.30, "push_zero_kernel_lwfa3d_64x64x256.md"),
+    ("lwfa_3d", 2): (17.2, 1.64, "push_zero_kernel_lwfa3d_64x64x256.md"),
 }
 
 
@@ -119,14 +119,23 @@ def aggregate_replicas(elapsed, units):
     return float(t.item()), float(u.item())
 
 
-def algorithmic_bytes(w, n_particles):
-    """Bytes the method must move once per step (state read + write): per
-    particle 2 * (4 packed cell + 4*dim offsets + 12 momentum [+4 weight]);
-    per cell 96 = gather E,B (24) + J write (12) + Yee reads E,B,J (36) +
-    writes E,B (24).  The push kernel alone: particles + 36 B per cell."""
+# A particle slot of a zero-field tile: its packed cell (absorption) and its
+# momentum (at rest or not) are read; a particle at rest keeps its state, so
+# nothing is written and its offsets are not read.
+ZERO_SLOT_BYTES = 4 + 12
+
+
+def algorithmic_bytes(w, n_particles, streamed=0.0):
+    """Bytes the method must move once per step: per particle of a live tile
+    the state read + written, 2 * (4 packed cell + 4*dim offsets + 12
+    momentum [+4 weight]); per slot of a zero-field tile (`streamed` of them)
+    ZERO_SLOT_BYTES; per cell 96 = gather E,B (24) + J write (12) + Yee reads
+    E,B,J (36) + writes E,B (24).  The particle phase alone: particles + 36 B
+    per cell."""
     sp = 4 + 4 * w.dim + 12 + (4 if (w.knots is not None or w.bunch is not None) else 0)
-    step = n_particles * 2 * sp + w.n_cells * 96
-    push = n_particles * 2 * sp + w.n_cells * 36
+    parts = (n_particles - streamed) * 2 * sp + streamed * ZERO_SLOT_BYTES
+    step = parts + w.n_cells * 96
+    push = parts + w.n_cells * 36
     return step, push, sp
 
 
@@ -521,7 +530,7 @@ def frozen_bench(args):
             d1 = sim.diagnostics()
             ms = e0.elapsed_time(e1) / args.steps
             sim.close()
-            _, push_bytes, sp = algorithmic_bytes(w, parts.n)
+            _, push_bytes, sp = algorithmic_bytes(w, parts.n, (d1["streamed"] - d0["streamed"]) / args.steps)
             push_ms = phases["push"] / args.steps
             rows["%s_order%d" % (case, order)] = {
                 "particle_steps_per_s": parts.n / (ms / 1e3), "ms_per_step": ms, "push_ms_per_step": push_ms,
@@ -645,7 +654,8 @@ def main():
     n_avg = 0.5 * (d0["n_particles"] + d1["n_particles"])
     ms, units = aggregate_replicas(ms, n_avg * args.steps)
     value = units / (ms / 1e3)
-    step_bytes, push_bytes, sp = algorithmic_bytes(w, n_avg)
+    streamed = (d1["streamed"] - d0["streamed"]) / args.steps
+    step_bytes, push_bytes, sp = algorithmic_bytes(w, n_avg, streamed)
     push_ms = phases["push"] / args.steps
     peaks = {}
     try:
@@ -654,12 +664,11 @@ def main():
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = push_bytes / (push_ms / 1e3) / 1e9
-    # the particle phase's two kernels: zero-field tiles streamed (particle
-    # state read and written, 2 S_p bytes per slot) and the staged tiles
-    streamed = (d1["streamed"] - d0["streamed"]) / args.steps
+    # the particle phase's two kernels: zero-field tiles streamed
+    # (ZERO_SLOT_BYTES per slot) and the staged tiles
     zero_ms = phases["push_zero"] / args.steps
     staged_ms = push_ms - zero_ms
-    zero_bytes = streamed * 2 * sp
+    zero_bytes = streamed * ZERO_SLOT_BYTES
     staged_bytes = push_bytes - zero_bytes
     kernels = [
         {"kernel": "push_zero_kernel<%d,%d> (zero-field tiles)" % (w.dim, w.order), "slots_per_launch": streamed,
@@ -709,7 +718,7 @@ def main():
         ms_f = e0.elapsed_time(e1)
         f1 = simf.diagnostics()
         nf = 0.5 * (f0["n_particles"] + f1["n_particles"])
-        sb_f, _, _ = algorithmic_bytes(w, nf)
+        sb_f, _, _ = algorithmic_bytes(w, nf, (f1["streamed"] - f0["streamed"]) / w.steps)
         full = {"value": nf * w.steps / (ms_f / 1e3), "ms_per_step": ms_f / w.steps, "steps": w.steps,
                 "step_roofline_frac": sb_f / (ms_f / w.steps / 1e3) / 1e9 / peak, "clocks": clk_f,
                 "sorts": int(f1["sorts"] - f0["sorts"]), "window_shifts": int(f1["shifts"]),

@@ -1367,45 +1367,64 @@ __global__ void __launch_bounds__(kZeroThreads, 3) push_zero_kernel(const Run *_
         const int t = it.a;
         const long long p0 = r.tile_off[t], p1 = r.tile_off[t + 1];
         bool moving = false;  // this thread left a moving particle for the second pass
-        // four consecutive slots per thread with 16-byte accesses where every
-        // array is 16-byte aligned; slot by slot elsewhere
-        uintptr_t al = (uintptr_t)pb.cell | (uintptr_t)pb.u[0] | (uintptr_t)pb.u[1] | (uintptr_t)pb.u[2];
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) al |= (uintptr_t)pb.off[a];
+        // A particle at rest (u = 0) in zero fields keeps its cell, offsets
+        // and momentum: the step reads its cell (absorption) and momentum
+        // and writes back only what changes (an absorbed cell, a -0 momentum
+        // component made +0 as the push makes it); its offsets are not
+        // touched.  Four consecutive slots per thread with 16-byte accesses
+        // where the arrays are 16-byte aligned; slot by slot elsewhere.
+        const uintptr_t al = (uintptr_t)pb.cell | (uintptr_t)pb.u[0] | (uintptr_t)pb.u[1] | (uintptr_t)pb.u[2];
         long long v0 = (p0 + 3) & ~3ll, v1 = p1 & ~3ll;
         if ((al & 15u) != 0 || v0 >= v1) v0 = v1 = p1;
-        for (long long g = (v0 >> 2) + threadIdx.x; g < (v1 >> 2); g += blockDim.x) {
-            int4 c4 = reinterpret_cast<const int4 *>(pb.cell)[g];
-            float4 o4[DIM], u4[3];
+        // (two groups of four slots per thread and iteration, both loaded
+        // before either is processed: more bytes in flight)
+        const long long gend = v1 >> 2;
+        for (long long g = (v0 >> 2) + threadIdx.x; g < gend; g += 2 * blockDim.x) {
+            const long long gg[2] = {g, g + blockDim.x};
+            int4 c4[2];
+            float4 u4[2][3];
 #pragma unroll
-            for (int a = 0; a < DIM; ++a) o4[a] = reinterpret_cast<const float4 *>(pb.off[a])[g];
+            for (int h = 0; h < 2; ++h) {
+                if (gg[h] >= gend) break;
+                c4[h] = reinterpret_cast<const int4 *>(pb.cell)[gg[h]];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) u4[a] = reinterpret_cast<const float4 *>(pb.u[a])[g];
-            int32_t cl[4] = {c4.x, c4.y, c4.z, c4.w};
-            float uu[4][3] = {{u4[0].x, u4[1].x, u4[2].x}, {u4[0].y, u4[1].y, u4[2].y},
-                              {u4[0].z, u4[1].z, u4[2].z}, {u4[0].w, u4[1].w, u4[2].w}};
+                for (int a = 0; a < 3; ++a) u4[h][a] = reinterpret_cast<const float4 *>(pb.u[a])[gg[h]];
+            }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) moving = zero_slot<DIM>(r, z, cl[q], uu[q]) || moving;
-            // (a moving slot's values are written back unchanged; the second
-            // pass advances it)
-            reinterpret_cast<int4 *>(pb.cell)[g] = make_int4(cl[0], cl[1], cl[2], cl[3]);
+            for (int h = 0; h < 2; ++h) {
+                if (gg[h] >= gend) break;
+                int32_t cl[4] = {c4[h].x, c4[h].y, c4[h].z, c4[h].w};
+                float uu[4][3] = {{u4[h][0].x, u4[h][1].x, u4[h][2].x}, {u4[h][0].y, u4[h][1].y, u4[h][2].y},
+                                  {u4[h][0].z, u4[h][1].z, u4[h][2].z}, {u4[h][0].w, u4[h][1].w, u4[h][2].w}};
 #pragma unroll
-            for (int a = 0; a < DIM; ++a) reinterpret_cast<float4 *>(pb.off[a])[g] = o4[a];
+                for (int q = 0; q < 4; ++q) moving = zero_slot<DIM>(r, z, cl[q], uu[q]) || moving;
+                // (a moving slot is left as it is; the second pass advances it)
+                if (cl[0] != c4[h].x || cl[1] != c4[h].y || cl[2] != c4[h].z || cl[3] != c4[h].w)
+                    reinterpret_cast<int4 *>(pb.cell)[gg[h]] = make_int4(cl[0], cl[1], cl[2], cl[3]);
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
-                reinterpret_cast<float4 *>(pb.u[a])[g] = make_float4(uu[0][a], uu[1][a], uu[2][a], uu[3][a]);
+                for (int a = 0; a < 3; ++a) {
+                    const float4 n4 = make_float4(uu[0][a], uu[1][a], uu[2][a], uu[3][a]);
+                    const float4 o4 = u4[h][a];
+                    if (__float_as_int(n4.x) != __float_as_int(o4.x) || __float_as_int(n4.y) != __float_as_int(o4.y) ||
+                        __float_as_int(n4.z) != __float_as_int(o4.z) || __float_as_int(n4.w) != __float_as_int(o4.w))
+                        reinterpret_cast<float4 *>(pb.u[a])[gg[h]] = n4;
+                }
+            }
         }
         // the ragged ends (and every slot when an array is not 16-byte aligned)
         const long long ends = (v0 - p0) + (p1 - v1);
         for (long long e = threadIdx.x; e < ends; e += blockDim.x) {
             const long long i = e < v0 - p0 ? p0 + e : v1 + (e - (v0 - p0));
-            int32_t cl = pb.cell[i];
-            float uu[3] = {pb.u[0][i], pb.u[1][i], pb.u[2][i]};
+            const int32_t c0 = pb.cell[i];
+            int32_t cl = c0;
+            const float u0[3] = {pb.u[0][i], pb.u[1][i], pb.u[2][i]};
+            float uu[3] = {u0[0], u0[1], u0[2]};
             moving = zero_slot<DIM>(r, z, cl, uu) || moving;
-            pb.cell[i] = cl;
+            if (cl != c0) pb.cell[i] = cl;
             if (cl >= 0) {
 #pragma unroll
-                for (int a = 0; a < 3; ++a) pb.u[a][i] = uu[a];
+                for (int a = 0; a < 3; ++a)
+                    if (__float_as_int(uu[a]) != __float_as_int(u0[a])) pb.u[a][i] = uu[a];
             }
         }
         // second pass, rare (a moving particle deposits, so its tile's fields
