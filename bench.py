@@ -99,6 +99,11 @@ def particle_chunks(w):
 ZERO_PROFILE = {
     ("lwfa_3d", 2): (17.2, 1.64, "push_zero_kernel_lwfa3d_64x64x256.md"),
 }
+# the same per live-tile particle for the staged kernel (classification
+# included in its events, not in these figures)
+STAGED_PROFILE = {
+    ("lwfa_3d", 2): (42.8, 32.7, "push_kernel_lwfa3d_quadratic_128x128x512.md"),
+}
 
 
 def aggregate_replicas(elapsed, units):
@@ -125,18 +130,29 @@ def aggregate_replicas(elapsed, units):
 ZERO_SLOT_BYTES = 4 + 12
 
 
-def algorithmic_bytes(w, n_particles, streamed=0.0):
+def algorithmic_bytes(w, n_particles, streamed=0.0, live_cells=None):
     """Bytes the method must move once per step: per particle of a live tile
     the state read + written, 2 * (4 packed cell + 4*dim offsets + 12
     momentum [+4 weight]); per slot of a zero-field tile (`streamed` of them)
-    ZERO_SLOT_BYTES; per cell 96 = gather E,B (24) + J write (12) + Yee reads
-    E,B,J (36) + writes E,B (24).  The particle phase alone: particles + 36 B
-    per cell."""
+    ZERO_SLOT_BYTES; per cell of a live tile (`live_cells`, default every
+    cell) 36 = gather E,B (24) + J write (12); per cell 60 = Yee reads E,B,J
+    (36) + writes E,B (24).  The particle phase alone: particles + 36 B per
+    live cell."""
     sp = 4 + 4 * w.dim + 12 + (4 if (w.knots is not None or w.bunch is not None) else 0)
     parts = (n_particles - streamed) * 2 * sp + streamed * ZERO_SLOT_BYTES
-    step = parts + w.n_cells * 96
-    push = parts + w.n_cells * 36
+    cells = w.n_cells if live_cells is None else min(float(w.n_cells), live_cells)
+    step = parts + cells * 36 + w.n_cells * 60
+    push = parts + cells * 36
     return step, push, sp
+
+
+def tile_cells(w, tuning):
+    """Cells of one tile: the tuning's tile, else the default of the
+    dimension (3D 8 x 8 x 8, 2D 16 x 16)."""
+    t = (tuning or {}).get("tile")
+    if t:
+        return int(np.prod(t[: w.dim]))
+    return 512 if w.dim == 3 else 256
 
 
 class Clocks:
@@ -530,7 +546,11 @@ def frozen_bench(args):
             d1 = sim.diagnostics()
             ms = e0.elapsed_time(e1) / args.steps
             sim.close()
-            _, push_bytes, sp = algorithmic_bytes(w, parts.n, (d1["streamed"] - d0["streamed"]) / args.steps)
+            tun = json.loads(args.tuning) if args.tuning else None
+            _, push_bytes, sp = algorithmic_bytes(
+                w, parts.n, (d1["streamed"] - d0["streamed"]) / args.steps,
+                (d1["live_tiles"] - d0["live_tiles"]) / args.steps * tile_cells(w, tun)
+                if d1["live_tiles"] + d1["streamed"] > d0["live_tiles"] + d0["streamed"] else None)
             push_ms = phases["push"] / args.steps
             rows["%s_order%d" % (case, order)] = {
                 "particle_steps_per_s": parts.n / (ms / 1e3), "ms_per_step": ms, "push_ms_per_step": push_ms,
@@ -655,7 +675,8 @@ def main():
     ms, units = aggregate_replicas(ms, n_avg * args.steps)
     value = units / (ms / 1e3)
     streamed = (d1["streamed"] - d0["streamed"]) / args.steps
-    step_bytes, push_bytes, sp = algorithmic_bytes(w, n_avg, streamed)
+    live_cells = (d1["live_tiles"] - d0["live_tiles"]) / args.steps * tile_cells(w, tuning)
+    step_bytes, push_bytes, sp = algorithmic_bytes(w, n_avg, streamed, live_cells if streamed > 0 else None)
     push_ms = phases["push"] / args.steps
     peaks = {}
     try:
@@ -682,14 +703,17 @@ def main():
     # the roofline reports the particle phase's dominant kernel by time
     dom = kernels[0] if zero_ms >= staged_ms else kernels[1]
     dom_bytes, dom_ms = dom["bytes_per_launch"], dom["avg_launch_ms"]
-    prof = ZERO_PROFILE.get((w.name, w.order)) if (not tuning and dom is kernels[0]) else None
-    traffic = prof[0] * streamed if prof else None
+    units_dom = streamed if dom is kernels[0] else n_avg - streamed
+    prof = None
+    if not tuning:
+        prof = (ZERO_PROFILE if dom is kernels[0] else STAGED_PROFILE).get((w.name, w.order))
+    traffic = prof[0] * units_dom if prof else None
     issue = None
     if prof:
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         mhz = (clk or {}).get("sm_mhz") or 2070.0
         peak_issue = sms * 4 * mhz * 1e6  # four warp schedulers per SM, one instruction per clock each
-        ach_issue = prof[1] * streamed / (zero_ms / 1e3)
+        ach_issue = prof[1] * units_dom / (dom_ms / 1e3)
         issue = {"achieved": ach_issue, "peak": peak_issue, "unit": "warp-instructions/s",
                  "frac": ach_issue / peak_issue, "source": "profiles/" + prof[2]}
     status = d1["status"]
@@ -718,7 +742,9 @@ def main():
         ms_f = e0.elapsed_time(e1)
         f1 = simf.diagnostics()
         nf = 0.5 * (f0["n_particles"] + f1["n_particles"])
-        sb_f, _, _ = algorithmic_bytes(w, nf, (f1["streamed"] - f0["streamed"]) / w.steps)
+        sb_f, _, _ = algorithmic_bytes(w, nf, (f1["streamed"] - f0["streamed"]) / w.steps,
+                                       (f1["live_tiles"] - f0["live_tiles"]) / w.steps * tile_cells(w, tuning)
+                                       if f1["streamed"] > f0["streamed"] else None)
         full = {"value": nf * w.steps / (ms_f / 1e3), "ms_per_step": ms_f / w.steps, "steps": w.steps,
                 "step_roofline_frac": sb_f / (ms_f / w.steps / 1e3) / 1e9 / peak, "clocks": clk_f,
                 "sorts": int(f1["sorts"] - f0["sorts"]), "window_shifts": int(f1["shifts"]),
@@ -791,8 +817,11 @@ def main():
                      "peak": peak, "unit": "GB/s",
                      "frac": dom_bytes / (dom_ms / 1e3) / 1e9 / peak if dom_ms > 0 else None,
                      "traffic": traffic, "kernel": dom["kernel"],
-                     "traffic_source": ("ncu capture of a 1/4-scale case, %.1f B per slot scaled by the slots of "
-                                        "one launch, profiles/%s" % (prof[0], prof[2])) if prof else None,
+                     "traffic_source": ("ncu capture of a scaled-down case of the same workload, %.1f B per %s "
+                                        "scaled by the %ss of one launch, profiles/%s"
+                                        % (prof[0], *(("slot", "slot") if dom is kernels[0] else
+                                                      ("live-tile particle", "live-tile particle")), prof[2]))
+                     if prof else None,
                      "issue": issue, "bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms,
                      "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json)" if peaks else "fallback",
                      "phase": {"what": "particle phase: classification + push_kernel + push_zero_kernel",

@@ -248,6 +248,8 @@ typedef struct {
     int32_t status;        /* latched device status (PIC_OK or a PIC_E* code) */
     int32_t sorts;         /* tile sorts so far */
     int64_t streamed;      /* particle slots advanced by the zero-field tile kernel, all steps so far */
+    int64_t live_tiles;    /* non-empty tiles advanced by the staged kernel, all steps so far (with
+                              the zero-field tiles streamed; 0 otherwise) */
 } pic_diag;
 
 typedef struct pic_s pic_t;

@@ -68,7 +68,7 @@ class pic_diag(ctypes.Structure):
     _fields_ = [("step", c_int64), ("time", c_double), ("shifts", c_int64), ("W_E", c_double), ("W_B", c_double),
                 ("W_kin", c_double), ("gauss_resid", c_double), ("n_particles", c_int64),
                 ("imbalance", c_double), ("slow_path", c_int64), ("status", c_int32), ("sorts", c_int32),
-                ("streamed", c_int64)]
+                ("streamed", c_int64), ("live_tiles", c_int64)]
 
 
 # name -> (restype, argtypes); the order and types follow include/pic.h

@@ -52,6 +52,7 @@ struct RunState {
     int do_sort;                   // this step sorts (set by the sort decision)
     long long sorts;               // sorts so far
     unsigned long long streamed;   // particle slots of zero-field tiles streamed so far
+    unsigned long long live_tiles; // non-empty tiles the staged kernel advanced so far
 };
 
 // Immutable per-run descriptor (device copy).

@@ -1081,6 +1081,7 @@ int pic_diagnostics(pic_t *h, pic_diag *out)
     out->slow_path = (int64_t)st.slow_last;
     out->sorts = (int32_t)st.sorts;
     out->streamed = (int64_t)st.streamed;
+    out->live_tiles = (int64_t)st.live_tiles;
     out->status = status_code(st.status);
     return out->status;
 }

@@ -133,6 +133,11 @@ __global__ void classify_tiles_kernel(const Run *__restrict__ runs, const Item *
     // warp-aggregated appends (items of one warp keep their order)
     const unsigned lane = threadIdx.x & 31u, lt = (1u << lane) - 1u;
     const unsigned m_live = __ballot_sync(0xffffffffu, take && is_live);
+    {  // live tiles per run (diagnostics): one atomic per run and warp
+        const unsigned peers = __match_any_sync(0xffffffffu, take && is_live ? it.run : -1);
+        if (take && is_live && lane == (unsigned)(__ffs(peers) - 1))
+            atomicAdd(&runs[it.run].state->live_tiles, (unsigned long long)__popc(peers));
+    }
     const unsigned m_zero = __ballot_sync(0xffffffffu, take && !is_live);
     int b_live = 0, b_zero = 0;
     if (lane == 0) {

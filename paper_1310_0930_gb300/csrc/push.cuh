@@ -1270,10 +1270,11 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
 // at every one of its particles.  The Boris push then returns u unchanged
 // (every term adds or multiplies exact zeros; a zero momentum comes out as
 // +0), so a particle at rest stays where it is and deposits no current: its
-// step reads its state and writes it back.  Such tiles are streamed by this
-// kernel with 16-byte accesses (four consecutive slots per thread; the ragged
-// ends of a tile's range slot by slot) and no shared-memory tiles, so that
-// many CTAs per SM keep loads in flight.  A particle of such a tile that does
+// step reads its cell (absorption at an open window's ends) and momentum and
+// changes nothing else.  Such tiles are streamed by this kernel with 16-byte
+// loads (two groups of four consecutive slots per thread; the ragged ends of
+// a tile's range slot by slot) and no shared-memory tiles, so that many CTAs
+// per SM keep loads in flight.  A particle of such a tile that does
 // move takes the general slow path (the gather from global memory reads the
 // same zeros; the current goes to global memory by atomics) and is counted as
 // a slow-path particle.  Particles outside their tile's drift region cost
