@@ -91,6 +91,14 @@ struct Run {
     // 0 if all are +0 (cleared by the first B half step, set by the second; set
     // for every tile whenever E or B is written from outside the timestep)
     uint8_t *fz;
+    // per tile, per step (null: not kept): jt = 1 if a particle of the slow
+    // path (strays, the unsorted tail, movers of zero-field tiles) deposited
+    // current from a cell of the tile; quiet = 1 if the field update of the
+    // tile's cells is the identity this step (no E, B or J in reach), so the
+    // Yee kernels and the J reset leave them alone.  qr[a]: tiles along axis
+    // a within a tile's deposit reach (drift plus the window's reach).
+    uint8_t *jt, *quiet;
+    int qr[3];
     long long capacity;
     // laser antenna
     int laser_on, laser_pol, laser_plane;

@@ -59,20 +59,31 @@ __device__ double laser_r2(const Run &r, int i, int j)
 __device__ __forceinline__ void clear_tile_flags(const Run &r, const Seg &seg, int ri, int t)
 {
     const int nthreads = (seg.start[ri + 1] - seg.start[ri]) * blockDim.x;
-    for (; t < r.ntiles; t += nthreads) r.fz[t] = 0;
+    for (; t < r.ntiles; t += nthreads) {
+        r.fz[t] = 0;
+        if (r.jt) r.jt[t] = 0;
+    }
+}
+
+// The cells of a quiet tile keep E = B = J = +0 through the step (see
+// quiet_kernel): their field update is the identity.
+__device__ __forceinline__ bool quiet_cell(const Run &r, int i, int j, int k)
+{
+    return r.quiet && r.quiet[tile_of(r, i, j, k)];
 }
 
 template <int DIM>
-__global__ void yee_b_kernel(const Run *__restrict__ runs, Seg seg, int second)
+__device__ __forceinline__ void yee_b_block(const Run *__restrict__ runs, Seg seg, int second, int vb)
 {
-    const int ri = seg_run(seg, blockIdx.x);
+    const int ri = seg_run(seg, vb);
     const Run &r = runs[ri];
-    const int idx = (blockIdx.x - seg.start[ri]) * blockDim.x + threadIdx.x;
+    const int idx = (vb - seg.start[ri]) * blockDim.x + threadIdx.x;
     if (!second && r.fz) clear_tile_flags(r, seg, ri, idx);
     if (idx >= r.ncell) return;
     const RunState &s = *r.state;
     const int n0 = r.n[0], n1 = r.n[1];
     const int i = idx % n0, j = (idx / n0) % n1, k = DIM == 3 ? idx / (n0 * n1) : 0;
+    if (quiet_cell(r, i, j, k)) return;
     const int cx = (i + 1 == n0 ? 0 : i + 1) + n0 * (j + n1 * k);
     const int cy = i + n0 * ((j + 1 == n1 ? 0 : j + 1) + n1 * k);
     const float h = 0.5f * r.dt;
@@ -127,15 +138,22 @@ __global__ void yee_b_kernel(const Run *__restrict__ runs, Seg seg, int second)
 }
 
 template <int DIM>
-__global__ void yee_e_kernel(const Run *__restrict__ runs, Seg seg)
+__global__ void yee_b_kernel(const Run *__restrict__ runs, Seg seg, int second)
 {
-    const int ri = seg_run(seg, blockIdx.x);
+    for (int vb = blockIdx.x; vb < seg.nblocks; vb += gridDim.x) yee_b_block<DIM>(runs, seg, second, vb);
+}
+
+template <int DIM>
+__device__ __forceinline__ void yee_e_block(const Run *__restrict__ runs, Seg seg, int vb)
+{
+    const int ri = seg_run(seg, vb);
     const Run &r = runs[ri];
-    const int idx = (blockIdx.x - seg.start[ri]) * blockDim.x + threadIdx.x;
+    const int idx = (vb - seg.start[ri]) * blockDim.x + threadIdx.x;
     if (idx >= r.ncell) return;
     const RunState &s = *r.state;
     const int n0 = r.n[0], n1 = r.n[1];
     const int i = idx % n0, j = (idx / n0) % n1, k = DIM == 3 ? idx / (n0 * n1) : 0;
+    if (quiet_cell(r, i, j, k)) return;
     const int mx = (i == 0 ? n0 - 1 : i - 1) + n0 * (j + n1 * k);
     const int my = i + n0 * ((j == 0 ? n1 - 1 : j - 1) + n1 * k);
     const float dt = r.dt;
@@ -177,6 +195,12 @@ __global__ void yee_e_kernel(const Run *__restrict__ runs, Seg seg)
     Ez[idx] = nv[2];
 }
 
+template <int DIM>
+__global__ void yee_e_kernel(const Run *__restrict__ runs, Seg seg)
+{
+    for (int vb = blockIdx.x; vb < seg.nblocks; vb += gridDim.x) yee_e_block<DIM>(runs, seg, vb);
+}
+
 // ---------------------------------------------------------------------------
 // The same updates with four consecutive x cells per thread: rows of n0 % 4 ==
 // 0 cells, 16-byte vector loads and stores of the own cells and of the +-y,
@@ -196,14 +220,10 @@ __device__ __forceinline__ void unpack4(const float4 q, float (&v)[4])
     v[3] = q.w;
 }
 
+// The four cells idx0 .. idx0+3 (one x row, one tile) of a B half step.
 template <int DIM>
-__global__ void yee_b_quad_kernel(const Run *__restrict__ runs, Seg seg, int second)
+__device__ __forceinline__ void yee_b_quad_group(const Run &r, int second, int idx0)
 {
-    const int ri = seg_run(seg, blockIdx.x);
-    const Run &r = runs[ri];
-    const int idx0 = (blockIdx.x - seg.start[ri]) * kBlock + 4 * threadIdx.x;
-    if (!second && r.fz) clear_tile_flags(r, seg, ri, (blockIdx.x - seg.start[ri]) * blockDim.x + threadIdx.x);
-    if (idx0 >= r.ncell) return;
     const RunState &s = *r.state;
     const int n0 = r.n[0], n1 = r.n[1];
     const int i0 = idx0 % n0, row = idx0 / n0, j = row % n1, k = DIM == 3 ? row / n1 : 0;
@@ -289,12 +309,21 @@ __global__ void yee_b_quad_kernel(const Run *__restrict__ runs, Seg seg, int sec
 }
 
 template <int DIM>
-__global__ void yee_e_quad_kernel(const Run *__restrict__ runs, Seg seg)
+__global__ void yee_b_quad_kernel(const Run *__restrict__ runs, Seg seg, int second)
 {
-    const int ri = seg_run(seg, blockIdx.x);
-    const Run &r = runs[ri];
-    const int idx0 = (blockIdx.x - seg.start[ri]) * kBlock + 4 * threadIdx.x;
-    if (idx0 >= r.ncell) return;
+    for (int vb = blockIdx.x; vb < seg.nblocks; vb += gridDim.x) {
+        const int ri = seg_run(seg, vb);
+        const Run &r = runs[ri];
+        const int idx0 = (vb - seg.start[ri]) * kBlock + 4 * threadIdx.x;
+        if (!second && r.fz) clear_tile_flags(r, seg, ri, (vb - seg.start[ri]) * blockDim.x + threadIdx.x);
+        if (idx0 < r.ncell) yee_b_quad_group<DIM>(r, second, idx0);
+    }
+}
+
+// The four cells idx0 .. idx0+3 (one x row, one tile) of the E step.
+template <int DIM>
+__device__ __forceinline__ void yee_e_quad_group(const Run &r, int idx0)
+{
     const RunState &s = *r.state;
     const int n0 = r.n[0], n1 = r.n[1];
     const int i0 = idx0 % n0, row = idx0 / n0, j = row % n1, k = DIM == 3 ? row / n1 : 0;
@@ -377,12 +406,117 @@ __global__ void yee_e_quad_kernel(const Run *__restrict__ runs, Seg seg)
     st4(r.E[2] + idx0, nz);
 }
 
-__global__ void zero_j_kernel(const Run *__restrict__ runs, Seg seg)
+template <int DIM>
+__global__ void yee_e_quad_kernel(const Run *__restrict__ runs, Seg seg)
 {
-    const int ri = seg_run(seg, blockIdx.x);
+    for (int vb = blockIdx.x; vb < seg.nblocks; vb += gridDim.x) {
+        const int ri = seg_run(seg, vb);
+        const Run &r = runs[ri];
+        const int idx0 = (vb - seg.start[ri]) * kBlock + 4 * threadIdx.x;
+        if (idx0 < r.ncell) yee_e_quad_group<DIM>(r, idx0);
+    }
+}
+
+// The same over a list of rows of tiles along x (those with a tile that is
+// not quiet this step): one row of tiles per block iteration, its cells in
+// x rows of four-cell groups (whole rows: the access pattern of the cell
+// grid).  Entry a of a row is ty + nt[1] tz.
+__device__ __forceinline__ int tile_group_cell(const Run &r, int a, int g, int &valid)
+{
+    const int G0 = r.n[0] >> 2, T1 = 1 << r.tlog[1];
+    const int gx = g % G0, gy = (g / G0) % T1, gz = g / (G0 * T1);
+    const int ty = a % r.nt[1], tz = a / r.nt[1];
+    const int y = (ty << r.tlog[1]) + gy, z = r.dim == 3 ? (tz << r.tlog[2]) + gz : 0;
+    valid = y < r.n[1] && (r.dim != 3 || z < r.n[2]);
+    return 4 * gx + r.n[0] * (y + r.n[1] * z);
+}
+
+__device__ __forceinline__ int tile_groups(const Run &r)
+{
+    return (r.n[0] >> 2) * (1 << r.tlog[1]) * (r.dim == 3 ? 1 << r.tlog[2] : 1);
+}
+
+template <int DIM>
+__global__ void yee_b_list_kernel(const Run *__restrict__ runs, const Item *__restrict__ list,
+                                  const int *__restrict__ count, int second)
+{
+    const int n = *count;
+    for (int e = blockIdx.x; e < n; e += gridDim.x) {
+        const Item it = list[e];
+        const Run &r = runs[it.run];
+        const int ng = tile_groups(r);
+        for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+            int valid;
+            const int idx0 = tile_group_cell(r, it.a, g, valid);
+            if (valid) yee_b_quad_group<DIM>(r, second, idx0);
+        }
+    }
+}
+
+template <int DIM>
+__global__ void yee_e_list_kernel(const Run *__restrict__ runs, const Item *__restrict__ list,
+                                  const int *__restrict__ count)
+{
+    const int n = *count;
+    for (int e = blockIdx.x; e < n; e += gridDim.x) {
+        const Item it = list[e];
+        const Run &r = runs[it.run];
+        const int ng = tile_groups(r);
+        for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+            int valid;
+            const int idx0 = tile_group_cell(r, it.a, g, valid);
+            if (valid) yee_e_quad_group<DIM>(r, idx0);
+        }
+    }
+}
+
+// J reset of the tiles a list holds (four cells per thread, 16-byte stores)
+__global__ void zero_j_list_kernel(const Run *__restrict__ runs, const Item *__restrict__ list,
+                                   const int *__restrict__ count)
+{
+    const int n = *count;
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e = blockIdx.x; e < n; e += gridDim.x) {
+        const Item it = list[e];
+        const Run &r = runs[it.run];
+        const int ng = tile_groups(r);
+        for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+            int valid;
+            const int idx0 = tile_group_cell(r, it.a, g, valid);
+            if (!valid) continue;
+            if (r.jst == 4) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) reinterpret_cast<float4 *>(r.J[0])[idx0 + q] = z;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) *reinterpret_cast<float4 *>(r.J[c] + idx0) = z;
+            }
+        }
+    }
+}
+
+// Tile flags of the step that just ended: cleared once the quiet tiles are
+// known (the B half steps set the field flags again, the slow path the
+// deposit flags).
+__global__ void clear_flags_kernel(const Run *__restrict__ runs)
+{
+    const Run &r = runs[blockIdx.y];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= r.ntiles) return;
+    r.fz[t] = 0;
+    if (r.jt) r.jt[t] = 0;
+}
+
+__device__ __forceinline__ void zero_j_block(const Run *__restrict__ runs, Seg seg, int vb)
+{
+    const int ri = seg_run(seg, vb);
     const Run &r = runs[ri];
-    const int idx = (blockIdx.x - seg.start[ri]) * blockDim.x + threadIdx.x;
+    const int idx = (vb - seg.start[ri]) * blockDim.x + threadIdx.x;
     if (idx >= r.ncell) return;
+    if (r.quiet) {  // a tile quiet at the last step kept J = 0 (no deposit reached it)
+        const int n0 = r.n[0], n1 = r.n[1], row = idx / n0;
+        if (quiet_cell(r, idx % n0, row % n1, r.dim == 3 ? row / n1 : 0)) return;
+    }
     if (r.jst == 4) {
         reinterpret_cast<float4 *>(r.J[0])[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
@@ -390,6 +524,116 @@ __global__ void zero_j_kernel(const Run *__restrict__ runs, Seg seg)
     r.J[0][idx] = 0.f;
     r.J[1][idx] = 0.f;
     r.J[2][idx] = 0.f;
+}
+
+__global__ void zero_j_kernel(const Run *__restrict__ runs, Seg seg)
+{
+    for (int vb = blockIdx.x; vb < seg.nblocks; vb += gridDim.x) zero_j_block(runs, seg, vb);
+}
+
+// Four cells per thread (kQuadThreads per block of kBlock cells), 16-byte stores.
+__device__ __forceinline__ void zero_j_quad_block(const Run *__restrict__ runs, Seg seg, int vb)
+{
+    const int ri = seg_run(seg, vb);
+    const Run &r = runs[ri];
+    const int idx0 = (vb - seg.start[ri]) * kBlock + 4 * threadIdx.x;
+    if (idx0 >= r.ncell) return;
+    if (r.quiet) {  // a tile quiet at the last step kept J = 0 (the four cells share one tile)
+        const int n0 = r.n[0], n1 = r.n[1], row = idx0 / n0;
+        if (quiet_cell(r, idx0 % n0, row % n1, r.dim == 3 ? row / n1 : 0)) return;
+    }
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r.jst == 4) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) reinterpret_cast<float4 *>(r.J[0])[idx0 + e] = z;
+        return;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) *reinterpret_cast<float4 *>(r.J[c] + idx0) = z;
+}
+
+__global__ void zero_j_quad_kernel(const Run *__restrict__ runs, Seg seg)
+{
+    for (int vb = blockIdx.x; vb < seg.nblocks; vb += gridDim.x) zero_j_quad_block(runs, seg, vb);
+}
+
+// Grid of the cell kernels: a few resident blocks per SM that walk the cell
+// segment's blocks (most blocks of a quiet box return at once; launching
+// one block per 256 cells would cost more than their work).
+int num_sms()
+{
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 1;
+    }
+    return sms;
+}
+
+int cell_grid(const Seg &cells, int blocks_per_sm)
+{
+    const int g = num_sms() * blocks_per_sm;
+    return cells.nblocks < g ? (cells.nblocks > 0 ? cells.nblocks : 1) : g;
+}
+
+// Quiet tiles of this step, computed after the particle phase and before the
+// field update: a tile is quiet when no tile within twice its deposit reach
+// (2 qr tiles per axis) has a field flag set (E and B were +0 there after the
+// last step: no live tile's particles can have deposited into this tile, and
+// no field can propagate into it within the step's three half updates, at
+// most one cell each), no slow-path particle within its reach (qr) deposited
+// this step, and the antenna's plane is not within its reach.  Such a tile's
+// E, B and J are +0 before the update and stay +0 after it.
+__global__ void quiet_kernel(const Run *__restrict__ runs)
+{
+    const Run &r = runs[blockIdx.y];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (!r.quiet || t >= r.ntiles) return;
+    const int d3 = r.dim == 3;
+    const int nt0 = r.nt[0], nt1 = r.nt[1], nt2 = d3 ? r.nt[2] : 1;
+    const int tx = t % nt0, ty = (t / nt0) % nt1, tz = d3 ? t / (nt0 * nt1) : 0;
+    const int q0 = r.qr[0], q1 = r.qr[1], q2 = d3 ? r.qr[2] : 0;
+    bool q = true;
+    for (int dz = -2 * q2; dz <= 2 * q2 && q; ++dz) {
+        const int z = modi(tz + dz, nt2);
+        for (int dy = -2 * q1; dy <= 2 * q1 && q; ++dy) {
+            const int y = modi(ty + dy, nt1);
+            for (int dx = -2 * q0; dx <= 2 * q0 && q; ++dx) {
+                const int u = modi(tx + dx, nt0) + nt0 * (y + nt1 * z);
+                const bool near = abs(dx) <= q0 && abs(dy) <= q1 && abs(dz) <= q2;
+                q = !r.fz[u] && !(near && r.jt[u]);
+            }
+        }
+    }
+    if (q && r.laser_on) {  // the antenna's plane (storage index) within reach
+        const int nl = r.n[r.dim - 1], ntl = d3 ? nt2 : nt1, ql = d3 ? q2 : q1;
+        int st = r.laser_plane + r.state->origin;
+        st = st >= nl ? st - nl : st;
+        int dl = abs((d3 ? tz : ty) - (st >> r.tlog[r.dim - 1]));
+        dl = dl < ntl - dl ? dl : ntl - dl;
+        q = dl > ql;
+    }
+    r.quiet[t] = q ? 1 : 0;
+}
+
+// The rows of tiles along x with a tile that is not quiet, for the field
+// update (one thread per row, warp-aggregated appends).
+__global__ void quiet_rows_kernel(const Run *__restrict__ runs, Item *__restrict__ nq, int *__restrict__ nq_count)
+{
+    const Run &r = runs[blockIdx.y];
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nrows = r.nt[1] * (r.dim == 3 ? r.nt[2] : 1);
+    bool busy = false;
+    if (r.quiet && a < nrows)
+        for (int tx = 0; tx < r.nt[0] && !busy; ++tx) busy = !r.quiet[tx + r.nt[0] * a];
+    const unsigned m = __ballot_sync(0xffffffffu, busy);
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0 && m) base = atomicAdd(nq_count, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (busy) nq[base + __popc(m & ((1u << lane) - 1u))] = Item{(int)blockIdx.y, 0, a, 0};
 }
 
 // storage offset of physical plane `pl` (last axis) and transverse position q
@@ -569,20 +813,23 @@ __global__ void window_commit_kernel(const Run *__restrict__ runs, int nruns)
 
 }  // namespace
 
-cudaError_t launch_zero_j(const Run *runs, Seg cells, cudaStream_t st)
+cudaError_t launch_zero_j(const Run *runs, Seg cells, bool quad, cudaStream_t st)
 {
-    zero_j_kernel<<<cells.nblocks, kBlock, 0, st>>>(runs, cells);
+    if (quad) zero_j_quad_kernel<<<cell_grid(cells, 24), kQuadThreads, 0, st>>>(runs, cells);
+    else zero_j_kernel<<<cell_grid(cells, 8), kBlock, 0, st>>>(runs, cells);
     return cudaGetLastError();
 }
 
 cudaError_t launch_yee_b(int dim, const Run *runs, Seg cells, int second_half, bool quad, cudaStream_t st)
 {
     if (quad) {
-        if (dim == 3) yee_b_quad_kernel<3><<<cells.nblocks, kQuadThreads, 0, st>>>(runs, cells, second_half);
-        else yee_b_quad_kernel<2><<<cells.nblocks, kQuadThreads, 0, st>>>(runs, cells, second_half);
+        const int g = cell_grid(cells, 24);
+        if (dim == 3) yee_b_quad_kernel<3><<<g, kQuadThreads, 0, st>>>(runs, cells, second_half);
+        else yee_b_quad_kernel<2><<<g, kQuadThreads, 0, st>>>(runs, cells, second_half);
     } else {
-        if (dim == 3) yee_b_kernel<3><<<cells.nblocks, kBlock, 0, st>>>(runs, cells, second_half);
-        else yee_b_kernel<2><<<cells.nblocks, kBlock, 0, st>>>(runs, cells, second_half);
+        const int g = cell_grid(cells, 8);
+        if (dim == 3) yee_b_kernel<3><<<g, kBlock, 0, st>>>(runs, cells, second_half);
+        else yee_b_kernel<2><<<g, kBlock, 0, st>>>(runs, cells, second_half);
     }
     return cudaGetLastError();
 }
@@ -590,11 +837,13 @@ cudaError_t launch_yee_b(int dim, const Run *runs, Seg cells, int second_half, b
 cudaError_t launch_yee_e(int dim, const Run *runs, Seg cells, bool quad, cudaStream_t st)
 {
     if (quad) {
-        if (dim == 3) yee_e_quad_kernel<3><<<cells.nblocks, kQuadThreads, 0, st>>>(runs, cells);
-        else yee_e_quad_kernel<2><<<cells.nblocks, kQuadThreads, 0, st>>>(runs, cells);
+        const int g = cell_grid(cells, 24);
+        if (dim == 3) yee_e_quad_kernel<3><<<g, kQuadThreads, 0, st>>>(runs, cells);
+        else yee_e_quad_kernel<2><<<g, kQuadThreads, 0, st>>>(runs, cells);
     } else {
-        if (dim == 3) yee_e_kernel<3><<<cells.nblocks, kBlock, 0, st>>>(runs, cells);
-        else yee_e_kernel<2><<<cells.nblocks, kBlock, 0, st>>>(runs, cells);
+        const int g = cell_grid(cells, 8);
+        if (dim == 3) yee_e_kernel<3><<<g, kBlock, 0, st>>>(runs, cells);
+        else yee_e_kernel<2><<<g, kBlock, 0, st>>>(runs, cells);
     }
     return cudaGetLastError();
 }
@@ -608,6 +857,32 @@ cudaError_t launch_mur_save(const Run *runs, Seg planes, cudaStream_t st)
 cudaError_t launch_mur_apply(const Run *runs, Seg planes, cudaStream_t st)
 {
     mur_apply_kernel<<<planes.nblocks, kBlock, 0, st>>>(runs, planes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_quiet(const Run *runs, int nruns, int max_tiles, Item *nq, int *nq_count, cudaStream_t st)
+{
+    if (max_tiles <= 0) return cudaSuccess;
+    const dim3 g((max_tiles + kBlock - 1) / kBlock, nruns);
+    quiet_kernel<<<g, kBlock, 0, st>>>(runs);
+    quiet_rows_kernel<<<g, kBlock, 0, st>>>(runs, nq, nq_count);  // (rows <= tiles)
+    clear_flags_kernel<<<g, kBlock, 0, st>>>(runs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_list(int which, int dim, const Run *runs, const Item *nq, const int *nq_count, int second,
+                              cudaStream_t st)
+{
+    const int g = num_sms() * 4;  // (resident blocks walk the list)
+    constexpr int kListThreads = 256;
+    if (which == 0) zero_j_list_kernel<<<g, kListThreads, 0, st>>>(runs, nq, nq_count);
+    else if (which == 1) {
+        if (dim == 3) yee_b_list_kernel<3><<<g, kListThreads, 0, st>>>(runs, nq, nq_count, second);
+        else yee_b_list_kernel<2><<<g, kListThreads, 0, st>>>(runs, nq, nq_count, second);
+    } else {
+        if (dim == 3) yee_e_list_kernel<3><<<g, kListThreads, 0, st>>>(runs, nq, nq_count);
+        else yee_e_list_kernel<2><<<g, kListThreads, 0, st>>>(runs, nq, nq_count);
+    }
     return cudaGetLastError();
 }
 

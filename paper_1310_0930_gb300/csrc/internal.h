@@ -73,7 +73,7 @@ cudaError_t launch_push_zero(int dim, int order, bool split, const Run *runs, co
                              int max_items, int num_sms, cudaStream_t st);
 
 // fields.cu
-cudaError_t launch_zero_j(const Run *runs, Seg cells, cudaStream_t st);
+cudaError_t launch_zero_j(const Run *runs, Seg cells, bool quad, cudaStream_t st);
 // quad: four x cells per thread with 16-byte accesses (every run's n0 a
 // multiple of 4 and its field arrays 16-byte aligned)
 cudaError_t launch_yee_b(int dim, const Run *runs, Seg cells, int second_half, bool quad, cudaStream_t st);
@@ -81,6 +81,15 @@ cudaError_t launch_yee_e(int dim, const Run *runs, Seg cells, bool quad, cudaStr
 cudaError_t launch_mur_save(const Run *runs, Seg planes, cudaStream_t st);
 cudaError_t launch_mur_apply(const Run *runs, Seg planes, cudaStream_t st);
 cudaError_t launch_end_step(const Run *runs, int nruns, cudaStream_t st);
+// quiet tiles of this step (after the particle phase, before the field
+// update): the quiet flags, the list of the rows of tiles along x holding a
+// tile that is not quiet (nq, Item::a = ty + nt[1] tz; count in *nq_count,
+// which the caller zeroes first), then the step's tile flags cleared
+cudaError_t launch_quiet(const Run *runs, int nruns, int max_tiles, Item *nq, int *nq_count, cudaStream_t st);
+// the field update over the rows of tiles of a list: which 0 = J reset, 1 = B
+// half step (second: the step's second half), 2 = E step; 4-cell rows only
+cudaError_t launch_field_list(int which, int dim, const Run *runs, const Item *nq, const int *nq_count, int second,
+                              cudaStream_t st);
 cudaError_t launch_window(const Run *runs, Seg planes, Seg inject, cudaStream_t st);
 
 // sort.cu

@@ -90,6 +90,8 @@ struct pic_s {
     bool classify = true;         // stream the zero-field tiles (launch_classify)
     Item *d_live = nullptr;       // per step: tail items, then the live tiles
     Item *d_zero = nullptr;       // per step: the zero-field tiles
+    Item *d_nq = nullptr;         // per step: the rows of tiles with a tile that is not quiet (field update, next J reset)
+    bool field_list = false;      // the field update walks d_nq (quiet tiles on, 4-cell rows)
     int *d_cnt = nullptr;         // [4]: live tiles, zero tiles, work queue of the live kernel, spare
     int stage_lo[3] = {0, 0, 0}, stage_len[3] = {1, 1, 1};  // field region a tile stages
     int *d_seg = nullptr;  // 5 segment tables of nruns+1 ints
@@ -353,11 +355,17 @@ int build_items(pic_s *h)
     if (h->d_items) dev_free(h, h->d_items);
     if (h->d_live) dev_free(h, h->d_live);
     if (h->d_zero) dev_free(h, h->d_zero);
+    if (h->d_nq) dev_free(h, h->d_nq);
     const size_t nb = sizeof(Item) * (items.size() ? items.size() : 1);
     h->d_items = (Item *)dev_alloc(h, nb);
     h->d_live = (Item *)dev_alloc(h, nb);
     h->d_zero = (Item *)dev_alloc(h, nb);
-    if (!h->d_items || !h->d_live || !h->d_zero) return PIC_ENOMEM;
+    h->d_nq = (Item *)dev_alloc(h, nb);  // (every tile of every run fits)
+    if (!h->d_items || !h->d_live || !h->d_zero || !h->d_nq) return PIC_ENOMEM;
+    // the field update walks the non-quiet tiles when every run keeps quiet
+    // flags and 4-cell rows
+    h->field_list = h->classify && h->yee_quad;
+    for (int i = 0; i < h->nruns; ++i) h->field_list = h->field_list && h->runs[i].r.quiet;
     h->n_items = (int)items.size();
     h->n_tail = n_tail;
     cudaError_t e = cudaMemcpyAsync(h->d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice,
@@ -365,6 +373,20 @@ int build_items(pic_s *h)
     // the live list starts with the tail items; the classification appends the live tiles
     if (e == cudaSuccess && n_tail)
         e = cudaMemcpyAsync(h->d_live, items.data(), sizeof(Item) * n_tail, cudaMemcpyHostToDevice, h->stream);
+    // the list of rows of tiles (along x) that are not quiet starts with every
+    // row, so that the first J reset clears them all (each step's quiet
+    // kernels then write the list the next J reset and that step's field
+    // update walk)
+    std::vector<Item> rows;
+    for (int i = 0; i < h->nruns; ++i) {
+        const Run &r = h->runs[i].r;
+        const int nrows = r.nt[1] * (r.dim == 3 ? r.nt[2] : 1);
+        for (int a = 0; a < nrows; ++a) rows.push_back(Item{i, 0, a, 0});
+    }
+    const int n_all = (int)rows.size();
+    if (e == cudaSuccess && n_all > 0)
+        e = cudaMemcpyAsync(h->d_nq, rows.data(), sizeof(Item) * n_all, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_cnt + 3, &n_all, sizeof(int), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     return cuda_fail(e);
 }
@@ -417,7 +439,9 @@ int enqueue_step(pic_s *h, bool sort, bool adaptive)
         if (e == cudaSuccess) e = cudaMemcpyAsync(rc.st, h->d_states, sizeof(RunState), cudaMemcpyDeviceToDevice, st);
     }
     mark(PIC_PH_ZERO_J);
-    if (e == cudaSuccess) e = launch_zero_j(R, h->seg_cells, st);
+    // J is +0 outside the tiles that were not quiet at the last step
+    if (e == cudaSuccess && h->field_list) e = launch_field_list(0, h->dim, R, h->d_nq, h->d_cnt + 3, 0, st);
+    else if (e == cudaSuccess) e = launch_zero_j(R, h->seg_cells, h->yee_quad, st);
     mark(PIC_PH_PUSH);
     if (h->classify) {
         // live tiles (and the tail) through the staged kernel, zero-field tiles streamed
@@ -439,20 +463,34 @@ int enqueue_step(pic_s *h, bool sort, bool adaptive)
         if (ev && e == cudaSuccess) e = cudaEventRecord(ev[kMarkZero], st);
     }
     mark(PIC_PH_YEE_B1);
-    if (e == cudaSuccess) e = launch_yee_b(h->dim, R, h->seg_cells, 0, h->yee_quad, st);
-    mark(PIC_PH_YEE_E);
-    if (e == cudaSuccess && h->any_open) e = launch_mur_save(R, h->seg_planes, st);
-    if (e == cudaSuccess) e = launch_yee_e(h->dim, R, h->seg_cells, h->yee_quad, st);
-    if (e == cudaSuccess && h->any_open) e = launch_mur_apply(R, h->seg_planes, st);
-    mark(PIC_PH_YEE_B2);
-    if (e == cudaSuccess) e = launch_yee_b(h->dim, R, h->seg_cells, 1, h->yee_quad, st);
+    if (h->field_list) {  // quiet tiles: their field update is the identity; the others from a list
+        if (e == cudaSuccess) e = launch_quiet(R, h->nruns, h->max_tiles, h->d_nq, h->d_cnt + 3, st);
+        if (e == cudaSuccess) e = launch_field_list(1, h->dim, R, h->d_nq, h->d_cnt + 3, 0, st);
+        mark(PIC_PH_YEE_E);
+        if (e == cudaSuccess && h->any_open) e = launch_mur_save(R, h->seg_planes, st);
+        if (e == cudaSuccess) e = launch_field_list(2, h->dim, R, h->d_nq, h->d_cnt + 3, 0, st);
+        if (e == cudaSuccess && h->any_open) e = launch_mur_apply(R, h->seg_planes, st);
+        mark(PIC_PH_YEE_B2);
+        if (e == cudaSuccess) e = launch_field_list(1, h->dim, R, h->d_nq, h->d_cnt + 3, 1, st);
+    } else {
+        if (e == cudaSuccess) e = launch_yee_b(h->dim, R, h->seg_cells, 0, h->yee_quad, st);
+        mark(PIC_PH_YEE_E);
+        if (e == cudaSuccess && h->any_open) e = launch_mur_save(R, h->seg_planes, st);
+        if (e == cudaSuccess) e = launch_yee_e(h->dim, R, h->seg_cells, h->yee_quad, st);
+        if (e == cudaSuccess && h->any_open) e = launch_mur_apply(R, h->seg_planes, st);
+        mark(PIC_PH_YEE_B2);
+        if (e == cudaSuccess) e = launch_yee_b(h->dim, R, h->seg_cells, 1, h->yee_quad, st);
+    }
     mark(PIC_PH_WINDOW);
     if (e == cudaSuccess) e = launch_end_step(R, h->nruns, st);
     if (e == cudaSuccess && h->any_window) e = launch_window(R, h->seg_planes, h->seg_inject, st);
     mark(kMarkEnd);
     if (ev) {
         h->prof_steps += 1;
-        h->prof_launches += (sort ? 6 : 0) + 6 + (h->classify ? 2 : 0) + (h->any_open ? 2 : 0) + (h->any_window ? 3 : 0);
+        // sort 8, J reset 1, particle phase 1 (with the streaming: classification,
+        // staged, streaming kernels and quiet tiles 4), Yee 3, end of step 1
+        h->prof_launches += (sort || adaptive ? 8 : 0) + 1 + (h->classify ? 3 : 1) + (h->field_list ? 2 : 0) + 3 + 1 +
+                            (h->any_open ? 2 : 0) + (h->any_window ? 3 : 0) + (h->adj && h->adj->rec_on ? 1 : 0);
     }
     return cuda_fail(e);
 }
@@ -609,6 +647,19 @@ int init_run(pic_s *h, HostRun &hr, int idx)
     r.tile_cnt = (int32_t *)dev_alloc(h, sizeof(int32_t) * ((size_t)r.ntiles * r.nsub + 1));
     r.fz = (uint8_t *)dev_alloc(h, (size_t)r.ntiles);
     if (!r.rho0 || !hr.rho || !hr.rho32 || !r.mur || !r.tile_off || !r.tile_cnt || !r.fz) return PIC_ENOMEM;
+    if (h->classify) {  // quiet tiles: the field update skips them (with the zero-field streaming)
+        static const int kDepositReach[5] = {0, 2, 3, 3, 4};  // cells beyond a particle's cell its window reaches
+        for (int a = 0; a < 3; ++a) {
+            const int T = 1 << r.tlog[a], reach = r.drift + kDepositReach[r.order];
+            r.qr[a] = a < r.dim ? (reach + T - 1) / T : 0;
+        }
+        r.jt = (uint8_t *)dev_alloc(h, (size_t)r.ntiles);
+        r.quiet = (uint8_t *)dev_alloc(h, (size_t)r.ntiles);
+        if (!r.jt || !r.quiet) return PIC_ENOMEM;
+        if (cudaMemsetAsync(r.jt, 0, (size_t)r.ntiles, h->stream) != cudaSuccess ||
+            cudaMemsetAsync(r.quiet, 0, (size_t)r.ntiles, h->stream) != cudaSuccess)
+            return PIC_ECUDA;
+    }
     cudaError_t e = cudaSuccess;
     for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
         e = cudaMemsetAsync(r.E[a], 0, sizeof(float) * ncell, h->stream);

@@ -899,6 +899,12 @@ __device__ __noinline__ SlowOut advance_global(const Run &r, const GlobalFields 
     const GlobalGather<DIM, P> gather{gf};
     o.ok = push_move<DIM, P>(r, gather, c, d, u, d1, k, ig);
     if (!o.ok) return o;
+    if (r.jt) {  // this move deposits current near its tile: the tile's neighbours are not quiet
+        bool moves = DIM == 2 && u[2] != 0.f;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) moves = moves || k[a] != 0 || d1[a] != d[a];
+        if (moves) r.jt[tile_of(r, c0, c1, DIM == 3 ? c2 : 0)] = 1;
+    }
     const float qw = r.q * w;
     float *J[3] = {r.J[0], r.J[1], r.J[2]};
     const int n0 = gf.n0, n1 = gf.n1, n2 = gf.n2;
