@@ -650,7 +650,8 @@ int init_run(pic_s *h, HostRun &hr, int idx)
     if (h->classify) {  // quiet tiles: the field update skips them (with the zero-field streaming)
         static const int kDepositReach[5] = {0, 2, 3, 3, 4};  // cells beyond a particle's cell its window reaches
         for (int a = 0; a < 3; ++a) {
-            const int T = 1 << r.tlog[a], reach = r.drift + kDepositReach[r.order];
+            // (a particle may be a drift allowance, or one move, from its tile)
+            const int T = 1 << r.tlog[a], reach = (r.drift > 1 ? r.drift : 1) + kDepositReach[r.order];
             r.qr[a] = a < r.dim ? (reach + T - 1) / T : 0;
         }
         r.jt = (uint8_t *)dev_alloc(h, (size_t)r.ntiles);
