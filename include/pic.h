@@ -145,7 +145,7 @@ typedef void (*pic_free_fn)(void *ptr, void *ctx);
 /* Tuning: tile[a] cells per tile per axis (powers of two, 0 = default);
  * sort_interval: steps between tile sorts under the fixed policy (0 =
  * default, 4), the longest interval under the adaptive one (0 = default,
- * 16); sort_policy: 0 = adaptive (default): each step the device sorts a
+ * 32); sort_policy: 0 = adaptive (default): each step the device sorts a
  * run when sort_interval steps have passed since its last sort or when its
  * push has sent, summed over the steps since that sort, at least 1/65536 of
  * its particles down the slow path from their tiles (particles outside their
@@ -195,7 +195,13 @@ typedef void (*pic_free_fn)(void *ptr, void *ctx);
  * tile's particles by row of cells along x (their y and z cell in the
  * tile), so that the particles one warp pushes together lie in one or two
  * rows and share field-tile addresses; 2 = no order inside a tile.  Only the
- * assignment of particles to threads changes. */
+ * assignment of particles to threads changes.
+ * quiet_tiles (with stream_zero_tiles on): the field update and the J reset
+ * skip the tiles whose E, B and J stay +0 through the step (no fields within
+ * twice a tile's deposit reach after the last step, no slow-path deposit in
+ * reach, no antenna plane in reach) and walk the others as a list: 0 =
+ * default (on for handles of at least 2^22 cells), 1 = on, 2 = off.  The
+ * result is the same either way. */
 typedef struct {
     int32_t tile[3];
     int32_t sort_interval;
@@ -211,6 +217,7 @@ typedef struct {
     int32_t deposit;
     int32_t j_layout;
     int32_t sort_rows;
+    int32_t quiet_tiles;
 } pic_tuning;
 
 typedef struct {

@@ -45,7 +45,7 @@ class pic_tuning(ctypes.Structure):
                 ("use_graph", c_int32), ("persistent", c_int32), ("sort_sub", c_int32),
                 ("tma", c_int32), ("adjoint_keep", c_int32), ("sort_policy", c_int32),
                 ("stream_zero_tiles", c_int32), ("deposit", c_int32), ("j_layout", c_int32),
-                ("sort_rows", c_int32)]
+                ("sort_rows", c_int32), ("quiet_tiles", c_int32)]
 
 
 pic_alloc_fn = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p)

@@ -29,6 +29,8 @@ constexpr int kSortHashLog = 9, kSortHash = 1 << kSortHashLog, kSortProbe = 32;
 // adaptive sort: sort once strays (particles outside their tile's drift
 // region) add up to n_total / kSortSlowDiv particle-steps since the last sort
 constexpr unsigned long long kSortSlowDiv = 65536;
+// ... or once the unsorted tail the window injected holds n_total / kSortTailDiv
+constexpr unsigned long long kSortTailDiv = 64;
 // The exclusive scan of the (tile, sub-bucket) counters runs in blocks of
 // kScanChunk keys (kScanThreads threads x kScanItems consecutive keys).
 constexpr int kScanThreads = 256, kScanItems = 16, kScanChunk = kScanThreads * kScanItems;

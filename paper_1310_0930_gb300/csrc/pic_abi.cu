@@ -27,7 +27,7 @@ constexpr int kTail = 256;              // particles per tail work item (at leas
 // order, the end mark, and the start of the zero-field kernel (the end of
 // PIC_PH_PUSH_ZERO is the mark that opens PIC_PH_YEE_B1)
 constexpr int kMarkEnd = PIC_PH_WINDOW + 1, kMarkZero = kMarkEnd + 1, kEvPerStep = kMarkZero + 1;
-constexpr int kSortMaxAdaptive = 16;    // default longest interval between sorts, adaptive policy
+constexpr int kSortMaxAdaptive = 32;    // default longest interval between sorts, adaptive policy
 
 struct HostRun {
     pic_config cfg;
@@ -99,6 +99,7 @@ struct pic_s {
     Seg seg_cells{}, seg_planes{}, seg_parts{}, seg_inject{}, seg_keys{};
     int sort_sub = 1;
     bool sort_rows = true;  // each tile's particles grouped by row of cells along x
+    int quiet_mode = 0;     // pic_tuning.quiet_tiles
     bool use_tma = false;
     bool split = false;  // virtual-trajectory deposit (pic_tuning.deposit = 1)
     bool j4 = false;     // four-component current nodes (pic_tuning.j_layout = 1)
@@ -220,6 +221,7 @@ int validate(const pic_config *c)
     if (t.deposit < 0 || t.deposit > 1 || (t.deposit == 1 && t.tma > 0)) return PIC_EINVAL;
     if (t.j_layout < 0 || t.j_layout > 1) return PIC_EINVAL;
     if (t.sort_rows < 0 || t.sort_rows > 2 || (t.sort_rows == 1 && t.sort_sub > 1)) return PIC_EINVAL;
+    if (t.quiet_tiles < 0 || t.quiet_tiles > 2) return PIC_EINVAL;
     return PIC_OK;
 }
 
@@ -363,9 +365,16 @@ int build_items(pic_s *h)
     h->d_nq = (Item *)dev_alloc(h, nb);  // (every tile of every run fits)
     if (!h->d_items || !h->d_live || !h->d_zero || !h->d_nq) return PIC_ENOMEM;
     // the field update walks the non-quiet tiles when every run keeps quiet
-    // flags and 4-cell rows
+    // flags and 4-cell rows, and the handle is large enough for the three
+    // extra launches per step to pay (below 2^22 cells a step takes tens of
+    // microseconds and the cell kernels are faster)
     h->field_list = h->classify && h->yee_quad;
-    for (int i = 0; i < h->nruns; ++i) h->field_list = h->field_list && h->runs[i].r.quiet;
+    long long cells = 0;
+    for (int i = 0; i < h->nruns; ++i) {
+        h->field_list = h->field_list && h->runs[i].r.quiet;
+        cells += h->runs[i].r.ncell;
+    }
+    h->field_list = h->field_list && (h->quiet_mode == 1 || (h->quiet_mode == 0 && cells >= (1ll << 22)));
     h->n_items = (int)items.size();
     h->n_tail = n_tail;
     cudaError_t e = cudaMemcpyAsync(h->d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice,
@@ -647,7 +656,7 @@ int init_run(pic_s *h, HostRun &hr, int idx)
     r.tile_cnt = (int32_t *)dev_alloc(h, sizeof(int32_t) * ((size_t)r.ntiles * r.nsub + 1));
     r.fz = (uint8_t *)dev_alloc(h, (size_t)r.ntiles);
     if (!r.rho0 || !hr.rho || !hr.rho32 || !r.mur || !r.tile_off || !r.tile_cnt || !r.fz) return PIC_ENOMEM;
-    if (h->classify) {  // quiet tiles: the field update skips them (with the zero-field streaming)
+    if (h->classify && h->quiet_mode != 2) {  // quiet tiles: the field update skips them (with the zero-field streaming)
         static const int kDepositReach[5] = {0, 2, 3, 3, 4};  // cells beyond a particle's cell its window reaches
         for (int a = 0; a < 3; ++a) {
             // (a particle may be a drift allowance, or one move, from its tile)
@@ -743,6 +752,7 @@ int create_common(const pic_config *cfgs, int n, pic_t **out)
     h->persistent = t.persistent == 1 || (t.persistent == 0 && n > 1);
     h->sort_sub = t.sort_sub ? t.sort_sub : 1;
     h->sort_rows = t.sort_rows == 1 || (t.sort_rows == 0 && h->sort_sub == 1);
+    h->quiet_mode = t.quiet_tiles;
     h->use_tma = t.tma > 0;
     h->split = t.deposit == 1;
     h->j4 = t.j_layout == 1;

@@ -115,8 +115,9 @@ __device__ __forceinline__ int key_of_cell(const KeyCtx &k, int32_t c)
 // slow path (global gather and global atomics) and stalls the other lanes of
 // its warp meanwhile: a fraction of a percent of strays costs the push more
 // than a sort, so the threshold is low.  The unsorted tail of particles
-// injected by the moving window is not counted (it is pushed by CTAs of its
-// own, and the longest interval bounds it).
+// injected by the moving window is not counted as strays (it is pushed by
+// CTAs of its own); a run also sorts once its tail holds n_total /
+// kSortTailDiv particles (tail particles take the slow path).
 // The kernels of the sort below skip the runs that do not sort.
 __global__ void sort_decide_kernel(const Run *__restrict__ runs, int nruns, int force, int max_interval,
                                    int adaptive)
@@ -127,7 +128,9 @@ __global__ void sort_decide_kernel(const Run *__restrict__ runs, int nruns, int 
     bool go = force != 0;
     if (adaptive) {
         const unsigned long long n = s.n_total > 0 ? (unsigned long long)s.n_total : 0ull;
-        go = go || s.since_sort >= max_interval || (s.slow_acc > 0 && s.slow_acc * kSortSlowDiv >= n);
+        const unsigned long long tail = s.n_total > s.n_sorted ? (unsigned long long)(s.n_total - s.n_sorted) : 0ull;
+        go = go || s.since_sort >= max_interval || (s.slow_acc > 0 && s.slow_acc * kSortSlowDiv >= n) ||
+             tail * kSortTailDiv >= n;
     }
     s.do_sort = go ? 1 : 0;
     if (go) {

@@ -84,6 +84,7 @@ def make_config(w: Workload, *, tuning: Optional[dict] = None, track_ids=False, 
     cfg.tuning.deposit = int(t.get("deposit", 0))
     cfg.tuning.j_layout = int(t.get("j_layout", 0))
     cfg.tuning.sort_rows = int(t.get("sort_rows", 0))
+    cfg.tuning.quiet_tiles = int(t.get("quiet_tiles", 0))
     if alloc is not None:
         cfg.alloc = alloc
         cfg.free = free

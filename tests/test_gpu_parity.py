@@ -144,7 +144,7 @@ def test_adaptive_sort_follows_the_slow_path():
     interval, a fast stream (|u| = 5, 0.69 cells per step) sorts as soon as
     particles stray beyond the drift region; both step like the fixed policy."""
     steps = 40
-    for uth, lo, hi in ((0.01, 2, 4), (5.0, 8, 41)):
+    for uth, lo, hi in ((0.01, 1, 3), (5.0, 8, 41)):
         w = inputs.thermal_2d(n=(64, 64), steps=steps)
         w.uth = uth
         parts = inputs.background(w)

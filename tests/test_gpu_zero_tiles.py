@@ -1,8 +1,10 @@
 """Zero-field tiles: each step the device classifies the tiles, and those whose
 staged field region is all +0 (E = B = 0 at every particle) are advanced by a
-streaming kernel instead of the staged tile kernel.  The results must not
-depend on that choice: against the same run with every tile staged
-(stream_zero_tiles = 2), and against the FP64 oracle.
+streaming kernel instead of the staged tile kernel; quiet tiles (E, B and J
++0 through the step) are left out of the field update.  The results must not
+depend on either choice: against the same run with every tile staged
+(stream_zero_tiles = 2), with the field update over every tile
+(quiet_tiles = 2), and against the FP64 oracle.
 
 Tolerances as in the other parity tests: fields relative L2 <= 1e-5 between
 the two device runs (only the order of the FP32 atomic current sums
@@ -32,7 +34,8 @@ def test_lwfa_3d_streamed_tiles_equal_staged_and_oracle():
     w.window.t0 = 10.0
     parts = inputs.background(w)
     extra = 16 * 16 * 8 * 40
-    gpu, orc = pair(w, parts, extra=extra)
+    # (quiet tiles forced on: at this size the default leaves them off)
+    gpu, orc = pair(w, parts, extra=extra, tuning={"quiet_tiles": 1})
     staged = Simulation(w, tuning={"stream_zero_tiles": 2}, track_ids=True)
     staged.load(parts)
     gpu.profile_begin(10)
@@ -145,3 +148,45 @@ def test_immobile_plasma_in_imposed_fields_gathers_and_stays():
     for name in FIELD_NAMES:
         assert rel_l2(gpu.field(name), orc.field(name)) <= 1e-5, name
     gpu.close()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_quiet_tiles_leave_the_fields_unchanged(dim):
+    """The field update over the non-quiet rows of tiles only (quiet_tiles =
+    1) against the update over every cell (quiet_tiles = 2), both with the
+    zero-field streaming, and against the oracle: a laser entering a plasma
+    box through its rear plane and a window that starts moving, so that the
+    quiet region ahead of the pulse shrinks, and the window injects plasma
+    (slow-path tail particles) at the front."""
+    if dim == 3:
+        w = inputs.lwfa_3d(n=(16, 16, 128), steps=70)
+        w.laser.a0, w.laser.waist, w.laser.fwhm = 1.5, 5.0, 6.0
+        w.window.t0 = 10.0
+        extra = 16 * 16 * 8 * 60
+    else:
+        w = inputs.lwfa_2d(nx=32, nz=256, ppc=(2, 2), density=0.01, a0=2.0, waist=8.0, steps=120)
+        w.laser.fwhm = 6.0
+        w.window.t0 = 18.0
+        extra = 32 * 4 * 120
+    parts = inputs.background(w)
+    on, orc = pair(w, parts, extra=extra, tuning={"quiet_tiles": 1})
+    off = Simulation(w, tuning={"quiet_tiles": 2}, track_ids=True)
+    off.load(parts)
+    on.step(w.steps)
+    off.step(w.steps)
+    orc.step(w.steps)
+    d, do = on.diagnostics(), off.diagnostics()
+    assert d["status"] == 0 and do["status"] == 0
+    assert d["shifts"] == do["shifts"] == orc.shifts > 5
+    assert d["n_particles"] == do["n_particles"] == orc.np
+    assert 0 < d["streamed"]
+    for name in FIELD_NAMES:
+        a = on.field(name).astype(np.float64)
+        assert rel_l2(a, off.field(name)) <= 1e-5, name
+        assert rel_l2(a, orc.field(name)) <= 1e-4, name
+    for name in ("Jx", "Jy", "Jz"):
+        assert rel_l2(on.field(name), off.field(name)) <= 1e-5, name
+    pa, pb = _by_id(on.particles()), _by_id(off.particles())
+    assert np.array_equal(pa["id"], pb["id"]) and np.array_equal(pa["cell"], pb["cell"])
+    on.close()
+    off.close()
