@@ -1278,15 +1278,17 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
 // +0), so a particle at rest stays where it is and deposits no current: its
 // step reads its cell (absorption at an open window's ends) and momentum and
 // changes nothing else.  Such tiles are streamed by this kernel with 16-byte
-// loads (two groups of four consecutive slots per thread; the ragged ends of
-// a tile's range slot by slot) and no shared-memory tiles, so that many CTAs
-// per SM keep loads in flight.  A particle of such a tile that does
+// loads (four groups of four consecutive slots per thread, two CTAs of 256
+// threads per SM; the ragged ends of a tile's range slot by slot) and no
+// shared-memory tiles; each CTA loads its next item while it streams the
+// current one.  A particle of such a tile that does
 // move takes the general slow path (the gather from global memory reads the
 // same zeros; the current goes to global memory by atomics) and is counted as
 // a slow-path particle.  Particles outside their tile's drift region cost
 // nothing here (no tile is staged) and are not counted as strays: the
 // adaptive sort counts the strays that slow the staged kernel down.
 constexpr int kZeroThreads = 256;
+constexpr int kZeroGroups = 4;  // groups of four slots per thread and iteration
 
 struct ZeroCtx {
     int origin, nl;
@@ -1345,34 +1347,37 @@ __device__ __forceinline__ void zero_mover(const Run &r, const ZeroCtx &z, const
 }
 
 template <int DIM, int P, bool SPLIT>
-__global__ void __launch_bounds__(kZeroThreads, 3) push_zero_kernel(const Run *__restrict__ runs,
+__global__ void __launch_bounds__(kZeroThreads, 2) push_zero_kernel(const Run *__restrict__ runs,
                                                                     const Item *__restrict__ list,
                                                                     const int *__restrict__ count)
 {
     __shared__ Run rs;
-    __shared__ unsigned s_slow;
     const int n = *count;
+    int w = blockIdx.x;
+    if (w >= n) return;
     int cur = -1;
-    for (int w = blockIdx.x; w < n; w += gridDim.x) {
-        const Item it = list[w];
-        __syncthreads();  // (the previous item is done with rs and the counter)
-        if (it.run != cur) {
+    ParticleBuf pb;
+    ZeroCtx z;
+    Item it = list[w];
+    for (; w < n; w += gridDim.x) {
+        if (it.run != cur) {  // (the same in every thread)
+            __syncthreads();  // (every thread is done with the previous run's copy)
             const int *src = reinterpret_cast<const int *>(runs + it.run);
             int *dst = reinterpret_cast<int *>(&rs);
             for (int q = threadIdx.x; q < (int)(sizeof(Run) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
             cur = it.run;
+            __syncthreads();
+            const RunState *stp = rs.state;
+            pb = rs.P[stp->buf];
+            z.origin = stp->origin;
+            z.nl = rs.n[DIM - 1];
+            z.last_shift = DIM == 3 ? rs.bits[0] + rs.bits[1] : rs.bits[0];
         }
-        if (threadIdx.x == 0) s_slow = 0;
-        __syncthreads();
         const Run &r = rs;
-        const RunState *stp = r.state;
-        const ParticleBuf pb = r.P[stp->buf];
-        ZeroCtx z;
-        z.origin = stp->origin;
-        z.nl = r.n[DIM - 1];
-        z.last_shift = DIM == 3 ? r.bits[0] + r.bits[1] : r.bits[0];
         const int t = it.a;
         const long long p0 = r.tile_off[t], p1 = r.tile_off[t + 1];
+        // (the next item is loaded while this one streams)
+        if (w + (int)gridDim.x < n) it = list[w + gridDim.x];
         bool moving = false;  // this thread left a moving particle for the second pass
         // A particle at rest (u = 0) in zero fields keeps its cell, offsets
         // and momentum: the step reads its cell (absorption) and momentum
@@ -1383,22 +1388,24 @@ __global__ void __launch_bounds__(kZeroThreads, 3) push_zero_kernel(const Run *_
         const uintptr_t al = (uintptr_t)pb.cell | (uintptr_t)pb.u[0] | (uintptr_t)pb.u[1] | (uintptr_t)pb.u[2];
         long long v0 = (p0 + 3) & ~3ll, v1 = p1 & ~3ll;
         if ((al & 15u) != 0 || v0 >= v1) v0 = v1 = p1;
-        // (two groups of four slots per thread and iteration, both loaded
-        // before either is processed: more bytes in flight)
+        // (kZeroGroups groups of four slots per thread and iteration, all
+        // loaded before any is processed: a tile of 4096 slots is one
+        // iteration of 256 threads, its loads all in flight together)
         const long long gend = v1 >> 2;
-        for (long long g = (v0 >> 2) + threadIdx.x; g < gend; g += 2 * blockDim.x) {
-            const long long gg[2] = {g, g + blockDim.x};
-            int4 c4[2];
-            float4 u4[2][3];
+        for (long long g = (v0 >> 2) + threadIdx.x; g < gend; g += kZeroGroups * blockDim.x) {
+            long long gg[kZeroGroups];
+            int4 c4[kZeroGroups];
+            float4 u4[kZeroGroups][3];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < kZeroGroups; ++h) {
+                gg[h] = g + h * (long long)blockDim.x;
                 if (gg[h] >= gend) break;
                 c4[h] = reinterpret_cast<const int4 *>(pb.cell)[gg[h]];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) u4[h][a] = reinterpret_cast<const float4 *>(pb.u[a])[gg[h]];
             }
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < kZeroGroups; ++h) {
                 if (gg[h] >= gend) break;
                 int32_t cl[4] = {c4[h].x, c4[h].y, c4[h].z, c4[h].w};
                 float uu[4][3] = {{u4[h][0].x, u4[h][1].x, u4[h][2].x}, {u4[h][0].y, u4[h][1].y, u4[h][2].y},
@@ -1446,13 +1453,9 @@ __global__ void __launch_bounds__(kZeroThreads, 3) push_zero_kernel(const Run *_
                 ++slow;
                 zero_mover<DIM, P, SPLIT>(r, z, pb, i);
             }
-            if (slow) atomicAdd(&s_slow, slow);
+            if (slow) atomicAdd(&r.state->slow, (unsigned long long)slow);
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            if (s_slow) atomicAdd(&r.state->slow, (unsigned long long)s_slow);
-            atomicAdd(&r.state->streamed, (unsigned long long)(p1 - p0));
-        }
+        if (threadIdx.x == 0) atomicAdd(&r.state->streamed, (unsigned long long)(p1 - p0));
     }
 }
 
