@@ -246,13 +246,23 @@ __global__ void __launch_bounds__(kSortThreads) sort_count_kernel(const Run *__r
         __syncthreads();
         const int lane = threadIdx.x & 31;
 #pragma unroll
-        for (int j = 0; j < kSortItems; ++j) {
-            const int key = sub_key(kc, key_of_cell(kc, cell[j]), item_slot(i0, j), cell[j]);
-            const unsigned peers = key_peers(key);
-            if (key >= 0 && lane == __ffs(peers) - 1) {
-                const int e = table_slot(t, key);
-                if (e >= 0) atomicAdd(&t.cnt[e], __popc(peers));
-                else atomicAdd(&r.tile_cnt[key], __popc(peers));
+        for (int g = 0; g < kSortItems / 4; ++g) {
+            int key[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                key[q] = sub_key(kc, key_of_cell(kc, cell[4 * g + q]), item_slot(i0, 4 * g + q), cell[4 * g + q]);
+            // (a sorted chunk: each thread's four consecutive slots mostly
+            // share a key, and a warp counts them as one item of weight 4)
+            const int nq = __all_sync(0xffffffffu, key[0] == key[1] && key[0] == key[2] && key[0] == key[3]) ? 1 : 4;
+            for (int q = 0; q < nq; ++q) {
+                const int kq = key[q];
+                const unsigned peers = key_peers(kq);
+                if (kq >= 0 && lane == __ffs(peers) - 1) {
+                    const int e = table_slot(t, kq);
+                    const int c = (5 - nq) * __popc(peers);
+                    if (e >= 0) atomicAdd(&t.cnt[e], c);
+                    else atomicAdd(&r.tile_cnt[kq], c);
+                }
             }
         }
         __syncthreads();
@@ -396,19 +406,48 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_scatter_kernel(const Run
         const unsigned below = (1u << lane) - 1u;
         int slot[kSortItems], rank[kSortItems];
 #pragma unroll
-        for (int j = 0; j < kSortItems; ++j) {
-            const int key = sub_key(kc, key_of_cell(kc, cell[j]), item_slot(i0, j), cell[j]);
-            const unsigned peers = key_peers(key);
-            const int leader = __ffs(peers) - 1;
-            int e = -2, off = 0;
-            if (key >= 0 && lane == leader) {
-                e = table_slot(t, key);
-                off = e >= 0 ? atomicAdd(&t.cnt[e], __popc(peers)) : atomicAdd(&r.tile_cnt[key], __popc(peers));
+        for (int g = 0; g < kSortItems / 4; ++g) {
+            int key[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                key[q] = sub_key(kc, key_of_cell(kc, cell[4 * g + q]), item_slot(i0, 4 * g + q), cell[4 * g + q]);
+            if (__all_sync(0xffffffffu, key[0] == key[1] && key[0] == key[2] && key[0] == key[3])) {
+                // each thread's four slots share a key: one item of weight 4
+                // per thread; slot q of each peer lane gets rank q (peers) +
+                // (peers below), so that one store instruction of the copy
+                // writes consecutive addresses
+                const unsigned peers = key_peers(key[0]);
+                const int leader = __ffs(peers) - 1;
+                int e = -2, off = 0;
+                if (key[0] >= 0 && lane == leader) {
+                    e = table_slot(t, key[0]);
+                    off = e >= 0 ? atomicAdd(&t.cnt[e], 4 * __popc(peers))
+                                 : atomicAdd(&r.tile_cnt[key[0]], 4 * __popc(peers));
+                }
+                e = __shfl_sync(0xffffffffu, e, leader);
+                off = __shfl_sync(0xffffffffu, off, leader);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    slot[4 * g + q] = key[0] >= 0 ? e : -2;
+                    rank[4 * g + q] = off + q * __popc(peers) + __popc(peers & below);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int key1 = key[q];
+                    const unsigned peers = key_peers(key1);
+                    const int leader = __ffs(peers) - 1;
+                    int e = -2, off = 0;
+                    if (key1 >= 0 && lane == leader) {
+                        e = table_slot(t, key1);
+                        off = e >= 0 ? atomicAdd(&t.cnt[e], __popc(peers)) : atomicAdd(&r.tile_cnt[key1], __popc(peers));
+                    }
+                    e = __shfl_sync(0xffffffffu, e, leader);
+                    off = __shfl_sync(0xffffffffu, off, leader);
+                    slot[4 * g + q] = key1 >= 0 ? e : -2;  // -2: dead or outside the window, -1: rank is absolute
+                    rank[4 * g + q] = off + __popc(peers & below);
+                }
             }
-            e = __shfl_sync(0xffffffffu, e, leader);
-            off = __shfl_sync(0xffffffffu, off, leader);
-            slot[j] = key >= 0 ? e : -2;  // -2: dead or outside the window, -1: rank is absolute
-            rank[j] = off + __popc(peers & below);
         }
         __syncthreads();
         for (int e = threadIdx.x; e < kSortHash; e += blockDim.x)
