@@ -97,7 +97,7 @@ def particle_chunks(w):
 # processed, scaled to the timed launches by their slot counts (the kernel's
 # traffic grows in proportion to its slots).
 ZERO_PROFILE = {
-    ("lwfa_3d", 2): (17.2, 1.64, "push_zero_kernel_lwfa3d_64x64x256.md"),
+    ("lwfa_3d", 2): (16.9, 1.52, "push_zero_kernel_lwfa3d_64x64x256.md"),
 }
 # the same per live-tile particle for the staged kernel (classification
 # included in its events, not in these figures)
