@@ -59,35 +59,157 @@ __device__ __forceinline__ bool live(const Run &r, const RunState &s, int32_t c,
     return true;
 }
 
+// Charge density rho = sum_p q w S(x - x_i) at the nodes (Sec. 2), FP64
+// sums.  Each CTA takes a chunk of kChargeChunk consecutive slots.  Slots
+// are in tile order after a sort and in load order before (neighbouring
+// slots hold neighbouring particles in both), so a chunk's node windows
+// usually fit a small box: the CTA accumulates the chunk's values in that
+// box in shared memory, as a fixed-point split of each value x = v S (the
+// nearest integer of x and 12 bits of the remainder, two int32 words, with
+// S = min(2^30 / sum |q w|, kChargeMax / max |q w|) over the chunk, so that
+// no word overflows and each split is exact), and adds each non-zero box
+// node to rho with one FP64 atomic.  The split represents each value to
+// 2^-13 / S, below the FP32 rounding of the value itself.  A chunk whose box
+// would exceed kChargeBox nodes (particles far apart: across a periodic
+// seam, or a run in no particular order) adds every value to rho directly.
+constexpr int kChargeChunk = 4096, kChargeItems = kChargeChunk / kBlock;
+constexpr int kChargeBox = 5120;           // nodes of the shared box (two words each)
+constexpr float kChargeRound = 12582912.f;  // 1.5 * 2^23: x + kChargeRound = 2^23 + 2^22 + rint(x), |x| < 2^22
+constexpr int kChargeRoundBits = 0x4B400000;
+constexpr float kChargeMax = 4.0e6f;  // bound on one scaled value (< 2^22)
+
 template <int DIM, int P>
-__global__ void charge_kernel(const Run *__restrict__ run, double *__restrict__ rho, long long cap)
+__global__ void __launch_bounds__(kBlock) charge_kernel(const Run *__restrict__ run, double *__restrict__ rho,
+                                                        long long cap)
 {
+    __shared__ int box[2 * kChargeBox];
+    __shared__ int s_lo[3], s_hi[3];
+    __shared__ float s_sum;
+    __shared__ unsigned s_max;
     const Run &r = *run;
     const RunState &s = *r.state;
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= s.n_total) return;
+    const long long i0 = (long long)blockIdx.x * kChargeChunk;
+    if (i0 >= s.n_total) return;
     const ParticleBuf pb = r.P[s.buf];
-    int c[3];
-    if (!live(r, s, pb.cell[i], c[0], c[1], c[2])) return;
-    int base[3] = {0, 0, 0};
-    float w[3][P + 1] = {};
+    if (threadIdx.x < 3) {
+        s_lo[threadIdx.x] = 0x7fffffff;
+        s_hi[threadIdx.x] = -0x7fffffff;
+    }
+    if (threadIdx.x == 0) {
+        s_sum = 0.f;
+        s_max = 0u;
+    }
+    __syncthreads();
+    // the bounding box of the chunk's live cells and the scale bounds
+    int lo[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, hi[3] = {-0x7fffffff, -0x7fffffff, -0x7fffffff};
+    float sum = 0.f, mx = 0.f;
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) Shape<P>::node(c[a], pb.off[a][i], base[a], w[a]);
-    // node values in FP32 (one rounding per value), sums in FP64: FP64
-    // arithmetic runs at a small fraction of the FP32 rate on this GPU
-    const float qw = r.q * (pb.w ? pb.w[i] : r.w_const);
-    const int n0 = r.n[0], n1 = r.n[1], n2 = DIM == 3 ? r.n[2] : 1;
+    for (int k = 0; k < kChargeItems; ++k) {
+        const long long i = i0 + (long long)k * kBlock + threadIdx.x;
+        int c[3] = {0, 0, 0};
+        if (i < s.n_total && live(r, s, pb.cell[i], c[0], c[1], c[2])) {
 #pragma unroll
-    for (int qz = 0; qz < (DIM == 3 ? P + 1 : 1); ++qz)
-#pragma unroll
-        for (int qy = 0; qy <= P; ++qy)
-#pragma unroll
-            for (int qx = 0; qx <= P; ++qx) {
-                const double v = (double)(qw * w[0][qx] * w[1][qy] * (DIM == 3 ? w[2][qz] : 1.f));
-                int x = wrapi(base[0] + qx, n0), y = wrapi(base[1] + qy, n1);
-                int z = DIM == 3 ? wrapi(base[2] + qz, n2) : 0;
-                atomicAdd(rho + x + n0 * (y + n1 * z), v);
+            for (int a = 0; a < DIM; ++a) {
+                lo[a] = min(lo[a], c[a]);
+                hi[a] = max(hi[a], c[a]);
             }
+            const float aq = fabsf(r.q * (pb.w ? pb.w[i] : r.w_const));
+            sum += aq;
+            mx = fmaxf(mx, aq);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            lo[a] = min(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = max(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+        }
+        sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            atomicMin(&s_lo[a], lo[a]);
+            atomicMax(&s_hi[a], hi[a]);
+        }
+        atomicAdd(&s_sum, sum);
+        atomicMax(&s_max, __float_as_uint(mx));  // (non-negative floats order as their bits)
+    }
+    __syncthreads();
+    if (s_hi[0] < s_lo[0]) return;  // (no live particle in the chunk; the same in every thread)
+    constexpr int NL = P / 2;       // nodes below a particle's cell (nodes above: NL + 1)
+    int org[3] = {0, 0, 0}, bd[3] = {1, 1, 1};
+    long long nodes = 1;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        org[a] = s_lo[a] - NL;
+        bd[a] = s_hi[a] - s_lo[a] + 2 * NL + 2;
+        nodes *= bd[a];
+    }
+    const bool use_box = nodes <= kChargeBox;  // (the same in every thread)
+    const float M = __uint_as_float(s_max), B = 1.01f * s_sum;
+    if (!(M > 0.f)) return;  // (no charge in the chunk)
+    const float S = fminf(1073741824.f / B, kChargeMax / M);
+    if (use_box) {
+        for (int q = threadIdx.x; q < 2 * (int)nodes; q += blockDim.x) box[q < (int)nodes ? q : kChargeBox + q - (int)nodes] = 0;
+        __syncthreads();
+    }
+    const int n0 = r.n[0], n1 = r.n[1], n2 = DIM == 3 ? r.n[2] : 1;
+#pragma unroll 1
+    for (int k = 0; k < kChargeItems; ++k) {
+        const long long i = i0 + (long long)k * kBlock + threadIdx.x;
+        int c[3] = {0, 0, 0};
+        if (i >= s.n_total || !live(r, s, pb.cell[i], c[0], c[1], c[2])) continue;
+        int base[3] = {0, 0, 0};
+        float w[3][P + 1] = {};
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) Shape<P>::node(c[a], pb.off[a][i], base[a], w[a]);
+        const float qw = r.q * (pb.w ? pb.w[i] : r.w_const);
+        if (use_box) {
+            const float qs = qw * S;
+            const int b0 = (base[0] - org[0]) + bd[0] * ((base[1] - org[1]) + bd[1] * (base[2] - org[2]));
+#pragma unroll
+            for (int qz = 0; qz < (DIM == 3 ? P + 1 : 1); ++qz)
+#pragma unroll
+                for (int qy = 0; qy <= P; ++qy)
+#pragma unroll
+                    for (int qx = 0; qx <= P; ++qx) {
+                        const float x = qs * w[0][qx] * w[1][qy] * (DIM == 3 ? w[2][qz] : 1.f);
+                        const float t = x + kChargeRound;          // kChargeRound + rint(x), exact
+                        const float rem = x - (t - kChargeRound);  // x - rint(x), exact, |rem| <= 1/2
+                        const float tl = fmaf(rem, 4096.f, kChargeRound);
+                        const int q = b0 + qx + bd[0] * (qy + bd[1] * qz);
+                        atomicAdd(&box[q], __float_as_int(t) - kChargeRoundBits);
+                        atomicAdd(&box[kChargeBox + q], __float_as_int(tl) - kChargeRoundBits);
+                    }
+        } else {
+            // node values in FP32 (one rounding per value), sums in FP64
+#pragma unroll
+            for (int qz = 0; qz < (DIM == 3 ? P + 1 : 1); ++qz)
+#pragma unroll
+                for (int qy = 0; qy <= P; ++qy)
+#pragma unroll
+                    for (int qx = 0; qx <= P; ++qx) {
+                        const double v = (double)(qw * w[0][qx] * w[1][qy] * (DIM == 3 ? w[2][qz] : 1.f));
+                        const int x = wrapi(base[0] + qx, n0), y = wrapi(base[1] + qy, n1);
+                        const int z = DIM == 3 ? wrapi(base[2] + qz, n2) : 0;
+                        atomicAdd(rho + x + (long long)n0 * (y + (long long)n1 * z), v);
+                    }
+        }
+    }
+    if (!use_box) return;
+    __syncthreads();
+    const double inv = 1.0 / (double)S, inv_lo = inv / 4096.0;
+    for (int q = threadIdx.x; q < (int)nodes; q += blockDim.x) {
+        const int vh = box[q], vl = box[kChargeBox + q];
+        if ((vh | vl) == 0) continue;
+        const int bx = q % bd[0], byz = q / bd[0], by = byz % bd[1], bz = byz / bd[1];
+        const int x = modi(org[0] + bx, n0), y = modi(org[1] + by, n1), z = DIM == 3 ? modi(org[2] + bz, n2) : 0;
+        atomicAdd(rho + x + (long long)n0 * (y + (long long)n1 * z), (double)vh * inv + (double)vl * inv_lo);
+    }
+    (void)cap;
 }
 
 __device__ __forceinline__ unsigned long long warp_slot(unsigned long long *count, bool want)
@@ -255,7 +377,7 @@ cudaError_t launch_to_float(const double *src, float *dst, long long n, cudaStre
 
 cudaError_t launch_charge(int dim, int order, const Run *run, double *rho, long long cap, cudaStream_t st)
 {
-    unsigned g = (unsigned)((cap + kBlock - 1) / kBlock);
+    unsigned g = (unsigned)((cap + kChargeChunk - 1) / kChargeChunk);
     if (g == 0) return cudaSuccess;
     if (dim == 2) {
         if (order == 1) charge_kernel<2, 1><<<g, kBlock, 0, st>>>(run, rho, cap);
