@@ -783,7 +783,8 @@ def main():
         e2e = {"value": units_e2e / sec, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(96 + 96 / args.steps),
                "includes": "pic_load_particles from pinned host memory, %d x (pic_step + pic_sync), "
-                           "pic_diagnostics" % args.steps}
+                           "pic_diagnostics (the handle, with its particle buffers of the configured "
+                           "capacity, is created before the timed region)" % args.steps}
         sim2.close()
         del sim2, pinned
 

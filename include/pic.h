@@ -234,7 +234,9 @@ typedef struct {
     pic_laser laser;
     pic_window window;
     uint64_t seed;
-    int64_t capacity;    /* particle slots (0 = 1.25x the first load + injection room) */
+    int64_t capacity;    /* particle slots, allocated by pic_create (two buffers; PIC_ENOMEM
+                            there if they do not fit); 0 = 1.25x the first load + injection
+                            room, allocated by the first pic_load_particles */
     pic_tuning tuning;
     pic_alloc_fn alloc;  /* NULL: cudaMalloc */
     pic_free_fn free;

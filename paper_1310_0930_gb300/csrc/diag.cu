@@ -34,9 +34,14 @@ __global__ void pack_kernel(const Run *__restrict__ run, long long base, long lo
     }
     if (!ok) atomicOr(&s.status, kStatusBadIndex);
     pb.cell[o] = ok ? pack_cell(r, c[0], c[1], dim == 3 ? c[2] : 0) : -1;
-    pb.u[0][o] = u[i];
-    pb.u[1][o] = u[n + i];
-    pb.u[2][o] = u[2 * n + i];
+    const float u0 = u[i], u1 = u[n + i], u2 = u[2 * n + i];
+    pb.u[0][o] = u0;
+    pb.u[1][o] = u1;
+    pb.u[2][o] = u2;
+    // a moving particle deposits current at the first step: its tile is
+    // staged then, not streamed as a field-free tile (several threads may
+    // store the same 1)
+    if (ok && (u0 != 0.f || u1 != 0.f || u2 != 0.f) && r.fz) r.fz[tile_of(r, c[0], c[1], dim == 3 ? c[2] : 0)] = 1;
     if (pb.w) pb.w[o] = w ? w[i] : r.w_const;
     if (pb.id) pb.id[o] = (int32_t)o;
 }

@@ -680,7 +680,9 @@ int init_run(pic_s *h, HostRun &hr, int idx)
     if (e == cudaSuccess) e = cudaMemsetAsync(r.rho0, 0, sizeof(double) * ncell, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(r.mur, 0, sizeof(float) * 8 * plane, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(r.tile_off, 0, sizeof(int32_t) * (r.ntiles + 1), h->stream);
-    if (e == cudaSuccess) e = flag_all_tiles(h, hr);
+    // E = B = +0 in every tile; loading a moving particle flags its tile
+    // (pack_kernel), writing E or B flags every tile
+    if (e == cudaSuccess) e = cudaMemsetAsync(r.fz, 0, (size_t)r.ntiles, h->stream);
     if (e != cudaSuccess) return PIC_ECUDA;
     const pic_laser &L = c.laser;
     r.laser_on = L.enabled;
@@ -817,6 +819,14 @@ int create_common(const pic_config *cfgs, int n, pic_t **out)
             aligned = aligned && (uintptr_t)hr.r.E[c] % 16 == 0 && (uintptr_t)hr.r.B[c] % 16 == 0 &&
                       (uintptr_t)hr.r.J[hr.r.jst == 4 ? 0 : c] % 16 == 0;
         h->yee_quad = h->yee_quad && aligned;
+        // a configured capacity is allocated now (the loads then only copy)
+        if (hr.cfg.capacity > 0) {
+            rc = alloc_particles(h, hr, hr.cfg.capacity, 0, 0);
+            if (rc) {
+                pic_destroy(h);
+                return rc;
+            }
+        }
     }
     int rc = upload_runs(h);
     if (!rc) rc = set_seg(h, 0, h->seg_cells, cells);
@@ -1188,7 +1198,7 @@ int pic_adjoint_begin(pic_t *h, int32_t total_steps, int32_t checkpoint_every)
     if (!h || total_steps < 1 || checkpoint_every < 1) return PIC_EINVAL;
     if (h->started || h->adj || h->nruns != 1) return PIC_ESTATE;
     HostRun &hr = h->runs[0];
-    if (!hr.cfg.track_ids || !hr.sp.per_particle_weight || !hr.r.P[0].cell) return PIC_EINVAL;
+    if (!hr.cfg.track_ids || !hr.sp.per_particle_weight || hr.loaded <= 0) return PIC_EINVAL;
     if (h->order > 3) return PIC_EINVAL;  // (the reverse kernels are compiled for orders 1 to 3)
     if (h->split) return PIC_EINVAL;      // (they transpose the undivided deposit)
     RunState st;
@@ -1521,7 +1531,7 @@ int pic_adjoint_particles(pic_t *h, float *lam_x, float *lam_u, const float *lam
     if (h->nruns != 1) return PIC_ESTATE;
     HostRun &hr = h->runs[0];
     if (!hr.cfg.track_ids || !hr.sp.per_particle_weight || hr.r.window_on || h->order > 3 || h->split ||
-        !hr.r.P[0].cell)
+        hr.loaded <= 0)
         return PIC_EINVAL;
     if (!h->started) {
         int rc = first_step_setup(h);
