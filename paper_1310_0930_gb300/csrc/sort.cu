@@ -15,14 +15,18 @@
 //   1. zero the key counters;
 //   2. histogram of keys, aggregated per warp (match on the key) and per CTA
 //      (a shared-memory key table over a chunk of kSortChunk slots), so that
-//      the global counters see a few atomics per chunk;
+//      the global counters see a few atomics per chunk; where each thread's
+//      four consecutive slots share one key (a chunk still in sorted order)
+//      the warp counts them as one item of weight four;
 //   3. exclusive scan of the counters in blocks of kScanChunk keys (block
 //      sums, an exclusive scan of the block sums, then each block adds its
 //      prefix); the counters become the scatter cursors and tile_off[t] the
 //      offset of key (t, 0);
 //   4. scatter every live particle into the alternate buffer at
 //      offset[key] + rank: ranks within the chunk come from the CTA's key
-//      table, and one cursor atomic per (chunk, key) reserves the range;
+//      table (weight-four items as in the count, ranked so that the lanes
+//      of one store instruction write consecutive slots), and one cursor
+//      atomic per (chunk, key) reserves the range;
 //   5. flip the buffer and set the sorted count.
 // Order within a key is not stable (cursor atomics); nothing downstream
 // depends on it.
