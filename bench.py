@@ -102,7 +102,7 @@ ZERO_PROFILE = {
 # the same per live-tile particle for the staged kernel (classification
 # included in its events, not in these figures)
 STAGED_PROFILE = {
-    ("lwfa_3d", 2): (42.8, 32.7, "push_kernel_lwfa3d_quadratic_128x128x512.md"),
+    ("lwfa_3d", 2): (42.7, 32.7, "push_kernel_lwfa3d_quadratic_128x128x512.md"),
 }
 
 
