@@ -365,9 +365,6 @@ def adjoint_measure(args, S, warmup):
     from paper_1310_0930_gb300.sim import Simulation, TorchMemory
 
     torch.cuda.set_device(0)
-    # (blocks the caching allocator kept from the legs before go back first:
-    # the library sizes the records it keeps by the device's free memory)
-    torch.cuda.empty_cache()
     w = inputs.adjoint_2d(steps=S)
     parts = inputs.background(w)
     obj = (100.0, 300.0, 2.0)
