@@ -71,8 +71,10 @@ cudaError_t launch_push(int dim, int order, const int *tile, int drift, int vari
 // then advanced by the streaming kernel (launch_push_zero).
 cudaError_t launch_classify(const Run *runs, const Item *items, int n_tail, int n_items, const int *stage_lo,
                             const int *stage_len, Item *live, Item *zero, int *cnt, cudaStream_t st);
+// wide: every run's tiles hold at least 4096 particles (four groups of four
+// slots per thread and two CTAs per SM; otherwise two groups, three CTAs)
 cudaError_t launch_push_zero(int dim, int order, bool split, const Run *runs, const Item *zero, const int *count,
-                             int max_items, int num_sms, cudaStream_t st);
+                             int max_items, int num_sms, bool wide, cudaStream_t st);
 
 // fields.cu
 cudaError_t launch_zero_j(const Run *runs, Seg cells, bool quad, cudaStream_t st);

@@ -88,6 +88,7 @@ struct pic_s {
     int n_items = 0;
     int n_tail = 0;               // leading tail items of d_items
     bool classify = true;         // stream the zero-field tiles (launch_classify)
+    bool zero_wide = true;        // every run's tiles hold >= 4096 particles (streaming kernel variant)
     Item *d_live = nullptr;       // per step: tail items, then the live tiles
     Item *d_zero = nullptr;       // per step: the zero-field tiles
     Item *d_nq = nullptr;         // per step: the rows of tiles with a tile that is not quiet (field update, next J reset)
@@ -464,7 +465,8 @@ int enqueue_step(pic_s *h, bool sort, bool adaptive)
         if (e == cudaSuccess) e = launch_push(h->dim, h->order, h->tile, h->drift, h->variant(), a, st);
         if (ev && e == cudaSuccess) e = cudaEventRecord(ev[kMarkZero], st);
         if (e == cudaSuccess)
-            e = launch_push_zero(h->dim, h->order, h->split, R, h->d_zero, h->d_cnt + 1, n_tiles, h->num_sms, st);
+            e = launch_push_zero(h->dim, h->order, h->split, R, h->d_zero, h->d_cnt + 1, n_tiles, h->num_sms,
+                                 h->zero_wide, st);
     } else {
         const PushArgs a{R, h->d_items, h->n_items, nullptr, 0, h->block, h->tail_block,
                          h->persistent ? h->d_queue : nullptr, h->num_sms};
@@ -532,6 +534,12 @@ int first_step_setup(pic_s *h)
     if (!rc) rc = set_seg(h, 3, h->seg_inject, inj);
     if (!rc) rc = build_items(h);
     if (rc) return rc;
+    h->zero_wide = true;
+    for (int i = 0; i < h->nruns; ++i) {
+        long long per_tile = 1;
+        for (int a = 0; a < h->dim; ++a) per_tile *= (long long)h->tile[a] * h->runs[i].sp.ppc[a];
+        h->zero_wide = h->zero_wide && per_tile >= 4096;
+    }
     // the initial electron charge is the neutralising background (rho_0)
     for (int i = 0; i < h->nruns; ++i) {
         HostRun &hr = h->runs[i];

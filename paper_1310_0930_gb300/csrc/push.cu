@@ -163,29 +163,29 @@ cudaError_t launch_classify(const Run *runs, const Item *items, int n_tail, int 
 }
 
 cudaError_t launch_push_zero(int dim, int order, bool split, const Run *runs, const Item *zero, const int *count,
-                             int max_items, int num_sms, cudaStream_t st)
+                             int max_items, int num_sms, bool wide, cudaStream_t st)
 {
     using namespace push_detail;
     if (split) {  // (moving particles of zero-field tiles deposit as virtual trajectories)
         if (dim == 2) {
-            if (order == 1) return launch_zero<2, 1, true>(runs, zero, count, max_items, num_sms, st);
-            if (order == 2) return launch_zero<2, 2, true>(runs, zero, count, max_items, num_sms, st);
-            return launch_zero<2, 3, true>(runs, zero, count, max_items, num_sms, st);
+            if (order == 1) return launch_zero<2, 1, true>(runs, zero, count, max_items, num_sms, wide, st);
+            if (order == 2) return launch_zero<2, 2, true>(runs, zero, count, max_items, num_sms, wide, st);
+            return launch_zero<2, 3, true>(runs, zero, count, max_items, num_sms, wide, st);
         }
-        if (order == 1) return launch_zero<3, 1, true>(runs, zero, count, max_items, num_sms, st);
-        if (order == 2) return launch_zero<3, 2, true>(runs, zero, count, max_items, num_sms, st);
-        return launch_zero<3, 3, true>(runs, zero, count, max_items, num_sms, st);
+        if (order == 1) return launch_zero<3, 1, true>(runs, zero, count, max_items, num_sms, wide, st);
+        if (order == 2) return launch_zero<3, 2, true>(runs, zero, count, max_items, num_sms, wide, st);
+        return launch_zero<3, 3, true>(runs, zero, count, max_items, num_sms, wide, st);
     }
     if (dim == 2) {
-        if (order == 1) return launch_zero<2, 1>(runs, zero, count, max_items, num_sms, st);
-        if (order == 2) return launch_zero<2, 2>(runs, zero, count, max_items, num_sms, st);
-        if (order == 3) return launch_zero<2, 3>(runs, zero, count, max_items, num_sms, st);
-        return launch_zero<2, 4>(runs, zero, count, max_items, num_sms, st);
+        if (order == 1) return launch_zero<2, 1>(runs, zero, count, max_items, num_sms, wide, st);
+        if (order == 2) return launch_zero<2, 2>(runs, zero, count, max_items, num_sms, wide, st);
+        if (order == 3) return launch_zero<2, 3>(runs, zero, count, max_items, num_sms, wide, st);
+        return launch_zero<2, 4>(runs, zero, count, max_items, num_sms, wide, st);
     }
-    if (order == 1) return launch_zero<3, 1>(runs, zero, count, max_items, num_sms, st);
-    if (order == 2) return launch_zero<3, 2>(runs, zero, count, max_items, num_sms, st);
-    if (order == 3) return launch_zero<3, 3>(runs, zero, count, max_items, num_sms, st);
-    return launch_zero<3, 4>(runs, zero, count, max_items, num_sms, st);
+    if (order == 1) return launch_zero<3, 1>(runs, zero, count, max_items, num_sms, wide, st);
+    if (order == 2) return launch_zero<3, 2>(runs, zero, count, max_items, num_sms, wide, st);
+    if (order == 3) return launch_zero<3, 3>(runs, zero, count, max_items, num_sms, wide, st);
+    return launch_zero<3, 4>(runs, zero, count, max_items, num_sms, wide, st);
 }
 
 }  // namespace pic

@@ -1278,17 +1278,21 @@ __device__ __forceinline__ void process_item(const Run *__restrict__ runs, const
 // +0), so a particle at rest stays where it is and deposits no current: its
 // step reads its cell (absorption at an open window's ends) and momentum and
 // changes nothing else.  Such tiles are streamed by this kernel with 16-byte
-// loads (four groups of four consecutive slots per thread, two CTAs of 256
-// threads per SM; the ragged ends of a tile's range slot by slot) and no
-// shared-memory tiles; each CTA loads its next item while it streams the
-// current one.  A particle of such a tile that does
+// loads (four groups of four consecutive slots per thread at two CTAs of
+// 256 threads per SM for tiles of 4096 slots and more, two groups at three
+// CTAs per SM for smaller tiles; the ragged ends of a tile's range slot by
+// slot) and no shared-memory tiles; each CTA loads its next item while it
+// streams the current one.  A particle of such a tile that does
 // move takes the general slow path (the gather from global memory reads the
 // same zeros; the current goes to global memory by atomics) and is counted as
 // a slow-path particle.  Particles outside their tile's drift region cost
 // nothing here (no tile is staged) and are not counted as strays: the
 // adaptive sort counts the strays that slow the staged kernel down.
 constexpr int kZeroThreads = 256;
-constexpr int kZeroGroups = 4;  // groups of four slots per thread and iteration
+// Groups of four slots per thread and iteration: four (two CTAs per SM) for
+// tiles of at least kZeroWideSlots slots, two (three CTAs per SM) for
+// smaller ones, whose passes would otherwise leave threads idle.
+constexpr int kZeroWideSlots = 4096;
 
 struct ZeroCtx {
     int origin, nl;
@@ -1346,10 +1350,10 @@ __device__ __forceinline__ void zero_mover(const Run &r, const ZeroCtx &z, const
     for (int a = 0; a < 3; ++a) pb.u[a][i] = so.u[a];
 }
 
-template <int DIM, int P, bool SPLIT>
-__global__ void __launch_bounds__(kZeroThreads, 2) push_zero_kernel(const Run *__restrict__ runs,
-                                                                    const Item *__restrict__ list,
-                                                                    const int *__restrict__ count)
+template <int DIM, int P, bool SPLIT, int NG>
+__global__ void __launch_bounds__(kZeroThreads, NG >= 4 ? 2 : 3) push_zero_kernel(const Run *__restrict__ runs,
+                                                                                 const Item *__restrict__ list,
+                                                                                 const int *__restrict__ count)
 {
     __shared__ Run rs;
     const int n = *count;
@@ -1388,16 +1392,16 @@ __global__ void __launch_bounds__(kZeroThreads, 2) push_zero_kernel(const Run *_
         const uintptr_t al = (uintptr_t)pb.cell | (uintptr_t)pb.u[0] | (uintptr_t)pb.u[1] | (uintptr_t)pb.u[2];
         long long v0 = (p0 + 3) & ~3ll, v1 = p1 & ~3ll;
         if ((al & 15u) != 0 || v0 >= v1) v0 = v1 = p1;
-        // (kZeroGroups groups of four slots per thread and iteration, all
-        // loaded before any is processed: a tile of 4096 slots is one
+        // (NG groups of four slots per thread and iteration, all loaded
+        // before any is processed: with NG = 4 a tile of 4096 slots is one
         // iteration of 256 threads, its loads all in flight together)
         const long long gend = v1 >> 2;
-        for (long long g = (v0 >> 2) + threadIdx.x; g < gend; g += kZeroGroups * blockDim.x) {
-            long long gg[kZeroGroups];
-            int4 c4[kZeroGroups];
-            float4 u4[kZeroGroups][3];
+        for (long long g = (v0 >> 2) + threadIdx.x; g < gend; g += NG * blockDim.x) {
+            long long gg[NG];
+            int4 c4[NG];
+            float4 u4[NG][3];
 #pragma unroll
-            for (int h = 0; h < kZeroGroups; ++h) {
+            for (int h = 0; h < NG; ++h) {
                 gg[h] = g + h * (long long)blockDim.x;
                 if (gg[h] >= gend) break;
                 c4[h] = reinterpret_cast<const int4 *>(pb.cell)[gg[h]];
@@ -1405,7 +1409,7 @@ __global__ void __launch_bounds__(kZeroThreads, 2) push_zero_kernel(const Run *_
                 for (int a = 0; a < 3; ++a) u4[h][a] = reinterpret_cast<const float4 *>(pb.u[a])[gg[h]];
             }
 #pragma unroll
-            for (int h = 0; h < kZeroGroups; ++h) {
+            for (int h = 0; h < NG; ++h) {
                 if (gg[h] >= gend) break;
                 int32_t cl[4] = {c4[h].x, c4[h].y, c4[h].z, c4[h].w};
                 float uu[4][3] = {{u4[h][0].x, u4[h][1].x, u4[h][2].x}, {u4[h][0].y, u4[h][1].y, u4[h][2].y},
@@ -1524,19 +1528,28 @@ cudaError_t launch_t(const Run *runs, const Item *items, int nitems, int block, 
     return cudaGetLastError();
 }
 
-template <int DIM, int P, bool SPLIT = false>
-cudaError_t launch_zero(const Run *runs, const Item *list, const int *count, int max_items, int num_sms,
-                        cudaStream_t st)
+template <int DIM, int P, bool SPLIT, int NG>
+cudaError_t launch_zero_ng(const Run *runs, const Item *list, const int *count, int max_items, int num_sms,
+                           cudaStream_t st)
 {
-    if (max_items <= 0) return cudaSuccess;
     int per_sm = 0;
     cudaError_t e =
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, push_zero_kernel<DIM, P, SPLIT>, kZeroThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, push_zero_kernel<DIM, P, SPLIT, NG>, kZeroThreads, 0);
     if (e != cudaSuccess) return e;
     int grid = num_sms * (per_sm > 0 ? per_sm : 1);
     grid = grid < max_items ? grid : max_items;
-    push_zero_kernel<DIM, P, SPLIT><<<grid, kZeroThreads, 0, st>>>(runs, list, count);
+    push_zero_kernel<DIM, P, SPLIT, NG><<<grid, kZeroThreads, 0, st>>>(runs, list, count);
     return cudaGetLastError();
+}
+
+// wide: every run's tiles hold at least kZeroWideSlots particles
+template <int DIM, int P, bool SPLIT = false>
+cudaError_t launch_zero(const Run *runs, const Item *list, const int *count, int max_items, int num_sms, bool wide,
+                        cudaStream_t st)
+{
+    if (max_items <= 0) return cudaSuccess;
+    return wide ? launch_zero_ng<DIM, P, SPLIT, 4>(runs, list, count, max_items, num_sms, st)
+                : launch_zero_ng<DIM, P, SPLIT, 2>(runs, list, count, max_items, num_sms, st);
 }
 
 }  // namespace push_detail
