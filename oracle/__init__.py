@@ -28,6 +28,20 @@ force, never against itself:
 * laser-plasma coupling  -- the linear wake of a weak Gaussian pulse: peak
                             field, wavelength at the group velocity, a0^2
                             scaling against the 1D closed form.
+* energies               -- kinetic energy of particles accelerated by a
+                            uniform field against its closed form, the work
+                            q E . dx of a step against the kinetic energy it
+                            adds, W_E + W_kin of a cold oscillation within the
+                            leapfrog bound (``tests/test_oracle_energy.py``).
+* density profile        -- the weights of the plasma a moving window injects
+                            follow the piecewise-linear knot profile at each
+                            particle's lab position.
+* deposit_current_split  -- virtual trajectories (Sec. 5.2 iv): continuity,
+                            total current, no split inside one node cell,
+                            Villasenor-Buneman pieces across faces.
+* energy history         -- one recorded 32x32 warm-plasma history
+                            (``tests/golden/``, written from this oracle alone)
+                            reproduced to round-off.
 LWFA physics beyond these (nonlinear wakes, self-injection): parity unpinned.
 """
 from __future__ import annotations
